@@ -1,0 +1,248 @@
+"""Pins for the oracle's per-ray field and compositing (Sec. 2, Sec. 3.1, Sec. 4.1, Sec. 1 DVR).
+
+* camera rays and candidate sets against an independent numpy brute force,
+* the direct per-piece summation equals the paper's coefficient-update
+  recurrence (Sec. 2, eq. Piecewise-Coefficients-Update) run here in exact
+  rational arithmetic from the same knots,
+* the summed approximations converge to the exact SPH field as the table gets
+  denser (Sec. 3.1), to within the approximation error,
+* compositing against closed forms and a dense Riemann sum.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_02896_b300 import synthetic as S
+
+
+@pytest.fixture(scope="module")
+def c1():
+    P = S.uniform_cube()
+    P["amp"] = S.particles_to_amp(P["mass"], P["value"], P["density"])
+    return P
+
+
+@pytest.fixture(scope="module")
+def lut_m4():
+    return oracle.lut_build("m4", 4, 3, 129)
+
+
+def _ray_np(cam, p):
+    f = np.array(cam["target"], float) - np.array(cam["eye"], float)
+    f /= np.linalg.norm(f)
+    r = np.cross(f, np.array(cam["up"], float))
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    W, H = cam["width"], cam["height"]
+    px, py = p % W, p // W
+    sx = 2 * (px + 0.5) / W - 1
+    sy = 1 - 2 * (py + 0.5) / H
+    if cam["projection"] == "perspective":
+        th = math.tan(math.radians(cam["fovy_deg"]) / 2)
+        d = f + sx * th * W / H * r + sy * th * u
+        return np.array(cam["eye"], float), d / np.linalg.norm(d)
+    return np.array(cam["eye"], float) + sx * cam["half_w"] * r + sy * cam["half_h"] * u, f
+
+
+@pytest.mark.parametrize("cam", [S.ortho_camera_z(64, 48), S.orbit_camera(40, 30, 25, 10)])
+def test_camera_rays(cam):
+    for p in [0, 7, cam["width"] * cam["height"] // 2 + 3, cam["width"] * cam["height"] - 1]:
+        o, v = oracle.camera_ray(cam, p)
+        o2, v2 = _ray_np(cam, p)
+        assert np.allclose(o, o2, atol=1e-15, rtol=0) and np.allclose(v, v2, atol=1e-15, rtol=0)
+
+
+def _brute_candidates(P, o, v, q, t_near):
+    x = P["pos"].astype(np.float64) - o
+    tc = x @ v
+    d = np.linalg.norm(x - tc[:, None] * v[None, :], axis=1)
+    h = P["h"].astype(np.float64)
+    R = q * h
+    ok = (d < R) & (tc + np.sqrt(np.clip(R * R - d * d, 0, None)) > t_near)
+    band = np.abs(d - R) <= 1e-6 * h
+    return set(np.nonzero(ok & ~band)[0]), set(np.nonzero(band)[0]), tc, d
+
+
+@pytest.mark.parametrize("cam", [S.ortho_camera_z(16, 16), S.orbit_camera(16, 16, 40, 25, distance=1.2)])
+def test_candidates_brute_force(c1, lut_m4, cam):
+    tf = S.tf_bumps()
+    pix = np.arange(cam["width"] * cam["height"])
+    R = oracle.render(c1, lut_m4, cam, tf, pix, cand_cap=512)
+    for r, p in enumerate(pix):
+        o, v = _ray_np(cam, p)
+        want, band, _, _ = _brute_candidates(c1, o, v, 2.0, cam["t_near"])
+        got = set(int(i) for i in R["cand_ids"][r][: R["stats"][r][0]])
+        assert want == got - band
+        assert R["stats"][r][1] == 5 * R["stats"][r][0]
+
+
+def _jump_coefficients(lut, j):
+    """Per knot of entry j (sorted), the localized difference coefficients (Sec. 2): right piece minus
+    left piece, expanded at the knot, in normalised units."""
+    K, D = lut["K"], lut["D"]
+    th = lut["theta"][j]
+    P = lut["pieces"][j]
+    m = len(th)
+    knots = oracle.entry_knots(lut, j)
+
+    def piece_poly(s_mid):
+        # polynomial (in s, as numpy poly1d) valid around s_mid
+        a = abs(s_mid)
+        lo = 0.0
+        for k in range(m):
+            if a <= th[k]:
+                loc = np.poly1d(P[k][::-1])
+                if s_mid >= 0:
+                    return loc(np.poly1d([1.0, -lo]))
+                return loc(np.poly1d([-1.0, -lo]))
+            lo = th[k]
+        return np.poly1d([0.0])
+
+    out = []
+    for i, s in enumerate(knots):
+        left = piece_poly(0.5 * (knots[i - 1] + s)) if i > 0 else np.poly1d([0.0])
+        right = piece_poly(0.5 * (s + knots[i + 1])) if i + 1 < len(knots) else np.poly1d([0.0])
+        diff = right - left
+        # Taylor coefficients at s
+        c = [diff.deriv(e)(s) / math.factorial(e) if e <= diff.order else 0.0 for e in range(D + 1)]
+        out.append((s, c))
+    return out
+
+
+def test_direct_summation_equals_recurrence(c1, lut_m4):
+    cam = S.ortho_camera_z(64, 64)
+    tf = S.tf_bumps()
+    pix = np.array([0, 1000, 2080, 3001], np.int32)
+    R = oracle.render(c1, lut_m4, cam, tf, pix, cand_cap=512, field_cap=4096)
+    D = lut_m4["D"]
+    nl = lut_m4["n_lambda"]
+    for r, p in enumerate(pix):
+        o, v = _ray_np(cam, p)
+        ids = R["cand_ids"][r][: R["stats"][r][0]]
+        knots = []
+        for i in ids:
+            x = c1["pos"][i].astype(np.float64) - o
+            tc = float(x @ v)
+            d = float(np.linalg.norm(x - tc * v))
+            h = float(c1["h"][i])
+            j = min(int(math.floor(d / h * (nl - 1) / 2.0 + 0.5)), nl - 1)
+            amp = float(c1["amp"][i]) / h ** 3
+            for s, cf in _jump_coefficients(lut_m4, j):
+                # real units: t = tc + s h, a_d = amp * c_d / h^d
+                knots.append((tc + s * h, [amp * cf[e] / h ** e for e in range(D + 1)]))
+        knots.sort(key=lambda kv: kv[0])
+        # eq. (Piecewise-Coefficients-Update) in exact rational arithmetic
+        a = [Fraction(0)] * (D + 1)
+        tprev = None
+        pieces = []
+        for k, (t, ah) in enumerate(knots):
+            tF = Fraction(t)
+            if tprev is not None:
+                dt = tF - tprev
+                a = [sum(math.comb(jj, dd) * a[jj] * dt ** (jj - dd) for jj in range(dd, D + 1)) for dd in range(D + 1)]
+            a = [a[dd] + Fraction(ah[dd]) for dd in range(D + 1)]
+            tprev = tF
+            if k + 1 < len(knots) and knots[k + 1][0] > t:
+                pieces.append((t, [float(x) for x in a]))
+        rows = R["field"][r][: R["stats"][r][5]]
+        assert len(rows) == len(pieces)
+        scale = max(abs(row[2]) for row in rows)
+        for (t, ac), row in zip(pieces, rows):
+            assert t == row[0]
+            for e in range(D + 1):
+                hpow = 0.08 ** e
+                assert abs(ac[e] - row[2 + e]) * hpow <= 1e-9 * scale, (r, t, e, ac[e], row[2 + e])
+
+
+def _sph_field(P, o, v, ts, kernel="m4"):
+    x = o[None, :] + ts[:, None] * v[None, :]
+    out = np.zeros(len(ts))
+    pos = P["pos"].astype(np.float64)
+    h = P["h"].astype(np.float64)
+    for i in range(0, len(pos)):
+        r = np.linalg.norm(x - pos[i], axis=1) / h[i]
+        w = np.vectorize(lambda rr: oracle.kernel_w(kernel, rr))(r[r < 2.0]) if np.any(r < 2.0) else None
+        if w is not None:
+            out[r < 2.0] += P["amp"][i] / h[i] ** 3 * w
+    return out
+
+
+def test_field_converges_to_sph_sum(c1):
+    cam = S.ortho_camera_z(64, 64)
+    tf = S.tf_bumps()
+    p = 2080
+    o, v = _ray_np(cam, p)
+    ts = np.linspace(0.9, 2.1, 1500)
+    exact = _sph_field(c1, o, v, ts)
+    errs = []
+    for n in (17, 65, 513):
+        lut = oracle.lut_build("m4", 4, 3, n)
+        R = oracle.render(c1, lut, cam, tf, np.array([p], np.int32), field_cap=4096)
+        approx = oracle.field_eval(R["field"][0][: R["stats"][0][5]], ts)
+        errs.append(np.linalg.norm(approx - exact) / np.linalg.norm(exact))
+    # denser tables converge toward the optimal-approximation floor (E_{4,3} ~ 1e-3)
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 3e-3
+
+
+def _tf_const(rgb, a, n=8, lo=0.0, hi=1.0, s=1.0):
+    rgba = np.zeros((n, 4))
+    rgba[:, :3] = rgb
+    rgba[:, 3] = a
+    return dict(rgba=rgba, lo=lo, hi=hi, sigma_scale=s)
+
+
+def test_composite_constant_field_closed_form():
+    tf = _tf_const([0.2, 0.5, 0.9], 1.7, s=1.3)
+    L = 0.8
+    rgb, T = oracle.composite_piece(tf, [0.4, 0.0], 0.0, L)
+    sig = 1.7 * 1.3
+    assert abs(T - math.exp(-sig * L)) < 1e-15
+    for c, ref in zip(rgb, [0.2, 0.5, 0.9]):
+        assert abs(c - ref * (1 - math.exp(-sig * L))) < 1e-14
+
+
+def test_composite_linear_colour_closed_form():
+    # sigma constant, colour linear in the field, field linear in t: closed form by parts
+    n = 5
+    rgba = np.zeros((n, 4))
+    rgba[:, 0] = np.linspace(0, 1, n)  # red = f on [0,1]
+    rgba[:, 3] = 2.0
+    tf = dict(rgba=rgba, lo=0.0, hi=1.0, sigma_scale=1.0)
+    a, b, L, sg = 0.1, 0.6, 1.2, 2.0  # f = a + b t stays inside [0,1]
+    rgb, T = oracle.composite_piece(tf, [a, b], 0.0, L)
+    # int_0^L (a + b t) sg e^{-sg t} dt
+    ref = a * (1 - math.exp(-sg * L)) + b * (1 / sg - math.exp(-sg * L) * (L + 1 / sg))
+    assert abs(rgb[0] - ref) < 1e-14
+    assert abs(T - math.exp(-sg * L)) < 1e-15
+
+
+def test_composite_many_crossings_riemann():
+    tf = S.tf_bumps(n=64, lo=0.0, hi=2.0, sigma_scale=3.0)
+    F = [0.1, 3.0, -2.5, 0.4]  # cubic: rises and falls through many nodes on [0, 1.5]
+    ya, yb = 0.0, 1.5
+    rgb, T = oracle.composite_piece(tf, F, ya, yb)
+    # dense midpoint rule of the same definition
+    N = 400000
+    t = (np.arange(N) + 0.5) * (yb - ya) / N + ya
+    f = np.polyval(F[::-1], t)
+    v = tf["rgba"].astype(np.float64)
+    x = np.clip((f - tf["lo"]) / (tf["hi"] - tf["lo"]), 0, 1) * (len(v) - 1)
+    i = np.minimum(np.floor(x).astype(int), len(v) - 2)
+    fr = x - i
+    col = v[i] * (1 - fr)[:, None] + v[i + 1] * fr[:, None]
+    sig = tf["sigma_scale"] * col[:, 3]
+    dt = (yb - ya) / N
+    tau = np.cumsum(sig) * dt - 0.5 * sig * dt
+    em = (col[:, :3] * (sig * np.exp(-tau))[:, None]).sum(0) * dt
+    assert np.allclose(rgb, em, atol=2e-8)
+    assert abs(T - math.exp(-sig.sum() * dt)) < 2e-8
+
+
+def test_ray_without_candidates_is_transparent(c1, lut_m4):
+    cam = S.ortho_camera_z(4, 4, lo=(5.0, 5.0), hi=(6.0, 6.0))
+    R = oracle.render(c1, lut_m4, cam, S.tf_bumps(), np.arange(16), cand_cap=8)
+    assert np.all(R["rgba"] == 0) and np.all(R["stats"][:, 0] == 0)
