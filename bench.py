@@ -1,0 +1,289 @@
+#!/usr/bin/env python
+"""Benchmark of the per-ray higher-order SPH field reconstruction + DVR path.
+
+Default workload (one B300): 16,777,216 particles from a Plummer-halo mixture
+with a uniform background (h spans about three decades), Wendland C2 kernel,
+K = 4 pieces of degree D = 3 per particle, a 4096-entry table, perspective
+camera 2048 x 2048.  One step = one frame rendered through the library
+(binning + render kernel); the particle set (384 MB, larger than L2) is
+resident.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sphdvr|reference]
+
+Under torchrun (N > 1) every rank renders its own frames (different cameras)
+of the same resident data: weak scaling, no data-path collective; the value
+is all ranks' rays over the slowest rank's time.  ``--impl reference`` times
+the FP64 CPU oracle on a bounded sample of the same frame's pixels.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2401_02896_b300 import synthetic as SY  # noqa: E402
+
+WORKLOADS = {
+    "halo16m": dict(n=16_777_216, a_range=(5e-4, 0.05), seed=SY.BASE_SEED + 2, kernel="wendland_c2", K=4, D=3,
+                    n_lambda=4096, res=2048,
+                    desc="halo mixture 16,777,216 particles (64 Plummer halos + 20% uniform background, "
+                         "h = expected 32-NN distance, ~3 decades), Wendland C2, K=4, D=3, 4096-entry table, "
+                         "perspective 2048x2048, FP32 anchored"),
+    "halo1m": dict(n=1_000_000, a_range=(5e-3, 0.05), seed=SY.BASE_SEED + 1, kernel="wendland_c2", K=4, D=3,
+                   n_lambda=4096, res=1024,
+                   desc="halo mixture 1,000,000 particles, Wendland C2, K=4, D=3, perspective 1024x1024"),
+}
+
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+
+
+def flops_per_segment(K, D):
+    """Algorithmic FP32 operations per particle-ray segment (FMA = 2):
+    candidate test 20; knot generation 3 + 2(K+1) + 2D(K+1); per knot the
+    coefficient update D(D+1) + D; per piece compositing 10D + 40."""
+    return 23 + (K + 1) * (2 + 2 * D + D * (D + 1) + D + 10 * D + 40)
+
+
+def clocks_start(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=f, stderr=subprocess.DEVNULL), f
+    except Exception:
+        return None, None
+
+
+def clocks_stop(proc, f, path, device):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except Exception:
+        proc.kill()
+    f.close()
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        c = [x.strip() for x in line.split(",")]
+        if len(c) < 9 or c[0] != str(device):
+            continue
+        try:
+            sm.append(float(c[1]))
+            mx = max(mx, float(c[2]))
+        except ValueError:
+            continue
+        for n, v in zip(names, c[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    if not sm:
+        return None
+    return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(sm))
+
+
+def make_inputs(w, device):
+    P = SY.halo_mixture(w["n"], a_range=w["a_range"], seed=w["seed"], device=device)
+    tf = SY.tf_density(P["value"])
+    return P, tf
+
+
+def camera_for(w, rank, step=0):
+    return SY.orbit_camera(w["res"], w["res"], azimuth_deg=30.0 + 7.0 * rank, elevation_deg=20.0)
+
+
+def cpu_oracle_rate(P, w, tf, n_pix, seed, threads=None):
+    """Oracle (FP64, C + OpenMP) rays/s on a seeded sample of pixels of the frame."""
+    import oracle
+
+    if threads:
+        oracle.set_threads(threads)
+    lut = oracle.lut_build(w["kernel"], w["K"], w["D"], w["n_lambda"])
+    cam = camera_for(w, 0)
+    pix = SY.pixel_sample(cam["width"], cam["height"], n_pix, seed)
+    amp = SY.particles_to_amp(P["mass"], P["value"], P["density"])
+    part = dict(pos=P["pos"], h=P["h"], amp=amp)
+    t = time.perf_counter()
+    R = oracle.render(part, lut, cam, tf, pix)
+    dt = time.perf_counter() - t
+    return dict(rays_per_s=n_pix / dt, seconds=dt, segments=int(R["stats"][:, 0].sum()), cores=oracle.num_threads(),
+                lut=lut, part=part, cam=cam)
+
+
+def run_reference(args, w, rank, world):
+    """The oracle as it stands, on the host cores: each step a 16-pixel sample of the frame."""
+    if rank != 0:
+        return
+    import oracle
+
+    P, tf = make_inputs(w, None)
+    lut = oracle.lut_build(w["kernel"], w["K"], w["D"], w["n_lambda"])
+    amp = SY.particles_to_amp(P["mass"], P["value"], P["density"])
+    part = dict(pos=P["pos"], h=P["h"], amp=amp)
+    cam = camera_for(w, 0)
+    per_step = 16
+    for i in range(args.warmup):
+        oracle.render(part, lut, cam, tf, SY.pixel_sample(cam["width"], cam["height"], per_step, 1000 + i))
+    t = time.perf_counter()
+    segs = 0
+    for i in range(args.steps):
+        R = oracle.render(part, lut, cam, tf, SY.pixel_sample(cam["width"], cam["height"], per_step, 2000 + i))
+        segs += int(R["stats"][:, 0].sum())
+    dt = time.perf_counter() - t
+    mrays = per_step * args.steps / dt / 1e6
+    line = dict(metric="Mrays/s", value=mrays, unit="Mrays/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * dt / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=w["desc"], particles=w["n"], width=w["res"], height=w["res"],
+                            sample="%d seeded pixels per step" % per_step),
+                segments_per_s=segs / dt,
+                cpu_baseline=dict(value=mrays, unit="Mrays/s", cores=oracle.num_threads(), kind="oracle",
+                                  sample="%d seeded pixels per step, %d steps" % (per_step, args.steps)),
+                e2e=dict(value=mrays, unit="Mrays/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sphdvr", choices=["sphdvr", "reference"])
+    ap.add_argument("--workload", default="halo16m", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-pixels", type=int, default=48)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32_anchored")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, w, rank, world)
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2401_02896_b300 import sphdvr as S
+
+    P, tf = make_inputs(w, "cuda")
+    ctx = S.sphdvr_create(local)
+    th, pc, _err = S.sphdvr_lut_build(w["kernel"], w["K"], w["D"], w["n_lambda"])
+    lut = S.sphdvr_lut_create(ctx, w["kernel"], w["K"], w["D"], w["n_lambda"], th, pc)
+    dev = torch.device("cuda", local)
+    tens = {k: torch.from_numpy(np.ascontiguousarray(P[k])).to(dev) for k in ("pos", "h", "mass", "density", "value")}
+    ds = S.sphdvr_dataset_create(ctx, tens["pos"], tens["h"], tens["mass"], tens["density"], tens["value"])
+    del tens
+    cam = camera_for(w, rank)
+    opts = dict(precision=args.precision, ert_eps=1e-5)
+    W, H = cam["width"], cam["height"]
+    out = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+
+    def frame():
+        S.sphdvr_render(ctx, ds, lut, cam, tf, opts, out.data_ptr(), stream=stream, allow_overflow=True)
+
+    for _ in range(max(3, args.warmup)):
+        frame()
+    torch.cuda.synchronize()
+    st0 = S.sphdvr_frame_stats(ctx)
+    # ---- timed region: device time, CUDA events on the render stream
+    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                            "bench_clocks_r%d.csv" % rank)
+    proc, fh = clocks_start(clk_path)
+    time.sleep(0.5)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    render_ns, launches, segs, knots = [], 0, 0, 0
+    evs[0].record()
+    for i in range(args.steps):
+        frame()
+        evs[i + 1].record()
+        st = S.sphdvr_frame_stats(ctx)  # reads the render kernel's own CUDA events
+        render_ns.append(st["render_ns"])
+        launches += st["launches"]
+        segs += st["segments"]
+        knots += st["knots"]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    frame_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = sum(frame_ms)
+    clocks = clocks_stop(proc, fh, clk_path, local)
+    t_max = total_ms
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    rays = W * H * args.steps * world
+    value = rays / (t_max / 1e3) / 1e6
+
+    # ---- end to end: host output buffer, copies inside the call
+    host = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True).numpy()
+    S.sphdvr_render_host(ctx, ds, lut, cam, tf, opts, host, stream=stream, allow_overflow=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S.sphdvr_render_host(ctx, ds, lut, cam, tf, opts, host, stream=stream, allow_overflow=True)
+    e2e_s = time.perf_counter() - t0
+    e2e_val = W * H * args.steps / e2e_s / 1e6
+    if dist:
+        dist.barrier()
+
+    if rank == 0:
+        seg_per_frame = segs / args.steps
+        fps = flops_per_segment(w["K"], w["D"])
+        kern_s = np.mean(render_ns) / 1e9
+        achieved = seg_per_frame * fps / kern_s / 1e12
+        lat = np.array(frame_ms)
+        line = dict(
+            metric="Mrays/s", value=value, unit="Mrays/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+            data="synthetic",
+            config=dict(workload=w["desc"], particles=w["n"], width=W, height=H, kernel=w["kernel"], K=w["K"],
+                        D=w["D"], n_lambda=w["n_lambda"], precision=args.precision, ert_eps=1e-5,
+                        l2="inputs larger than L2 (resident particles %.0f MB)" % (S.sphdvr_dataset_info(ds)["bytes"] / 1e6),
+                        parallelism="replicas: one frame stream per GPU" if world > 1 else "1 GPU"),
+            segments_per_s=seg_per_frame * args.steps * world / (t_max / 1e3),
+            p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+            frame_stats=dict(segments=int(seg_per_frame), knots=int(knots / args.steps), pairs=st0["pairs"],
+                             max_table=st0["max_table"], overflow=st0["overflow"], ert_rays=st0["ert_rays"],
+                             render_kernel_ms=kern_s * 1e3),
+            roofline=dict(bound="alu", achieved=achieved, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+                          frac=achieved / FP32_PEAK_TFLOPS, traffic=None,
+                          note="FP32 peak = 148 SMs x 128 lanes x 2 x 2032 MHz; algorithmic %d FLOP/segment" % fps),
+            e2e=dict(value=e2e_val, unit="Mrays/s", h2d_bytes_per_step=int(tf["rgba"].nbytes),
+                     d2h_bytes_per_step=int(W * H * 16)),
+            gpu_launches=int(launches),
+            clocks=clocks,
+        )
+        if not args.no_cpu_baseline:
+            cb = cpu_oracle_rate(P, w, tf, args.cpu_pixels, seed=77)
+            line["cpu_baseline"] = dict(value=cb["rays_per_s"] / 1e6, unit="Mrays/s", cores=cb["cores"], kind="oracle",
+                                        sample="%d seeded pixels of the same frame (%.1f s, %d segments)" % (
+                                            args.cpu_pixels, cb["seconds"], cb["segments"]))
+        print(json.dumps(line), flush=True)
+    S.sphdvr_dataset_free(ds)
+    S.sphdvr_lut_free(lut)
+    S.sphdvr_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * sphdvr -- per-ray higher-order SPH field reconstruction and direct volume
+ * rendering on one NVIDIA B300 (sm_103a), after arXiv 2401.02896
+ * ("Particle-Wise Higher-Order SPH Field Approximation for DVR").
+ *
+ * C ABI.  Every call returns an sphdvr_status and never throws.  Objects are
+ * opaque and owned by the library until their _free/_destroy call.  Output
+ * buffers are owned by the caller.  Pointers documented as "device" must be
+ * CUDA device pointers on the context's device; "host" pointers are ordinary
+ * host memory (pinned memory makes the copies faster but is not required).
+ * Calls on one context are not thread-safe; use one context per host thread.
+ *
+ * Method (paper sections):
+ *   Sec. 1     SPH field f(x) = sum_i a_i / l_i^3 w(|x - chi_i| / l_i), with
+ *              a_i = mass_i * value_i / density_i and l_i the smoothing length;
+ *              kernel w with compact support [0, q).
+ *   Sec. 3.1   on a ray x(t) = o + t v a particle contributes
+ *              a_i / l_i^3 B_L((t - t_chi) / l_i), B_L(s) = w(sqrt(L^2 + s^2)),
+ *              L = dist(chi_i, ray) / l_i; B_L is replaced by its optimal even
+ *              piecewise polynomial S_L (K pieces, degree <= D) taken from a
+ *              look-up table over equidistant L (nearest entry).
+ *   Sec. 2     each S_L is stored as knots with localized difference
+ *              coefficients; summing all particles amounts to sorting their
+ *              knots and running the coefficient-update recurrence (eq.
+ *              Piecewise-Coefficients-Update).
+ *   Sec. 1/2   the resulting piecewise polynomial of the field is classified by
+ *              a transfer function and composited front to back.
+ */
+#ifndef SPHDVR_H
+#define SPHDVR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPHDVR_OK = 0,
+  SPHDVR_EINVAL = 1,    /* invalid argument (null pointer, bad size, NaN, h <= 0, ...) */
+  SPHDVR_ENOMEM = 2,    /* a device or host allocation failed */
+  SPHDVR_ECUDA = 3,     /* a CUDA runtime call failed; see sphdvr_last_error */
+  SPHDVR_ETIMEOUT = 4,  /* a bounded wait ran out (serving) */
+  SPHDVR_EBUSY = 5,     /* a request can never fit the server's memory budget */
+  SPHDVR_EOVERFLOW = 6, /* a fixed-capacity buffer was too small; results are incomplete */
+  SPHDVR_EDEVICE = 7,   /* no usable CUDA device, or not a compute capability 10.3 device */
+  SPHDVR_ENOTFOUND = 8  /* unknown ticket or object */
+} sphdvr_status;
+
+typedef enum {
+  SPHDVR_KERNEL_M4 = 0,          /* cubic B-spline, Sec. 1 eq. (cubic-kernel), q = 2 */
+  SPHDVR_KERNEL_WENDLAND_C2 = 1, /* (21/16pi)(1-r/2)^4(2r+1), q = 2 */
+  SPHDVR_KERNEL_WENDLAND_C4 = 2, /* (495/256pi)(1-r/2)^6(35r^2/12+3r+1), q = 2 */
+  SPHDVR_KERNEL_POLY6 = 3        /* (315/64pi)(1-r^2)^3, q = 1 (test kernel) */
+} sphdvr_kernel;
+
+typedef enum {
+  /* FP32 knots, difference coefficients and compositing; the recurrence of
+   * Sec. 2 runs inside windows of sorted knots and every `anchor_every`-th
+   * window re-starts from the exact sum of the active particles' own pieces. */
+  SPHDVR_PREC_FP32_ANCHORED = 0,
+  /* FP32 recurrence run front to back along the whole ray with no re-start:
+   * the paper's plain scheme, which exhibits the drift of Sec. 4.1. */
+  SPHDVR_PREC_FP32_NAIVE = 1,
+  /* as NAIVE, but the recurrence's running coefficients are FP64. */
+  SPHDVR_PREC_FP64_NAIVE = 2
+} sphdvr_precision;
+
+/* Viewing rays.  Basis: f = normalize(target - eye), r = normalize(f x up),
+ * u = r x f.  Pixel (px, py), row 0 on top, index p = py * width + px:
+ *   sx = 2 (px + 0.5) / width - 1,  sy = 1 - 2 (py + 0.5) / height.
+ * Perspective: o = eye, v = normalize(f + sx tan(fovy/2) width/height r
+ *                                       + sy tan(fovy/2) u).
+ * Orthographic: o = eye + sx half_w r + sy half_h u, v = f.
+ * The ray is x(t) = o + t v for t >= t_near. */
+typedef struct {
+  int projection; /* 0 perspective, 1 orthographic */
+  double eye[3];
+  double target[3];
+  double up[3];
+  double fovy_deg; /* perspective: full vertical field of view in degrees */
+  double half_w;   /* orthographic: half width of the view rectangle */
+  double half_h;   /* orthographic: half height */
+  double t_near;
+  int width;
+  int height;
+} sphdvr_camera;
+
+/* Piecewise-linear RGBA transfer function (classification, Sec. 1).
+ * Node i sits at value lo + i (hi - lo)/(n - 1); values outside [lo, hi]
+ * clamp to the end nodes.  RGB is the emitted colour in [0,1]; the
+ * extinction coefficient per unit length is sigma(f) = sigma_scale * A(f). */
+typedef struct {
+  int n;             /* 2 <= n <= 4096 */
+  double lo, hi;     /* lo < hi */
+  const float* rgba; /* host pointer, n*4 floats */
+  double sigma_scale;
+} sphdvr_tf;
+
+/* Compositing (emission-absorption, front to back, black transparent
+ * background), over [max(first knot, t_near), last knot] of the ray:
+ *   RGB = int c(F(t)) sigma(F(t)) exp(-int_t0^t sigma(F)) dt,
+ *   A   = 1 - exp(-int sigma(F) dt),
+ * written as premultiplied float RGBA, 4 floats per pixel, row-major. */
+typedef struct {
+  int precision;     /* sphdvr_precision */
+  int anchor_every;  /* FP32_ANCHORED: re-anchor every n-th window (>= 1) */
+  float ert_eps;     /* stop a ray once its transmittance drops below this; 0 = never */
+  int persistent;    /* 1: persistent CTAs pulling sub-tiles from a device work queue */
+  float window_h;    /* a window of knots spans at most window_h times the smallest
+                        smoothing length among the ray's pending particles (> 0);
+                        0 selects the default 1.0 */
+  int reserved[3];   /* must be 0 */
+} sphdvr_render_opts;
+
+typedef struct sphdvr_ctx sphdvr_ctx;
+typedef struct sphdvr_lut sphdvr_lut;
+typedef struct sphdvr_dataset sphdvr_dataset;
+
+/* Human-readable name of a status code (static storage). */
+const char* sphdvr_status_string(int status);
+
+/* Library build string (static storage). */
+const char* sphdvr_version(void);
+
+/* Create a context on CUDA device `device`.  EDEVICE if the device does not
+ * exist or is not compute capability 10.3. */
+sphdvr_status sphdvr_create(int device, sphdvr_ctx** out);
+sphdvr_status sphdvr_destroy(sphdvr_ctx* ctx);
+
+/* Copy the context's last error message (NUL-terminated, truncated to len). */
+sphdvr_status sphdvr_last_error(const sphdvr_ctx* ctx, char* buf, size_t len);
+
+/* ---------------------------------------------------------------------------
+ * Look-up table (Sec. 3.1-3.4): for L_j = j q / (n_lambda - 1),
+ * j = 0..n_lambda-1, the optimal approximation S_{L_j} of B_{L_j}.  m =
+ * ceil(K/2) positive knots theta_1 < ... < theta_m (plus a middle knot at 0
+ * when K is even); on [theta_{k-1}, theta_k] (theta_0 = 0) S(s) equals
+ *   P_k(s) = sum_d pieces[j][k-1][d] (s - theta_{k-1})^d,  S(-s) = S(s),
+ * and S = 0 for |s| >= theta_m.  The last entry (L = q) is the zero function
+ * with all knots at 0.
+ * ------------------------------------------------------------------------- */
+
+/* Compute the table on the host in FP64 (CPU threads).  K in [1,4], D in
+ * [1,6], n_lambda in [2, 65536].  Host outputs, caller-allocated:
+ *   theta [n_lambda * m], pieces [n_lambda * m * (D+1)], err [n_lambda]
+ *   (err = ||S_L - B_L||_2, may be NULL).  EINVAL on bad arguments. */
+sphdvr_status sphdvr_lut_build(int kernel, int K, int D, int n_lambda, double* theta, double* pieces, double* err);
+
+/* Upload a table (host arrays in the layout above, e.g. from
+ * sphdvr_lut_build) to the context's device as FP32 knots, difference
+ * coefficients (Sec. 2) and pieces.  The library keeps no reference to the
+ * host arrays. */
+sphdvr_status sphdvr_lut_create(sphdvr_ctx* ctx, int kernel, int K, int D, int n_lambda, const double* theta,
+                                const double* pieces, sphdvr_lut** out);
+sphdvr_status sphdvr_lut_free(sphdvr_lut* lut);
+
+/* ---------------------------------------------------------------------------
+ * Particle data sets, resident on the device.
+ * ------------------------------------------------------------------------- */
+
+/* Copy n particles into the library and build the acceleration structure:
+ * particles are grouped in h-levels (factor 2 in smoothing length), sorted in
+ * Morton order within a level and cut into chunks of at most 32 particles,
+ * each chunk with its tight bounding box and maximum smoothing length.
+ * Inputs (all FP32, n entries; pos is n*3 xyz): host pointers, or device
+ * pointers when inputs_on_device != 0.  mass, density may be NULL (then 1).
+ * value may be NULL (then 1).  EINVAL when n < 1, a pointer is NULL, or any
+ * h is not finite and > 0 or any position is not finite.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream); the call returns after the
+ * build has completed.  The caller keeps ownership of the inputs. */
+sphdvr_status sphdvr_dataset_create(sphdvr_ctx* ctx, int64_t n, const float* pos, const float* h, const float* mass,
+                                    const float* density, const float* value, int inputs_on_device, void* stream,
+                                    sphdvr_dataset** out);
+sphdvr_status sphdvr_dataset_free(sphdvr_dataset* ds);
+
+/* info[0] particles, [1] chunks, [2] h-levels, [3] device bytes held,
+ * [4..7] 0. */
+sphdvr_status sphdvr_dataset_info(const sphdvr_dataset* ds, int64_t info[8]);
+
+/* ---------------------------------------------------------------------------
+ * Rendering.
+ * ------------------------------------------------------------------------- */
+
+/* Render one frame into `rgba_out` (DEVICE pointer, width*height*4 floats,
+ * caller-owned), enqueued on `stream` (cudaStream_t, NULL = legacy default).
+ * The call returns when the frame has been enqueued and its work buffers
+ * are in place; it synchronises the stream only to size those buffers.
+ * `opts` may be NULL (defaults: FP32_ANCHORED, anchor_every 1, ert_eps 1e-5,
+ * non-persistent).  The kernel w (and its support q) is the one the table
+ * was built for.  Returns EOVERFLOW
+ * (image still written, possibly wrong) if a per-ray buffer overflowed. */
+sphdvr_status sphdvr_render(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+                            const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
+                            float* rgba_out, void* stream);
+
+/* As sphdvr_render, but `rgba_host` is a HOST pointer: the call renders into
+ * a library-owned device buffer, copies the image to the host and returns
+ * after the copy has completed (end-to-end form). */
+sphdvr_status sphdvr_render_host(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+                                 const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
+                                 float* rgba_host, void* stream);
+
+/* Statistics of the context's last completed frame (synchronises its
+ * stream): out[0] rays, [1] candidate particle-ray segments, [2] knots,
+ * [3] windows, [4] chunk-tile pairs, [5] particle tests, [6] max table
+ * occupancy, [7] flags (bit 0 table overflow, bit 1 window overflow, bit 3 a
+ * knot arrived behind the processed part of its ray), [8] rays stopped
+ * by early termination, [9] device time of the render kernel in ns (CUDA
+ * events on the render stream), [10] kernel launches of the frame,
+ * [11..15] 0. */
+sphdvr_status sphdvr_frame_stats(sphdvr_ctx* ctx, int64_t out[16]);
+
+/* Parity hook: render the listed pixels with the same kernels and return,
+ * per pixel r (all HOST pointers):
+ *   rgba[4r..4r+3]
+ *   counts[4r..4r+3]: candidates, knots, field pieces written, flags
+ *   cand_ids[r*cand_cap ...]: original indices of the candidate particles
+ *   field[(r*field_cap + i)*(D+3) ...]: FP64 rows (t_a, t_b, A_0..A_D), one per
+ *     field piece of positive length, front to back, A the field's localized
+ *     coefficients at t_a (Sec. 2) as the kernel computed them.
+ * cand_ids / field may be NULL.  EOVERFLOW if a capacity was too small (the
+ * first entries are still written). */
+sphdvr_status sphdvr_debug_rays(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+                                const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
+                                int n_pix, const int* pix, float* rgba, int64_t* counts, int64_t* cand_ids,
+                                int cand_cap, double* field, int field_cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPHDVR_H */

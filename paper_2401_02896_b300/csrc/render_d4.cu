@@ -1,0 +1,30 @@
+// Instantiations of the render kernel for polynomial degree D = 4.
+#include "render.cuh"
+
+namespace sphdvr {
+
+template <typename S, int NW, bool DBG>
+static sphdvr_status launch(sphdvr_ctx* ctx, const RenderParams& p, int grid, size_t smem, cudaStream_t st) {
+  auto kern = k_render<4, S, NW, DBG>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "render smem attribute");
+  if (!ctx->ev_ready) {
+    if (cudaEventCreate(&ctx->ev_render0) != cudaSuccess || cudaEventCreate(&ctx->ev_render1) != cudaSuccess)
+      return cuda_err(ctx, cudaGetLastError(), "render events");
+    ctx->ev_ready = true;
+  }
+  cudaEventRecord(ctx->ev_render0, st);
+  kern<<<grid, NW * 32, smem, st>>>(p);
+  ++ctx->launches;
+  cudaEventRecord(ctx->ev_render1, st);
+  return cuda_err(ctx, cudaGetLastError(), "k_render");
+}
+
+sphdvr_status launch_render_d4(sphdvr_ctx* ctx, bool f64, bool dbg, const RenderParams& p, int grid, size_t smem,
+                                cudaStream_t st) {
+  if (dbg) return f64 ? launch<double, 1, true>(ctx, p, grid, smem, st) : launch<float, 1, true>(ctx, p, grid, smem, st);
+  return f64 ? launch<double, kRenderWarps, false>(ctx, p, grid, smem, st)
+             : launch<float, kRenderWarps, false>(ctx, p, grid, smem, st);
+}
+
+}  // namespace sphdvr

@@ -1,0 +1,137 @@
+// Internal declarations of the sphdvr library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sphdvr.h"
+
+namespace sphdvr {
+
+// Host look-up-table builder (lutgen.cpp).  Returns 0 on success.
+int build_lut_host(int kernel, int K, int D, int n_lambda, double* theta, double* pieces, double* err);
+
+constexpr int kChunk = 32;       // particles per chunk of the acceleration structure
+constexpr int kTile = 16;        // binning tile edge in pixels
+constexpr int kMaxTf = 4096;     // transfer-function nodes
+
+// Device copy of a look-up table.  For entry j:
+//   theta[j]             = (theta_1, theta_2)            (theta_2 unused when m = 1)
+//   jump[j*3*D + s*D + d-1]: localized difference coefficient of order d at
+//                          knot slot s (0: middle knot at 0, s>=1: knot +theta_s),
+//                          normalised units (Sec. 2); knot -theta_s mirrors
+//                          slot s with sign (-1)^(d+1).
+//   piece[j*2*(D+1) + (k-1)*(D+1) + d]: P_k local coefficients at theta_{k-1}.
+struct DevLut {
+  int kernel = 0, K = 0, D = 0, n_lambda = 0, m = 0;
+  float q = 2.f;
+  float reach = 2.f;  // largest theta_m of the table: knots lie within t_chi +- reach h
+  float2* theta = nullptr;
+  float* jump = nullptr;
+  float* piece = nullptr;
+};
+
+// Per-frame camera, precomputed on the host in FP64.
+struct DevCamera {
+  int proj;  // 0 perspective, 1 orthographic
+  int width, height;
+  double eye[3], f[3], r[3], u[3];
+  double tan_half, aspect, half_w, half_h, t_near;
+};
+
+struct DevTf {
+  int n;
+  float lo, hi, inv_dv;
+  const float4* rgba;  // (r, g, b, sigma_scale * A)
+};
+
+// Grow-only device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace sphdvr
+
+struct sphdvr_ctx {
+  int device = 0;
+  std::string last_error;
+  // frame work buffers (grow-only)
+  sphdvr::DevBuf chunk_rect, chunk_front, chunk_ntile, chunk_off, pair_key, pair_val, pair_key2, pair_val2,
+      tile_range, scan_tmp, sort_tmp, stats, tf, img, dbg_pix, dbg_rgba, dbg_counts, dbg_cands, dbg_field;
+  std::vector<int64_t> last_stats = std::vector<int64_t>(16, 0);
+  cudaStream_t last_stream = nullptr;
+  bool stats_pending = false;
+  int64_t last_pairs = 0;
+  int64_t launches = 0;        // kernel launches since the context was created
+  int64_t frame_launch0 = 0;   // value of `launches` when the last frame started
+  cudaEvent_t ev_render0 = nullptr, ev_render1 = nullptr;  // around the last render kernel
+  bool ev_ready = false;
+};
+
+struct sphdvr_lut {
+  sphdvr_ctx* ctx = nullptr;
+  sphdvr::DevLut d;
+};
+
+struct sphdvr_dataset {
+  sphdvr_ctx* ctx = nullptr;
+  int64_t n = 0;
+  int n_chunks = 0;
+  int n_levels = 0;
+  float4* pos = nullptr;    // (x, y, z, h) in chunk order
+  float* amp = nullptr;     // mass * value / density
+  int* orig = nullptr;      // original particle index
+  int2* chunk = nullptr;    // (start, count)
+  float4* chunk_lo = nullptr;  // tight bbox min, w = max h
+  float4* chunk_hi = nullptr;  // tight bbox max
+  size_t bytes = 0;
+};
+
+namespace sphdvr {
+
+// helpers implemented in api.cpp
+sphdvr_status set_err(sphdvr_ctx* ctx, sphdvr_status st, const std::string& msg);
+sphdvr_status cuda_err(sphdvr_ctx* ctx, cudaError_t e, const char* where);
+sphdvr_status ensure(sphdvr_ctx* ctx, DevBuf& b, size_t bytes);
+sphdvr_status dev_alloc(sphdvr_ctx* ctx, void** p, size_t bytes);
+
+// sort.cu
+// Exclusive prefix sum of n uint32 values (in may equal out).  If total is
+// non-null the grand total is written there (device pointer).
+sphdvr_status scan_exclusive_u32(sphdvr_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total,
+                                 cudaStream_t st);
+// Stable LSD radix sort of (key, value) pairs on key bits [0, nbits).
+// Result ends in keys/vals; keys2/vals2 are scratch of the same size.
+sphdvr_status radix_sort_u64(sphdvr_ctx* ctx, uint64_t* keys, uint32_t* vals, uint64_t* keys2, uint32_t* vals2,
+                             int64_t n, int nbits, cudaStream_t st);
+
+// dataset.cu
+sphdvr_status build_dataset(sphdvr_ctx* ctx, sphdvr_dataset* ds, const float* pos, const float* h,
+                            const float* mass, const float* density, const float* value, cudaStream_t st);
+
+// frame.cu
+struct RenderArgs {
+  const sphdvr_dataset* ds;
+  const DevLut* lut;
+  DevCamera cam;
+  int tf_n;
+  float tf_lo, tf_hi;
+  const sphdvr_render_opts* opts;
+  float* out;           // device image (normal mode)
+  // debug mode (parity hook): listed pixels, device outputs
+  int n_dbg = 0;
+  const int* dbg_pix = nullptr;
+  float* dbg_rgba = nullptr;
+  long long* dbg_counts = nullptr;
+  long long* dbg_cands = nullptr;
+  int cand_cap = 0;
+  double* dbg_field = nullptr;
+  int field_cap = 0;
+};
+sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st);
+
+}  // namespace sphdvr

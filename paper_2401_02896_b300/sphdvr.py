@@ -1,0 +1,292 @@
+"""Python binding of libsphdvr, the B300-native per-ray higher-order SPH DVR
+library (arXiv 2401.02896).
+
+Argument marshalling only: every function calls the C-ABI entry point of the
+same name in ``lib/libsphdvr.so`` (see ``include/sphdvr.h``).  Device memory
+and streams may come from PyTorch (``tensor.data_ptr()``,
+``torch.cuda.current_stream().cuda_stream``); nothing is computed here.
+The library must have been built (``python -m paper_2401_02896_b300._build``);
+importing the binding without it raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))  # the package directory
+LIB_PATH = os.path.join(_HERE, "lib", "libsphdvr.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, EOVERFLOW, EDEVICE, ENOTFOUND = range(9)
+KERNELS = {"m4": 0, "wendland_c2": 1, "wendland_c4": 2, "poly6": 3}
+PRECISIONS = {"fp32_anchored": 0, "fp32_naive": 1, "fp64_naive": 2}
+
+
+class SphdvrError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("sphdvr status %d (%s): %s" % (status, status_string(status), message))
+        self.status = status
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [
+        ("projection", ctypes.c_int),
+        ("eye", ctypes.c_double * 3),
+        ("target", ctypes.c_double * 3),
+        ("up", ctypes.c_double * 3),
+        ("fovy_deg", ctypes.c_double),
+        ("half_w", ctypes.c_double),
+        ("half_h", ctypes.c_double),
+        ("t_near", ctypes.c_double),
+        ("width", ctypes.c_int),
+        ("height", ctypes.c_int),
+    ]
+
+
+class Tf(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("lo", ctypes.c_double),
+        ("hi", ctypes.c_double),
+        ("rgba", ctypes.c_void_p),
+        ("sigma_scale", ctypes.c_double),
+    ]
+
+
+class RenderOpts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("anchor_every", ctypes.c_int),
+        ("ert_eps", ctypes.c_float),
+        ("persistent", ctypes.c_int),
+        ("window_h", ctypes.c_float),
+        ("reserved", ctypes.c_int * 3),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libsphdvr.so is not built (expected at %s); run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "sphdvr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "sphdvr_version": (ctypes.c_char_p, []),
+        "sphdvr_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp)]),
+        "sphdvr_destroy": (ctypes.c_int, [vp]),
+        "sphdvr_last_error": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+        "sphdvr_lut_build": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, vp, vp]),
+        "sphdvr_lut_create": (ctypes.c_int, [vp] + [ctypes.c_int] * 4 + [vp, vp, ctypes.POINTER(vp)]),
+        "sphdvr_lut_free": (ctypes.c_int, [vp]),
+        "sphdvr_dataset_create": (ctypes.c_int, [vp, ctypes.c_int64, vp, vp, vp, vp, vp, ctypes.c_int, vp,
+                                                 ctypes.POINTER(vp)]),
+        "sphdvr_dataset_free": (ctypes.c_int, [vp]),
+        "sphdvr_dataset_info": (ctypes.c_int, [vp, i64p]),
+        "sphdvr_render": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
+                                         ctypes.POINTER(RenderOpts), vp, vp]),
+        "sphdvr_render_host": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
+                                              ctypes.POINTER(RenderOpts), vp, vp]),
+        "sphdvr_frame_stats": (ctypes.c_int, [vp, i64p]),
+        "sphdvr_debug_rays": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
+                                             ctypes.POINTER(RenderOpts), ctypes.c_int, vp, vp, vp, vp, ctypes.c_int,
+                                             vp, ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def status_string(s):
+    return _lib.sphdvr_status_string(int(s)).decode()
+
+
+def version():
+    return _lib.sphdvr_version().decode()
+
+
+def last_error(ctx):
+    buf = ctypes.create_string_buffer(1024)
+    _lib.sphdvr_last_error(ctx, buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(st, ctx=None, allow=()):
+    if st != OK and st not in allow:
+        raise SphdvrError(st, last_error(ctx) if ctx else "")
+    return st
+
+
+def _p(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _kid(k):
+    return KERNELS[k] if isinstance(k, str) else int(k)
+
+
+# ---------------------------------------------------------------------------
+# plain-data conversions (camera / TF / options dicts as produced by
+# paper_2401_02896_b300.synthetic)
+# ---------------------------------------------------------------------------
+
+def camera_struct(cam):
+    c = Camera()
+    c.projection = 0 if cam["projection"] == "perspective" else 1
+    for i in range(3):
+        c.eye[i] = cam["eye"][i]
+        c.target[i] = cam["target"][i]
+        c.up[i] = cam["up"][i]
+    c.fovy_deg = cam.get("fovy_deg", 0.0)
+    c.half_w = cam.get("half_w", 0.0)
+    c.half_h = cam.get("half_h", 0.0)
+    c.t_near = cam.get("t_near", 0.0)
+    c.width = cam["width"]
+    c.height = cam["height"]
+    return c
+
+
+def tf_struct(tf):
+    rgba = np.ascontiguousarray(tf["rgba"], dtype=np.float32)
+    t = Tf()
+    t.n = rgba.shape[0]
+    t.lo = tf["lo"]
+    t.hi = tf["hi"]
+    t.rgba = rgba.ctypes.data
+    t.sigma_scale = tf.get("sigma_scale", 1.0)
+    t._keep = rgba  # keep the host array alive with the struct
+    return t
+
+
+def opts_struct(opts=None):
+    o = RenderOpts()
+    opts = opts or {}
+    o.precision = PRECISIONS[opts.get("precision", "fp32_anchored")] if isinstance(
+        opts.get("precision", "fp32_anchored"), str) else int(opts["precision"])
+    o.anchor_every = int(opts.get("anchor_every", 1))
+    o.ert_eps = float(opts.get("ert_eps", 1e-5))
+    o.persistent = int(opts.get("persistent", 0))
+    o.window_h = float(opts.get("window_h", 0.0))
+    return o
+
+
+# ---------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------
+
+def sphdvr_create(device=0):
+    h = ctypes.c_void_p()
+    st = _lib.sphdvr_create(int(device), ctypes.byref(h))
+    _check(st)
+    return h
+
+
+def sphdvr_destroy(ctx):
+    return _check(_lib.sphdvr_destroy(ctx))
+
+
+def sphdvr_lut_build(kernel, K, D, n_lambda):
+    """FP64 table of optimal approximations (host): returns (theta [n,m], pieces [n,m,D+1], err [n])."""
+    m = (K + 1) // 2
+    th = np.zeros((n_lambda, m))
+    pc = np.zeros((n_lambda, m, D + 1))
+    err = np.zeros(n_lambda)
+    _check(_lib.sphdvr_lut_build(_kid(kernel), K, D, n_lambda, _p(th), _p(pc), _p(err)))
+    return th, pc, err
+
+
+def sphdvr_lut_create(ctx, kernel, K, D, n_lambda, theta, pieces):
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    pc = np.ascontiguousarray(pieces, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(_lib.sphdvr_lut_create(ctx, _kid(kernel), K, D, n_lambda, _p(th), _p(pc), ctypes.byref(h)), ctx)
+    return h
+
+
+def sphdvr_lut_free(lut):
+    return _check(_lib.sphdvr_lut_free(lut))
+
+
+def sphdvr_dataset_create(ctx, pos, h, mass=None, density=None, value=None, stream=None):
+    """pos (n,3), h, mass, density, value (n,) float32: numpy arrays (host) or CUDA torch tensors (device)."""
+    on_dev = hasattr(pos, "data_ptr")
+    if on_dev:
+        ptrs = [None if a is None else ctypes.c_void_p(a.data_ptr()) for a in (pos, h, mass, density, value)]
+        keep = None
+        n = pos.shape[0]
+    else:
+        keep = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in (pos, h, mass, density, value)]
+        ptrs = [_p(a) for a in keep]
+        n = keep[0].shape[0]
+    out = ctypes.c_void_p()
+    st = _lib.sphdvr_dataset_create(ctx, int(n), ptrs[0], ptrs[1], ptrs[2], ptrs[3], ptrs[4], 1 if on_dev else 0,
+                                    ctypes.c_void_p(stream) if stream else None, ctypes.byref(out))
+    del keep
+    _check(st, ctx)
+    return out
+
+
+def sphdvr_dataset_free(ds):
+    return _check(_lib.sphdvr_dataset_free(ds))
+
+
+def sphdvr_dataset_info(ds):
+    info = (ctypes.c_int64 * 8)()
+    _check(_lib.sphdvr_dataset_info(ds, info))
+    return dict(particles=info[0], chunks=info[1], levels=info[2], bytes=info[3])
+
+
+def sphdvr_render(ctx, ds, lut, camera, tf, opts, out_ptr, stream=None, allow_overflow=False):
+    """Render into a device buffer (int pointer, e.g. torch tensor .data_ptr())."""
+    c, t, o = camera_struct(camera), tf_struct(tf), opts_struct(opts)
+    st = _lib.sphdvr_render(ctx, ds, lut, ctypes.byref(c), ctypes.byref(t), ctypes.byref(o),
+                            ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream) if stream else None)
+    return _check(st, ctx, (EOVERFLOW,) if allow_overflow else ())
+
+
+def sphdvr_render_host(ctx, ds, lut, camera, tf, opts, out=None, stream=None, allow_overflow=False):
+    """Render into host memory (numpy float32 (H, W, 4)); copies happen inside the call."""
+    c, t, o = camera_struct(camera), tf_struct(tf), opts_struct(opts)
+    if out is None:
+        out = np.empty((camera["height"], camera["width"], 4), np.float32)
+    st = _lib.sphdvr_render_host(ctx, ds, lut, ctypes.byref(c), ctypes.byref(t), ctypes.byref(o), _p(out),
+                                 ctypes.c_void_p(stream) if stream else None)
+    _check(st, ctx, (EOVERFLOW,) if allow_overflow else ())
+    return out
+
+
+def sphdvr_frame_stats(ctx):
+    s = (ctypes.c_int64 * 16)()
+    _check(_lib.sphdvr_frame_stats(ctx, s), ctx)
+    keys = ["rays", "segments", "knots", "windows", "pairs", "tests", "max_table", "overflow", "ert_rays",
+            "render_ns", "launches"]
+    return {k: int(s[i]) for i, k in enumerate(keys)}
+
+
+def sphdvr_debug_rays(ctx, ds, lut, camera, tf, opts, pixels, cand_cap=0, field_cap=0, D=None):
+    """Parity hook: per listed pixel, rgba, counts, candidate ids and field pieces (FP64 rows)."""
+    pix = np.ascontiguousarray(pixels, dtype=np.int32)
+    n = pix.shape[0]
+    rgba = np.zeros((n, 4), np.float32)
+    counts = np.zeros((n, 4), np.int64)
+    cands = np.full((n, cand_cap), -1, np.int64) if cand_cap else None
+    if field_cap and D is None:
+        raise ValueError("debug_rays needs D to size the field buffer")
+    field = np.zeros((n, field_cap, D + 3)) if field_cap else None
+    c, t, o = camera_struct(camera), tf_struct(tf), opts_struct(opts)
+    st = _lib.sphdvr_debug_rays(ctx, ds, lut, ctypes.byref(c), ctypes.byref(t), ctypes.byref(o), n, _p(pix),
+                                _p(rgba), _p(counts), _p(cands), int(cand_cap), _p(field), int(field_cap))
+    _check(st, ctx, (EOVERFLOW,))
+    return dict(rgba=rgba, counts=counts, cand_ids=cands, field=field, overflow=st == EOVERFLOW)
+
+
+def header_functions():
+    """Names of the functions ``include/sphdvr.h`` declares (used by the ABI tests)."""
+    import re
+
+    root = os.path.dirname(_HERE)
+    txt = open(os.path.join(root, "include", "sphdvr.h")).read()
+    return sorted(set(re.findall(r"^\S.*?\b(sphdvr_[a-z_0-9]+)\(", txt, re.M)))

@@ -54,7 +54,7 @@ def _plummer_radius(r, a, n, trunc=10.0):
 
 
 def halo_mixture(n=1_000_000, n_halos=64, bg_frac=0.2, a_range=(0.005, 0.05), seed=BASE_SEED + 1,
-                 neighbours=32, chunk=1 << 20):
+                 neighbours=32, chunk=1 << 20, device=None):
     """Plummer halos + uniform background in the unit cube.
 
     Halo centres U[0.1,0.9]^3, scale a log-uniform in ``a_range``, halo weights
@@ -85,8 +85,21 @@ def halo_mixture(n=1_000_000, n_halos=64, bg_frac=0.2, a_range=(0.005, 0.05), se
     pos32 = pos.astype(np.float32)
     # analytic number density of the mixture at each particle
     xmax = 10.0 ** 3 / (10.0 ** 2 + 1.0) ** 1.5
-    nd = np.full(n, float(n_bg), np.float64)  # background: n_bg per unit volume
+    if device is not None:
+        nd = _halo_density_torch(pos32, cen, a, counts, xmax, float(n_bg), device)
+    else:
+        nd = _halo_density_np(pos32, cen, a, counts, xmax, float(n_bg), chunk)
+    h = (neighbours / (4.0 / 3.0 * math.pi * nd)) ** (1.0 / 3.0)
+    mass = np.full(n, 1.0 / n, np.float32)
+    dens = (nd / n).astype(np.float32)
+    return dict(pos=pos32, h=h.astype(np.float32), mass=mass, density=dens, value=dens.copy())
+
+
+def _halo_density_np(pos32, cen, a, counts, xmax, n_bg, chunk):
+    n = pos32.shape[0]
+    nd = np.full(n, n_bg, np.float64)  # background: n_bg per unit volume
     p64 = pos32.astype(np.float64)
+    n_halos = len(a)
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
         acc = nd[s:e]
@@ -98,10 +111,28 @@ def halo_mixture(n=1_000_000, n_halos=64, bg_frac=0.2, a_range=(0.005, 0.05), se
             rho = 3.0 / (4.0 * math.pi * a[k] ** 3) * (1.0 + r2 / a[k] ** 2) ** -2.5
             acc += np.where(inside, counts[k] / xmax * rho, 0.0)
         nd[s:e] = acc
-    h = (neighbours / (4.0 / 3.0 * math.pi * nd)) ** (1.0 / 3.0)
-    mass = np.full(n, 1.0 / n, np.float32)
-    dens = (nd / n).astype(np.float32)
-    return dict(pos=pos32, h=h.astype(np.float32), mass=mass, density=dens, value=dens.copy())
+    return nd
+
+
+def _halo_density_torch(pos32, cen, a, counts, xmax, n_bg, device, chunk=1 << 22):
+    """Same analytic density as _halo_density_np, evaluated in float64 with torch."""
+    import torch
+
+    n = pos32.shape[0]
+    out = np.empty(n, np.float64)
+    cen_t = torch.tensor(cen, dtype=torch.float64, device=device)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        p = torch.from_numpy(pos32[s:e]).to(device=device, dtype=torch.float64)
+        acc = torch.full((e - s,), n_bg, dtype=torch.float64, device=device)
+        for k in range(len(a)):
+            if counts[k] == 0:
+                continue
+            r2 = ((p - cen_t[k]) ** 2).sum(dim=1)
+            rho = 3.0 / (4.0 * math.pi * a[k] ** 3) * (1.0 + r2 / a[k] ** 2) ** -2.5
+            acc += torch.where(r2 < (10.0 * a[k]) ** 2, counts[k] / xmax * rho, torch.zeros_like(rho))
+        out[s:e] = acc.cpu().numpy()
+    return out
 
 
 def dam_break_slab(n=64_000_000, seed=BASE_SEED + 4, neighbours=32, chunk=1 << 22):

@@ -1,0 +1,105 @@
+"""CPU-side checks of the C-ABI library (no GPU needed).
+
+* the in-tree libsphdvr.so loads and exports every function include/sphdvr.h declares;
+* argument validation paths return the documented status codes;
+* the library's own look-up-table builder (host code) agrees with the oracle's
+  table and reproduces the paper's printed E_{K,D} values (Sec. 5.2 figure).
+"""
+import ctypes
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import quad, simpson
+
+import oracle
+from _helpers import oracle_lut
+
+S = pytest.importorskip("paper_2401_02896_b300.sphdvr", reason="libsphdvr.so not built")
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_library_exports_every_declared_function():
+    names = S.header_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(S.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings():
+    for s in range(9):
+        assert S.status_string(s) and S.status_string(s) != "unknown status"
+    assert S.status_string(99) == "unknown status"
+    assert "sm_103a" in S.version()
+
+
+def test_create_without_cuda_device_reports_edevice():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(S.SphdvrError) as e:
+        S.sphdvr_create(0)
+    assert e.value.status == S.EDEVICE
+
+
+@pytest.mark.parametrize("args", [("m4", 0, 3, 64), ("m4", 5, 3, 64), ("m4", 4, 0, 64), ("m4", 4, 7, 64),
+                                  ("m4", 4, 3, 1), (9, 4, 3, 64)])
+def test_lut_build_rejects_bad_arguments(args):
+    with pytest.raises((S.SphdvrError, KeyError)) as e:
+        S.sphdvr_lut_build(*args)
+    if isinstance(e.value, S.SphdvrError):
+        assert e.value.status == S.EINVAL
+
+
+def test_null_handles_are_rejected():
+    lib = S._lib
+    assert lib.sphdvr_destroy(None) == S.EINVAL
+    assert lib.sphdvr_lut_free(None) == S.EINVAL
+    assert lib.sphdvr_dataset_free(None) == S.EINVAL
+    assert lib.sphdvr_create(0, None) == S.EINVAL
+    info = (ctypes.c_int64 * 8)()
+    assert lib.sphdvr_dataset_info(None, info) == S.EINVAL
+
+
+@pytest.mark.parametrize("kernel,K,D", [("m4", 4, 3), ("wendland_c2", 4, 3), ("wendland_c4", 4, 4), ("m4", 2, 2),
+                                        ("m4", 3, 3)])
+def test_library_table_matches_oracle_table(kernel, K, D):
+    n = 129
+    th, pc, err = S.sphdvr_lut_build(kernel, K, D, n)
+    L = oracle.lut_build(kernel, K, D, n)
+    e_o = L["err"][:-1]
+    e_p = err[:-1]
+    nb = L["normB"][:-1]
+    # never noticeably worse than the oracle's optimum, per entry
+    assert np.all(e_p <= e_o * (1 + 5e-3) + 1e-13 * nb)
+    # the error the library reports is the error of the approximation it returns
+    for j in [3, 40, 77, 120]:
+        e_chk, _ = oracle.fixed_knots(kernel, K, D, L["lam"][j], th[j])
+        assert abs(e_chk - err[j]) <= 1e-7 * nb[j] + 1e-12 * e_chk
+    # last entry: zero function
+    assert np.all(th[-1] == 0) and np.all(pc[-1] == 0)
+
+
+@pytest.mark.parametrize("key", ["2,1", "4,3", "3,2", "4,4"])
+def test_library_table_reproduces_printed_errors(key):
+    table = json.load(open(os.path.join(HERE, "golden", "paper_error_table.json")))
+    K, D = map(int, key.split(","))
+    th, pc, err = S.sphdvr_lut_build("m4", K, D, 257)
+    kap = math.sqrt(4 * math.pi * quad(lambda r: (r * oracle.kernel_w("m4", r)) ** 2, 0, 2, points=[1.0],
+                                       epsabs=1e-16)[0])
+    lam = np.arange(257) * 2.0 / 256
+    E = math.sqrt(2 * math.pi * simpson(lam * err ** 2, x=lam)) / kap
+    assert abs(E / table["E"][key] - 1) < 1.5e-4
+
+
+def test_library_table_poly6_exact():
+    th, pc, err = S.sphdvr_lut_build("poly6", 1, 6, 33)
+    lam = np.arange(33) / 32.0
+    for j in range(32):
+        nb = math.sqrt(oracle.ray_norm2("poly6", lam[j]))
+        assert err[j] <= 1e-10 * nb
+        assert abs(th[j][0] - math.sqrt(1 - lam[j] ** 2)) < 1e-5
