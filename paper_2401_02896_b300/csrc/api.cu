@@ -100,28 +100,25 @@ sphdvr_status check_camera(sphdvr_ctx* ctx, const sphdvr_camera* c, DevCamera* o
   return SPHDVR_OK;
 }
 
-sphdvr_status upload_tf(sphdvr_ctx* ctx, const sphdvr_tf* tf, cudaStream_t st) {
+// Validate the transfer function and pack it as (r, g, b, sigma_scale * A).
+sphdvr_status pack_tf(sphdvr_ctx* ctx, const sphdvr_tf* tf, std::vector<float4>& out) {
   if (!tf || !tf->rgba) return set_err(ctx, SPHDVR_EINVAL, "transfer function is NULL");
   if (tf->n < 2 || tf->n > kMaxTf) return set_err(ctx, SPHDVR_EINVAL, "transfer function: n out of [2, 4096]");
   if (!(tf->lo < tf->hi) || !std::isfinite(tf->lo) || !std::isfinite(tf->hi))
     return set_err(ctx, SPHDVR_EINVAL, "transfer function: need finite lo < hi");
   if (!(tf->sigma_scale >= 0) || !std::isfinite(tf->sigma_scale))
     return set_err(ctx, SPHDVR_EINVAL, "transfer function: sigma_scale must be finite and >= 0");
-  std::vector<float> h(4 * (size_t)tf->n);
+  out.resize(tf->n);
   for (int i = 0; i < tf->n; ++i) {
+    float v[4];
     for (int k = 0; k < 4; ++k) {
-      float v = tf->rgba[4 * i + k];
-      if (!std::isfinite(v) || v < 0) return set_err(ctx, SPHDVR_EINVAL, "transfer function: entries must be finite and >= 0");
-      h[4 * i + k] = v;
+      v[k] = tf->rgba[4 * i + k];
+      if (!std::isfinite(v[k]) || v[k] < 0)
+        return set_err(ctx, SPHDVR_EINVAL, "transfer function: entries must be finite and >= 0");
     }
-    h[4 * i + 3] = (float)(h[4 * i + 3] * tf->sigma_scale);
+    out[i] = make_float4(v[0], v[1], v[2], (float)(v[3] * tf->sigma_scale));
   }
-  sphdvr_status s = ensure(ctx, ctx->tf, h.size() * sizeof(float));
-  if (s != SPHDVR_OK) return s;
-  // the source is a stack vector: copy synchronously with respect to the host
-  cudaError_t e = cudaMemcpyAsync(ctx->tf.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return cuda_err(ctx, e, "upload transfer function");
+  return SPHDVR_OK;
 }
 
 sphdvr_status check_opts(sphdvr_ctx* ctx, const sphdvr_render_opts* o) {
@@ -379,10 +376,12 @@ static sphdvr_status do_render(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const 
   a.ds = ds;
   a.lut = &lut->d;
   if ((s = check_camera(ctx, cam, &a.cam)) != SPHDVR_OK) return s;
-  if ((s = upload_tf(ctx, tf, st)) != SPHDVR_OK) return s;
+  std::vector<float4> tfh;
+  if ((s = pack_tf(ctx, tf, tfh)) != SPHDVR_OK) return s;
   a.tf_n = tf->n;
   a.tf_lo = (float)tf->lo;
   a.tf_hi = (float)tf->hi;
+  a.tf_host = tfh.data();
   a.opts = opts;
   a.out = rgba_out;
   ctx->frame_launch0 = ctx->launches;

@@ -196,7 +196,8 @@ sphdvr_status build_dataset(sphdvr_ctx* ctx, sphdvr_dataset* ds, const float* po
   if ((e = cudaGetLastError()) != cudaSuccess) { cleanup(); return cuda_err(ctx, e, "k_keys"); }
   int lbits = 0;
   while ((1 << lbits) < nlev) ++lbits;
-  s = radix_sort_u64(ctx, keys, vals, keys2, vals2, n, 48 + lbits, st);
+  if ((s = ensure(ctx, ctx->sort_tmp, sort_tmp_words(n) * sizeof(uint32_t))) != SPHDVR_OK) { cleanup(); return s; }
+  s = radix_sort_u64(ctx, keys, vals, keys2, vals2, n, 48 + lbits, (uint32_t*)ctx->sort_tmp.p, st);
   if (s != SPHDVR_OK) { cleanup(); return s; }
   unsigned hcount[64];
   cudaMemcpyAsync(hcount, lcount, sizeof(hcount), cudaMemcpyDeviceToHost, st);

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <string>
 
 #include "render.cuh"
 
@@ -160,7 +161,56 @@ static sphdvr_status dispatch_render(sphdvr_ctx* ctx, int D, bool f64, bool dbg,
 
 
 
+namespace {
+
+// grow the context's pair buffers once the pair count is known
+sphdvr_status ctx_pair_sizer(sphdvr_ctx* ctx, FrameWork& w, size_t pairs, void*) {
+  const size_t np = std::max<size_t>(pairs, 1);
+  sphdvr_status s;
+  if ((s = ensure(ctx, ctx->pair_key, np * 8)) != SPHDVR_OK || (s = ensure(ctx, ctx->pair_val, np * 4)) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->pair_key2, np * 8)) != SPHDVR_OK || (s = ensure(ctx, ctx->pair_val2, np * 4)) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->sort_tmp, sort_tmp_words((int64_t)np) * sizeof(uint32_t))) != SPHDVR_OK)
+    return s;
+  w.pair_key = (uint64_t*)ctx->pair_key.p;
+  w.pair_val = (uint32_t*)ctx->pair_val.p;
+  w.pair_key2 = (uint64_t*)ctx->pair_key2.p;
+  w.pair_val2 = (uint32_t*)ctx->pair_val2.p;
+  w.pair_cap = np;
+  w.tmp = (uint32_t*)ctx->sort_tmp.p;
+  w.tmp_words = ctx->sort_tmp.bytes / sizeof(uint32_t);
+  return SPHDVR_OK;
+}
+
+}  // namespace
+
 sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st) {
+  const int tiles = ((a.cam.width + kTile - 1) / kTile) * ((a.cam.height + kTile - 1) / kTile);
+  const int nc = a.ds->n_chunks;
+  sphdvr_status s;
+  if ((s = ensure(ctx, ctx->chunk_rect, (size_t)nc * sizeof(float4))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->chunk_front, (size_t)nc * sizeof(unsigned))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->chunk_ntile, (size_t)nc * sizeof(uint32_t) + 16)) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->chunk_off, (size_t)nc * sizeof(uint32_t) + 16)) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->tile_range, (size_t)tiles * sizeof(int2))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->stats, 16 * sizeof(unsigned long long))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->scan_tmp, scan_tmp_words(nc) * sizeof(uint32_t))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->tf, (size_t)a.tf_n * sizeof(float4))) != SPHDVR_OK)
+    return s;
+  FrameWork w;
+  w.chunk_rect = (float4*)ctx->chunk_rect.p;
+  w.chunk_front = (unsigned*)ctx->chunk_front.p;
+  w.chunk_ntile = (uint32_t*)ctx->chunk_ntile.p;
+  w.chunk_off = (uint32_t*)ctx->chunk_off.p;
+  w.tile_range = (int2*)ctx->tile_range.p;
+  w.stats = (unsigned long long*)ctx->stats.p;
+  w.tf = (float4*)ctx->tf.p;
+  w.tmp = (uint32_t*)ctx->scan_tmp.p;
+  w.tmp_words = ctx->scan_tmp.bytes / sizeof(uint32_t);
+  return render_frame_ws(ctx, a, w, ctx_pair_sizer, nullptr, st);
+}
+
+sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w, PairSizer sizer, void* user,
+                              cudaStream_t st) {
   const sphdvr_dataset* ds = a.ds;
   const DevLut* L = a.lut;
   const DevCamera& cam = a.cam;
@@ -168,44 +218,39 @@ sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st
   const int n_tiles = tiles_x * tiles_y;
   const int nc = ds->n_chunks;
   sphdvr_status s;
-  if ((s = ensure(ctx, ctx->chunk_rect, (size_t)nc * sizeof(float4))) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->chunk_front, (size_t)nc * sizeof(unsigned))) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->chunk_ntile, (size_t)nc * sizeof(uint32_t) + 16)) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->chunk_off, (size_t)nc * sizeof(uint32_t) + 16)) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->tile_range, (size_t)n_tiles * sizeof(int2))) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->stats, 16 * sizeof(unsigned long long))) != SPHDVR_OK)
-    return s;
-  float4* rect = (float4*)ctx->chunk_rect.p;
-  unsigned* front = (unsigned*)ctx->chunk_front.p;
-  uint32_t* ntile = (uint32_t*)ctx->chunk_ntile.p;
-  uint32_t* off = (uint32_t*)ctx->chunk_off.p;
-  int2* trange = (int2*)ctx->tile_range.p;
-  unsigned long long* stats = (unsigned long long*)ctx->stats.p;
   cudaError_t e;
+  if ((e = cudaMemcpyAsync(w.tf, a.tf_host, (size_t)a.tf_n * sizeof(float4), cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return cuda_err(ctx, e, "transfer function upload");
+  float4* rect = w.chunk_rect;
+  unsigned* front = w.chunk_front;
+  uint32_t* ntile = w.chunk_ntile;
+  uint32_t* off = w.chunk_off;
+  int2* trange = w.tile_range;
+  unsigned long long* stats = w.stats;
   k_chunk_project<<<(nc + 255) / 256, 256, 0, st>>>(nc, ds->chunk_lo, ds->chunk_hi, cam, L->q, L->reach, tiles_x,
                                                     tiles_y, rect, front, ntile);
   ++ctx->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(ctx, e, "k_chunk_project");
   uint32_t* d_total = off + nc;
-  if ((s = scan_exclusive_u32(ctx, ntile, off, nc, d_total, st)) != SPHDVR_OK) return s;
+  if (w.tmp_words < scan_tmp_words(nc)) return set_err(ctx, SPHDVR_EOVERFLOW, "frame scratch too small for the scan");
+  if ((s = scan_exclusive_u32(ctx, ntile, off, nc, d_total, w.tmp, st)) != SPHDVR_OK) return s;
   uint32_t total = 0;
   if ((e = cudaMemcpyAsync(&total, d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return cuda_err(ctx, e, "pair count");
   ctx->last_pairs = total;
-  const size_t np = std::max<size_t>(total, 1);
-  if ((s = ensure(ctx, ctx->pair_key, np * 8)) != SPHDVR_OK || (s = ensure(ctx, ctx->pair_val, np * 4)) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->pair_key2, np * 8)) != SPHDVR_OK || (s = ensure(ctx, ctx->pair_val2, np * 4)) != SPHDVR_OK)
-    return s;
-  uint64_t* keys = (uint64_t*)ctx->pair_key.p;
-  uint32_t* vals = (uint32_t*)ctx->pair_val.p;
+  if (sizer && (s = sizer(ctx, w, total, user)) != SPHDVR_OK) return s;
+  if (w.pair_cap < total || w.tmp_words < sort_tmp_words(total))
+    return set_err(ctx, SPHDVR_EOVERFLOW, "frame scratch too small for " + std::to_string(total) + " chunk-tile pairs");
+  uint64_t* keys = w.pair_key;
+  uint32_t* vals = w.pair_val;
   k_emit_pairs<<<(nc + 255) / 256, 256, 0, st>>>(nc, rect, front, ntile, off, tiles_x, tiles_y, keys, vals);
   ++ctx->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(ctx, e, "k_emit_pairs");
   int tbits = 0;
   while ((1 << tbits) < n_tiles) ++tbits;
-  if ((s = radix_sort_u64(ctx, keys, vals, (uint64_t*)ctx->pair_key2.p, (uint32_t*)ctx->pair_val2.p, total,
-                          32 + tbits, st)) != SPHDVR_OK)
+  if ((s = radix_sort_u64(ctx, keys, vals, w.pair_key2, w.pair_val2, total, 32 + tbits, w.tmp, st)) != SPHDVR_OK)
     return s;
   if ((e = cudaMemsetAsync(trange, 0, (size_t)n_tiles * sizeof(int2), st)) != cudaSuccess)
     return cuda_err(ctx, e, "tile range memset");
@@ -242,7 +287,7 @@ sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st
   p.tf_lo = a.tf_lo;
   p.tf_dv = (a.tf_hi - a.tf_lo) / (a.tf_n - 1);
   p.tf_inv_dv = (float)((a.tf_n - 1) / ((double)a.tf_hi - (double)a.tf_lo));
-  p.tf = (const float4*)ctx->tf.p;
+  p.tf = w.tf;
   const sphdvr_render_opts* o = a.opts;
   int prec = o ? o->precision : SPHDVR_PREC_FP32_ANCHORED;
   p.anchor_every = (prec == SPHDVR_PREC_FP32_ANCHORED) ? std::max(1, o ? o->anchor_every : 1) : 0;

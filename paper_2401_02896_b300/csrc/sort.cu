@@ -151,8 +151,20 @@ __global__ void k_radix_scatter(const uint64_t* keys, const uint32_t* vals, uint
 
 }  // namespace
 
+size_t scan_tmp_words(int64_t n) {
+  size_t need = 16;
+  for (int64_t t = (n + kScanTile - 1) / kScanTile; t > 1; t = (t + kScanTile - 1) / kScanTile) need += (size_t)t + 1;
+  return need;
+}
+
+size_t sort_tmp_words(int64_t n) {
+  int64_t tiles = (n + kSortTile - 1) / kSortTile;
+  size_t hist_n = (size_t)tiles * 256;
+  return hist_n + scan_tmp_words((int64_t)hist_n);
+}
+
 sphdvr_status scan_exclusive_u32(sphdvr_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total,
-                                 cudaStream_t st) {
+                                 uint32_t* tmp, cudaStream_t st) {
   if (n <= 0) {
     if (total) {
       cudaError_t e = cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
@@ -169,22 +181,15 @@ sphdvr_status scan_exclusive_u32(sphdvr_ctx* ctx, const uint32_t* in, uint32_t* 
     ++ctx->launches;
     return cuda_err(ctx, cudaGetLastError(), "k_scan_single");
   }
-  int64_t tiles = (n + kScanTile - 1) / kScanTile;
-  // tile sums live in the context's scan buffer, recursion uses deeper slices
-  size_t need = 0;
-  for (int64_t t = tiles; t > 1; t = (t + kScanTile - 1) / kScanTile) need += (size_t)t + 1;
-  sphdvr_status s = ensure(ctx, ctx->scan_tmp, (need + 16) * sizeof(uint32_t));
-  if (s != SPHDVR_OK) return s;
-  // recursion: level buffers placed consecutively
+  // reduce-then-scan: tile sums of each level placed consecutively in tmp
   std::vector<std::pair<uint32_t*, int64_t>> levels;
   uint32_t* cur_out = out;
   const uint32_t* cur_in = in;
   int64_t cur_n = n;
-  uint32_t* pool = (uint32_t*)ctx->scan_tmp.p;
   size_t used = 0;
   while (cur_n > kScanTile) {
     int64_t t = (cur_n + kScanTile - 1) / kScanTile;
-    uint32_t* sums = pool + used;
+    uint32_t* sums = tmp + used;
     used += (size_t)t + 1;
     k_scan_tiles<<<(unsigned)t, kScanThreads, 0, st>>>(cur_in, cur_out, cur_n, sums);
     ++ctx->launches;
@@ -199,12 +204,10 @@ sphdvr_status scan_exclusive_u32(sphdvr_ctx* ctx, const uint32_t* in, uint32_t* 
   ++ctx->launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(ctx, e, "k_scan_single");
-  // propagate down
+  // propagate the scanned sums of level i (stored where level i+1 was scanned in place) down
   for (int i = (int)levels.size() - 1; i >= 0; --i) {
     int64_t t = (levels[i].second + kScanTile - 1) / kScanTile;
-    const uint32_t* offs = (i + 1 < (int)levels.size()) ? levels[i + 1].first : cur_out;
-    // the sums of level i were scanned in place at levels[i+1].first (or cur_out for the last)
-    offs = (i == (int)levels.size() - 1) ? cur_out : levels[i + 1].first;
+    const uint32_t* offs = (i == (int)levels.size() - 1) ? cur_out : levels[i + 1].first;
     k_scan_add<<<(unsigned)t, kScanThreads, 0, st>>>(levels[i].first, levels[i].second, offs);
     ++ctx->launches;
     e = cudaGetLastError();
@@ -214,13 +217,12 @@ sphdvr_status scan_exclusive_u32(sphdvr_ctx* ctx, const uint32_t* in, uint32_t* 
 }
 
 sphdvr_status radix_sort_u64(sphdvr_ctx* ctx, uint64_t* keys, uint32_t* vals, uint64_t* keys2, uint32_t* vals2,
-                             int64_t n, int nbits, cudaStream_t st) {
+                             int64_t n, int nbits, uint32_t* tmp, cudaStream_t st) {
   if (n <= 1) return SPHDVR_OK;
   int64_t tiles = (n + kSortTile - 1) / kSortTile;
   size_t hist_n = (size_t)tiles * 256;
-  sphdvr_status s = ensure(ctx, ctx->sort_tmp, hist_n * sizeof(uint32_t));
-  if (s != SPHDVR_OK) return s;
-  uint32_t* hist = (uint32_t*)ctx->sort_tmp.p;
+  uint32_t* hist = tmp;
+  uint32_t* scan_tmp = tmp + hist_n;
   int passes = (nbits + 7) / 8;
   uint64_t *ka = keys, *kb = keys2;
   uint32_t *va = vals, *vb = vals2;
@@ -230,7 +232,7 @@ sphdvr_status radix_sort_u64(sphdvr_ctx* ctx, uint64_t* keys, uint32_t* vals, ui
     ++ctx->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(ctx, e, "k_radix_hist");
-    s = scan_exclusive_u32(ctx, hist, hist, (int64_t)hist_n, nullptr, st);
+    sphdvr_status s = scan_exclusive_u32(ctx, hist, hist, (int64_t)hist_n, nullptr, scan_tmp, st);
     if (s != SPHDVR_OK) return s;
     k_radix_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, hist, (int)tiles);
     ++ctx->launches;

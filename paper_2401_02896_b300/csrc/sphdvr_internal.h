@@ -101,13 +101,17 @@ sphdvr_status dev_alloc(sphdvr_ctx* ctx, void** p, size_t bytes);
 
 // sort.cu
 // Exclusive prefix sum of n uint32 values (in may equal out).  If total is
-// non-null the grand total is written there (device pointer).
+// non-null the grand total is written there (device pointer).  tmp: device
+// scratch of scan_tmp_words(n) words.
+size_t scan_tmp_words(int64_t n);
 sphdvr_status scan_exclusive_u32(sphdvr_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total,
-                                 cudaStream_t st);
+                                 uint32_t* tmp, cudaStream_t st);
 // Stable LSD radix sort of (key, value) pairs on key bits [0, nbits).
-// Result ends in keys/vals; keys2/vals2 are scratch of the same size.
+// Result ends in keys/vals; keys2/vals2 are scratch of the same size; tmp:
+// device scratch of sort_tmp_words(n) words.
+size_t sort_tmp_words(int64_t n);
 sphdvr_status radix_sort_u64(sphdvr_ctx* ctx, uint64_t* keys, uint32_t* vals, uint64_t* keys2, uint32_t* vals2,
-                             int64_t n, int nbits, cudaStream_t st);
+                             int64_t n, int nbits, uint32_t* tmp, cudaStream_t st);
 
 // dataset.cu
 sphdvr_status build_dataset(sphdvr_ctx* ctx, sphdvr_dataset* ds, const float* pos, const float* h,
@@ -120,6 +124,7 @@ struct RenderArgs {
   DevCamera cam;
   int tf_n;
   float tf_lo, tf_hi;
+  const float4* tf_host;  // validated table (r, g, b, sigma_scale * A), host memory
   const sphdvr_render_opts* opts;
   float* out;           // device image (normal mode)
   // debug mode (parity hook): listed pixels, device outputs
@@ -132,6 +137,30 @@ struct RenderArgs {
   double* dbg_field = nullptr;
   int field_cap = 0;
 };
+// Device scratch of one frame: every buffer the binning and the render
+// kernel write besides the caller's image.
+struct FrameWork {
+  float4* chunk_rect = nullptr;       // [chunks]
+  unsigned* chunk_front = nullptr;    // [chunks]
+  uint32_t* chunk_ntile = nullptr;    // [chunks]
+  uint32_t* chunk_off = nullptr;      // [chunks + 4] (total at [chunks])
+  uint64_t* pair_key = nullptr;       // [pair_cap] x 2 buffers
+  uint64_t* pair_key2 = nullptr;
+  uint32_t* pair_val = nullptr;
+  uint32_t* pair_val2 = nullptr;
+  size_t pair_cap = 0;
+  int2* tile_range = nullptr;         // [tiles]
+  uint32_t* tmp = nullptr;            // scan / sort scratch
+  size_t tmp_words = 0;
+  unsigned long long* stats = nullptr;  // [16]
+  float4* tf = nullptr;               // transfer function (r, g, b, sigma)
+};
+// Render with scratch from the context's grow-only buffers.
 sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st);
+// Render with caller-provided scratch; `sizer` (if non-null) is called with
+// the pair count once it is known and must make room (return non-OK to stop).
+typedef sphdvr_status (*PairSizer)(sphdvr_ctx* ctx, FrameWork& w, size_t pairs, void* user);
+sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w, PairSizer sizer, void* user,
+                              cudaStream_t st);
 
 }  // namespace sphdvr

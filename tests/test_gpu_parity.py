@@ -127,3 +127,169 @@ def test_clustered_1m_sampled_pixels(S, ctx):
     finally:
         S.sphdvr_dataset_free(ds)
         S.sphdvr_lut_free(lt)
+
+
+@pytest.mark.parametrize("K,D", [(4, 1), (4, 2), (4, 4), (3, 3), (2, 3), (1, 4)])
+def test_small_uniform_degree_and_pieces_sweep(S, ctx, K, D):
+    """Other (K, D): odd K has no middle knot, K = 1 a single even piece."""
+    P = SY.uniform_cube()
+    lut = oracle_lut("m4", K, D, 1025)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.ortho_camera_z(24, 24)
+    tf = SY.tf_bumps()
+    try:
+        _check_rays(S, ctx, ds, lt, P, lut, cam, tf, np.arange(24 * 24))
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
+
+
+def test_perspective_inside_volume_with_t_near(S, ctx):
+    """Eye inside the particle cloud, t_near = 0.25: clipping of the first pieces and knots behind the eye."""
+    P = SY.uniform_cube()
+    lut = oracle_lut("m4", 4, 3, 4096)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.orbit_camera(32, 24, azimuth_deg=15, elevation_deg=10, distance=0.35, fovy_deg=60, t_near=0.25)
+    tf = SY.tf_bumps()
+    try:
+        _check_rays(S, ctx, ds, lt, P, lut, cam, tf, np.arange(32 * 24))
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
+
+
+def test_wendland_c4_degree4(S, ctx):
+    P = SY.uniform_cube(2000, h=0.06, seed=SY.BASE_SEED + 9)
+    lut = oracle_lut("wendland_c4", 4, 4, 2049)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.orbit_camera(32, 32, azimuth_deg=50, elevation_deg=35, distance=1.6)
+    tf = SY.tf_bumps(lo=0.0, hi=2.0)
+    try:
+        _check_rays(S, ctx, ds, lt, P, lut, cam, tf, np.arange(32 * 32))
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
+
+
+def test_precision_modes_order(S, ctx):
+    """The plain recurrence (Sec. 4.1) drifts; re-anchored FP32 windows do not."""
+    P = SY.uniform_cube()
+    lut = oracle_lut("m4", 4, 3, 4096)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.ortho_camera_z(32, 32)
+    tf = SY.tf_bumps()
+    pix = np.arange(32 * 32)
+    R = oracle.render(_orc_particles(P), lut, cam, tf, pix, field_cap=4096)
+    worst = {}
+    try:
+        for prec in ("fp32_anchored", "fp32_naive", "fp64_naive"):
+            g = S.sphdvr_debug_rays(ctx, ds, lt, cam, tf, dict(precision=prec, ert_eps=0.0), pix, field_cap=4096,
+                                    D=3)
+            e = [field_rel_l2(g["field"][r, :g["counts"][r, 2]], R["field"][r, :R["stats"][r, 5]], 3)
+                 for r in range(len(pix)) if R["stats"][r, 0]]
+            worst[prec] = max(e)
+        assert worst["fp32_anchored"] <= FIELD_REL_L2
+        # both plain recurrences drift (knot positions are FP32 offsets either way)
+        assert worst["fp32_naive"] > 10 * worst["fp32_anchored"]
+        assert worst["fp64_naive"] > 10 * worst["fp32_anchored"]
+        print(worst)
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
+
+
+def test_early_ray_termination_bound(S, ctx):
+    """Opaque transfer function: terminated rays differ from the complete oracle by at most ert_eps."""
+    import torch
+
+    P = SY.uniform_cube()
+    lut = oracle_lut("m4", 4, 3, 4096)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.ortho_camera_z(32, 32)
+    tf = SY.tf_bumps(sigma_scale=40.0)
+    eps = 1e-4
+    try:
+        out = torch.zeros((32, 32, 4), dtype=torch.float32, device="cuda")
+        S.sphdvr_render(ctx, ds, lt, cam, tf, dict(ert_eps=eps), out.data_ptr())
+        torch.cuda.synchronize()
+        st = S.sphdvr_frame_stats(ctx)
+        assert st["ert_rays"] > 0
+        R = oracle.render(_orc_particles(P), lut, cam, tf, np.arange(32 * 32))
+        err = np.abs(out.cpu().numpy().reshape(-1, 4) - R["rgba"]).max()
+        assert err <= eps + PIXEL_ABS, err
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
+
+
+def test_library_tables_end_to_end(S, ctx):
+    """Each side with its own table (library builder vs oracle builder): pixels within 2e-4."""
+    import torch
+
+    P = SY.uniform_cube()
+    th, pc, _ = S.sphdvr_lut_build("m4", 4, 3, 2049)
+    lt = S.sphdvr_lut_create(ctx, "m4", 4, 3, 2049, th, pc)
+    ds = S.sphdvr_dataset_create(ctx, P["pos"], P["h"], P["mass"], P["density"], P["value"])
+    cam = SY.ortho_camera_z(32, 32)
+    tf = SY.tf_bumps()
+    try:
+        out = torch.zeros((32, 32, 4), dtype=torch.float32, device="cuda")
+        S.sphdvr_render(ctx, ds, lt, cam, tf, dict(ert_eps=0.0), out.data_ptr())
+        torch.cuda.synchronize()
+        R = oracle.render(_orc_particles(P), oracle_lut("m4", 4, 3, 2049), cam, tf, np.arange(32 * 32))
+        assert np.abs(out.cpu().numpy().reshape(-1, 4) - R["rgba"]).max() <= PIXEL_ABS
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
+
+
+def test_no_particles_in_view_is_transparent(S, ctx):
+    import torch
+
+    P = SY.uniform_cube()
+    lut = oracle_lut("m4", 4, 3, 4096)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.ortho_camera_z(16, 16, lo=(3.0, 3.0), hi=(4.0, 4.0))
+    try:
+        out = torch.full((16, 16, 4), 7.0, dtype=torch.float32, device="cuda")
+        S.sphdvr_render(ctx, ds, lt, cam, SY.tf_bumps(), None, out.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.all(out == 0)
+        assert S.sphdvr_frame_stats(ctx)["segments"] == 0
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
+
+
+def test_invalid_inputs_are_rejected(S, ctx):
+    P = SY.uniform_cube(64)
+    bad = dict(P)
+    bad["h"] = P["h"].copy()
+    bad["h"][5] = 0.0
+    with pytest.raises(S.SphdvrError) as e:
+        S.sphdvr_dataset_create(ctx, bad["pos"], bad["h"], bad["mass"], bad["density"], bad["value"])
+    assert e.value.status == S.EINVAL
+    bad["h"][5] = np.nan
+    with pytest.raises(S.SphdvrError):
+        S.sphdvr_dataset_create(ctx, bad["pos"], bad["h"], bad["mass"], bad["density"], bad["value"])
+    lut = oracle_lut("m4", 4, 3, 257)
+    ds, lt = _mk(S, ctx, P, lut)
+    try:
+        cam = SY.ortho_camera_z(8, 8)
+        tf = SY.tf_bumps()
+        import torch
+
+        out = torch.zeros((8, 8, 4), dtype=torch.float32, device="cuda")
+        for c in [dict(cam, width=0), dict(cam, target=cam["eye"]), dict(cam, half_w=0.0)]:
+            with pytest.raises(S.SphdvrError) as e:
+                S.sphdvr_render(ctx, ds, lt, c, tf, None, out.data_ptr())
+            assert e.value.status == S.EINVAL
+        for t in [dict(tf, lo=2.0, hi=1.0), dict(tf, rgba=tf["rgba"][:1])]:
+            with pytest.raises(S.SphdvrError) as e:
+                S.sphdvr_render(ctx, ds, lt, cam, t, None, out.data_ptr())
+            assert e.value.status == S.EINVAL
+        with pytest.raises(S.SphdvrError):
+            S.sphdvr_render(ctx, ds, lt, cam, tf, dict(precision=7), out.data_ptr())
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
