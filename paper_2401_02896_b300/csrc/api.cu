@@ -188,7 +188,8 @@ sphdvr_status sphdvr_destroy(sphdvr_ctx* c) {
   cudaSetDevice(c->device);
   DevBuf* bufs[] = {&c->chunk_rect, &c->chunk_front, &c->chunk_ntile, &c->chunk_off, &c->pair_key, &c->pair_val,
                     &c->pair_key2, &c->pair_val2, &c->tile_range, &c->scan_tmp, &c->sort_tmp, &c->stats,
-                    &c->tf, &c->img, &c->dbg_pix, &c->dbg_rgba, &c->dbg_counts, &c->dbg_cands, &c->dbg_field};
+                    &c->tf, &c->img, &c->dbg_pix, &c->dbg_rgba, &c->dbg_counts, &c->dbg_cands, &c->dbg_field,
+                    &c->table, &c->work};
   for (DevBuf* b : bufs) free_buf(*b);
   if (c->ev_ready) {
     cudaEventDestroy(c->ev_render0);

@@ -137,7 +137,8 @@ __global__ void k_tile_ranges(int64_t n, const uint64_t* keys, int2* range) {
 // per-degree launchers (render_d<D>.cu)
 #define SPHDVR_DECL(D)                                                                                         \
   sphdvr_status launch_render_d##D(sphdvr_ctx* ctx, bool f64, bool dbg, const RenderParams& p, int grid,    \
-                                   size_t smem, cudaStream_t st);
+                                   size_t smem, cudaStream_t st);                                            \
+  int render_occupancy_d##D(bool f64, bool dbg, size_t smem);
 SPHDVR_DECL(1)
 SPHDVR_DECL(2)
 SPHDVR_DECL(3)
@@ -158,6 +159,42 @@ static sphdvr_status dispatch_render(sphdvr_ctx* ctx, int D, bool f64, bool dbg,
   }
   return set_err(ctx, SPHDVR_EINVAL, "D out of range");
 }
+
+static int render_occupancy(int D, bool f64, bool dbg, size_t smem) {
+  switch (D) {
+    case 1: return render_occupancy_d1(f64, dbg, smem);
+    case 2: return render_occupancy_d2(f64, dbg, smem);
+    case 3: return render_occupancy_d3(f64, dbg, smem);
+    case 4: return render_occupancy_d4(f64, dbg, smem);
+    case 5: return render_occupancy_d5(f64, dbg, smem);
+    case 6: return render_occupancy_d6(f64, dbg, smem);
+  }
+  return 0;
+}
+
+int render_grid(sphdvr_ctx* ctx, const RenderArgs& a) {
+  const bool dbg = a.n_dbg > 0;
+  const int prec = a.opts ? a.opts->precision : SPHDVR_PREC_FP32_ANCHORED;
+  const bool f64 = prec == SPHDVR_PREC_FP64_NAIVE;
+  const size_t smem = render_smem_bytes(a.tf_n, dbg ? 1 : kRenderWarps);
+  int nb = render_occupancy(a.lut->D, f64, dbg, smem);
+  if (ctx->num_sms <= 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, ctx->device);
+    ctx->num_sms = n > 0 ? n : 1;
+  }
+  int items;
+  if (dbg) {
+    items = a.n_dbg;
+  } else {
+    const int tiles = ((a.cam.width + kTile - 1) / kTile) * ((a.cam.height + kTile - 1) / kTile);
+    items = tiles * (kTile / 2) * (kTile / 2);
+  }
+  int grid = std::max(1, nb) * ctx->num_sms;
+  return std::max(1, std::min(grid, items));
+}
+
+size_t render_table_floats(int grid, bool dbg) { return (size_t)grid * (dbg ? 1 : kRenderWarps) * kTableWords; }
 
 
 
@@ -196,7 +233,14 @@ sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st
       (s = ensure(ctx, ctx->scan_tmp, scan_tmp_words(nc) * sizeof(uint32_t))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->tf, (size_t)a.tf_n * sizeof(float4))) != SPHDVR_OK)
     return s;
+  const int grid = render_grid(ctx, a);
+  if ((s = ensure(ctx, ctx->table, render_table_floats(grid, a.n_dbg > 0) * sizeof(float))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->work, 4 * sizeof(unsigned))) != SPHDVR_OK)
+    return s;
   FrameWork w;
+  w.table = (float*)ctx->table.p;
+  w.table_ctas = grid;
+  w.work = (unsigned*)ctx->work.p;
   w.chunk_rect = (float4*)ctx->chunk_rect.p;
   w.chunk_front = (unsigned*)ctx->chunk_front.p;
   w.chunk_ntile = (uint32_t*)ctx->chunk_ntile.p;
@@ -259,7 +303,8 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
     ++ctx->launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(ctx, e, "k_tile_ranges");
   }
-  if ((e = cudaMemsetAsync(stats, 0, 16 * sizeof(unsigned long long), st)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(stats, 0, 16 * sizeof(unsigned long long), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(w.work, 0, sizeof(unsigned), st)) != cudaSuccess)
     return cuda_err(ctx, e, "stats memset");
 
   RenderParams p;
@@ -269,6 +314,8 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
   p.amp = ds->amp;
   p.orig = ds->orig;
   p.chunk = ds->chunk;
+  p.chunk_lo = ds->chunk_lo;
+  p.chunk_hi = ds->chunk_hi;
   p.chunk_rect = rect;
   p.pair_key = keys;
   p.pair_val = vals;
@@ -305,14 +352,14 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
   p.dbg_field = a.dbg_field;
   p.field_cap = a.field_cap;
   const bool f64 = prec == SPHDVR_PREC_FP64_NAIVE;
-  if (a.n_dbg > 0) {
-    size_t smem = render_smem_bytes(a.tf_n, 1);
-    return dispatch_render(ctx, L->D, f64, true, p, a.n_dbg, smem, st);
-  }
-  constexpr int SW = 2, SH = 2;
-  const int grid = n_tiles * (kTile / SW) * (kTile / SH);
-  size_t smem = render_smem_bytes(a.tf_n, kRenderWarps);
-  return dispatch_render(ctx, L->D, f64, false, p, grid, smem, st);
+  const bool dbg = a.n_dbg > 0;
+  const int grid = std::min(render_grid(ctx, a), w.table_ctas);
+  p.scratch = w.table;
+  p.work = w.work;
+  p.n_items = n_tiles * (kTile / 2) * (kTile / 2);
+  p.dynamic = (o && o->persistent) ? 1 : 0;
+  size_t smem = render_smem_bytes(a.tf_n, dbg ? 1 : kRenderWarps);
+  return dispatch_render(ctx, L->D, f64, dbg, p, grid, smem, st);
 }
 
 }  // namespace sphdvr

@@ -20,11 +20,25 @@ static sphdvr_status launch(sphdvr_ctx* ctx, const RenderParams& p, int grid, si
   return cuda_err(ctx, cudaGetLastError(), "k_render");
 }
 
+template <typename S, int NW, bool DBG>
+static int occupancy(size_t smem) {
+  auto kern = k_render<1, S, NW, DBG>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NW * 32, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
 sphdvr_status launch_render_d1(sphdvr_ctx* ctx, bool f64, bool dbg, const RenderParams& p, int grid, size_t smem,
                                 cudaStream_t st) {
   if (dbg) return f64 ? launch<double, 1, true>(ctx, p, grid, smem, st) : launch<float, 1, true>(ctx, p, grid, smem, st);
   return f64 ? launch<double, kRenderWarps, false>(ctx, p, grid, smem, st)
              : launch<float, kRenderWarps, false>(ctx, p, grid, smem, st);
+}
+
+int render_occupancy_d1(bool f64, bool dbg, size_t smem) {
+  if (dbg) return f64 ? occupancy<double, 1, true>(smem) : occupancy<float, 1, true>(smem);
+  return f64 ? occupancy<double, kRenderWarps, false>(smem) : occupancy<float, kRenderWarps, false>(smem);
 }
 
 }  // namespace sphdvr

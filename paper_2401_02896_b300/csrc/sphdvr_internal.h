@@ -61,7 +61,9 @@ struct sphdvr_ctx {
   std::string last_error;
   // frame work buffers (grow-only)
   sphdvr::DevBuf chunk_rect, chunk_front, chunk_ntile, chunk_off, pair_key, pair_val, pair_key2, pair_val2,
-      tile_range, scan_tmp, sort_tmp, stats, tf, img, dbg_pix, dbg_rgba, dbg_counts, dbg_cands, dbg_field;
+      tile_range, scan_tmp, sort_tmp, stats, tf, img, dbg_pix, dbg_rgba, dbg_counts, dbg_cands, dbg_field, table,
+      work;
+  int num_sms = 0;
   std::vector<int64_t> last_stats = std::vector<int64_t>(16, 0);
   cudaStream_t last_stream = nullptr;
   bool stats_pending = false;
@@ -154,7 +156,13 @@ struct FrameWork {
   size_t tmp_words = 0;
   unsigned long long* stats = nullptr;  // [16]
   float4* tf = nullptr;               // transfer function (r, g, b, sigma)
+  float* table = nullptr;             // per-ray candidate tables of the persistent render grid
+  int table_ctas = 0;                 // CTAs the table scratch covers
+  unsigned* work = nullptr;           // work-queue counter
 };
+// Persistent render grid for this frame and the table scratch it needs (floats).
+int render_grid(sphdvr_ctx* ctx, const RenderArgs& a);
+size_t render_table_floats(int grid, bool dbg);
 // Render with scratch from the context's grow-only buffers.
 sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st);
 // Render with caller-provided scratch; `sizer` (if non-null) is called with
