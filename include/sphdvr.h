@@ -209,7 +209,8 @@ sphdvr_status sphdvr_render_host(sphdvr_ctx* ctx, const sphdvr_dataset* ds, cons
  * knot arrived behind the processed part of its ray), [8] rays stopped
  * by early termination, [9] device time of the render kernel in ns (CUDA
  * events on the render stream), [10] kernel launches of the frame,
- * [11..15] 0. */
+ * [11] largest number of particles active at one point of a ray, [12] windows
+ * shortened by the window_h limit, [13..15] 0. */
 sphdvr_status sphdvr_frame_stats(sphdvr_ctx* ctx, int64_t out[16]);
 
 /* Parity hook: render the listed pixels with the same kernels and return,

@@ -506,6 +506,26 @@ static ld optimise_knots(const lam_ctx* c, ld* xbest) {
     ld cv = local_opt(c, cx, sv[s], 0.5L / NG);
     if (cv < gbest) { gbest = cv; memcpy(gx, cx, sizeof(gx)); }
   }
+  /* The outer knot often has two nearby basins, on either side of the end of
+   * supp B_L (theta_m = T), closer together than the grid spacing: start a
+   * local search on both sides of that ridge as well. */
+  const ld ridge[4] = {0.97L, 0.995L, 1.01L, 1.04L};
+  for (int s = 0; s < ns && s < 4; s++) {
+    for (int rr = 0; rr < 4; rr++) {
+      ld cx[ORC_MAXM];
+      long r = starts[s];
+      for (int k = 0; k < m; k++) {
+        int ik = (int)(r % NG);
+        r /= NG;
+        cx[k] = k ? (ik + 0.5L) / NG : 1.5L * (ik + 0.5L) / NG;
+      }
+      cx[0] = ridge[rr];
+      ld cv = objective(c, cx);
+      if (!isfinite((double)cv)) continue;
+      cv = local_opt(c, cx, cv, 0.01L);
+      if (cv < gbest) { gbest = cv; memcpy(gx, cx, sizeof(gx)); }
+    }
+  }
   memcpy(xbest, gx, sizeof(gx));
   return gbest;
 }

@@ -438,6 +438,8 @@ sphdvr_status sphdvr_frame_stats(sphdvr_ctx* ctx, int64_t out[16]) {
     cudaGetLastError();
   }
   out[10] = ctx->launches - ctx->frame_launch0;
+  out[11] = ctx->last_stats[11];
+  out[12] = ctx->last_stats[12];
   return SPHDVR_OK;
 }
 

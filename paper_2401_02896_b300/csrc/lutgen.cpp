@@ -397,6 +397,19 @@ ld search(const Problem& P, ld* best) {
   }
   std::sort(starts.begin(), starts.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
   if (starts.size() > 8) starts.resize(8);
+  // the outer knot may have two basins straddling the end of the support
+  // (theta_m = T) closer than the scan resolves: seed both sides explicitly
+  {
+    const size_t nbest = std::min<size_t>(starts.size(), 3);
+    for (size_t s = 0; s < nbest; ++s)
+      for (ld f : {0.975L, 1.0L, 1.02L, 1.05L}) {
+        std::vector<ld> x = starts[s].second;
+        ld scale = f * P.T / x[n - 1];
+        for (int k = 0; k < n; ++k) x[k] *= scale;
+        ld v = P.objective(x.data());
+        if (std::isfinite((double)v)) starts.push_back({v, x});
+      }
+  }
   ld fbest = INFINITY;
   for (auto& s : starts) {
     ld x[kMaxM];

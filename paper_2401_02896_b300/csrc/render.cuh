@@ -31,7 +31,7 @@
 
 namespace sphdvr {
 
-constexpr int kCap = 2048;        // candidate table entries per ray (global scratch, L1-cached)
+constexpr int kCap = 4096;        // candidate table entries per ray (global scratch, L1-cached)
 constexpr int kKpl = 8;           // knots per lane in a window
 constexpr int kW = 32 * kKpl;     // window capacity (knots)
 constexpr int kNb = 64;           // buckets of the window sort
@@ -39,7 +39,7 @@ constexpr int kStageChunks = 16;  // chunks staged per batch
 constexpr int kStage = kStageChunks * kChunk;
 constexpr int kDefer = 48;        // new candidates that trigger window processing
 constexpr int kRenderWarps = 4;   // rays (warps) per CTA in normal rendering
-constexpr int kTableWords = 6 * kCap;  // per-ray table: 6 arrays of kCap words
+constexpr int kTableWords = 7 * kCap;  // per-ray table: 7 arrays of kCap words
 
 struct RenderParams {
   DevCamera cam;
@@ -265,6 +265,8 @@ struct WarpTable {
   float* hh;
   float* cc;
   float* tnext;
+  float* fst;  // lower bound on the particle's first knot when it was staged;
+               // non-decreasing along the table (batches arrive in bound order)
   int* meta;  // j | kn << 16 (kn = knots of this particle already passed)
   float* wk;  // emission buffer: position
   int* wv;    //                  entry | knot << 16
@@ -383,12 +385,13 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     T.hh = g + 2 * kCap;
     T.cc = g + 3 * kCap;
     T.tnext = g + 4 * kCap;
-    T.meta = (int*)(g + 5 * kCap);
+    T.fst = g + 5 * kCap;
+    T.meta = (int*)(g + 6 * kCap);
   }
   for (int i = threadIdx.x; i < p.tf_n; i += blockDim.x) s_tf[i] = p.tf[i];
   TfCtx tfc{s_tf, p.tf_n, p.tf_lo, p.tf_inv_dv, p.tf_dv};
-  unsigned long long st_cand = 0, st_tests = 0, st_knots = 0, st_win = 0, st_rays = 0, st_ert = 0;
-  int st_maxtab = 0, st_flags = 0;
+  unsigned long long st_cand = 0, st_tests = 0, st_knots = 0, st_win = 0, st_rays = 0, st_ert = 0, st_capped = 0;
+  int st_maxtab = 0, st_flags = 0, st_maxact = 0;
   const int K = p.K, m = p.m;
   const float q = p.q;
   const float t_near = (float)p.cam.t_near;
@@ -482,6 +485,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     const int2 tr = p.tile_range[tile];
     int ci = tr.x;
     const int ce = tr.y;
+    float Fprev = -__int_as_float(0x7f800000);  // bound that held before the current batch
 
     for (;;) {
       // ------------------------------------------------------------------ plan
@@ -542,6 +546,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
       __syncthreads();
       const int nplan = s_plan[kStageChunks];
       const float F = s_F[0];
+      const float Fbatch = Fprev;  // every knot of this batch's particles lies at or beyond it
+      Fprev = F;
       // ---------------------------------------------------------------- stage
       for (int i = threadIdx.x; i < nplan * kChunk; i += blockDim.x) {
         int c = s_plan[i / kChunk], r = i % kChunk;
@@ -657,6 +663,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
               float2 th = __ldg(p.theta + j);
               float tn = tc.hi + knot_sigma(K, m, th, 0) * h;
               T.tnext[slot] = tn;
+              T.fst[slot] = Fbatch;
               // a first knot before the processed part of the ray would mean the
               // ordering bound was violated: report it
               if (started && tn < Ta.hi - 1e-6f * fabsf(Ta.hi)) st_flags |= 8;
@@ -684,19 +691,32 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
         if (go) new_cands = 0;
         while (go && !done) {
           // active count, first pending knot, smallest pending h
-          int n_act = 0;
-          float tmin = __int_as_float(0x7f800000), hmin = __int_as_float(0x7f800000);
+          // lcap: longest window for which FP32 round-off stays small relative to
+          // every particle with a knot in it -- gamma h for an active particle; for
+          // a pending one, the window may run up to its first knot or gamma h
+          // beyond Ta, whichever is farther
+          int n_act = 0, n_fin = 0;
+          float tmin = __int_as_float(0x7f800000), lcap = __int_as_float(0x7f800000);
           for (int e = lane; e < n_tab; e += 32) {
             int kn = meta_kn(T.meta[e]);
-            if (kn >= 1 && kn <= K) ++n_act;
-            if (kn <= K) {
-              tmin = fminf(tmin, T.tnext[e]);
-              hmin = fminf(hmin, T.hh[e]);
+            if (kn > K) {
+              ++n_fin;
+              continue;
+            }
+            float tn = T.tnext[e], gh = p.window_h * T.hh[e];
+            tmin = fminf(tmin, tn);
+            if (kn >= 1) {
+              ++n_act;
+              lcap = fminf(lcap, gh);
+            } else {
+              lcap = fminf(lcap, fmaxf(tn - Ta.hi, gh));
             }
           }
           n_act = warp_sum_i(n_act);
+          n_fin = warp_sum_i(n_fin);
+          st_maxact = max(st_maxact, n_act);
           tmin = warp_min(tmin);
-          hmin = warp_min(hmin);
+          lcap = warp_min(lcap);
           if (tmin == __int_as_float(0x7f800000)) {
             n_tab = 0;
             break;
@@ -764,21 +784,35 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
 #pragma unroll
             for (int d = 0; d <= D; ++d) carry[d] = (S)0;
           }
-          // a window ends at the bound F, and spans at most window_h * hmin so that
-          // FP32 round-off inside it stays small relative to every particle
-          const float Uh_lim = p.window_h * hmin;
+          // a window ends at the bound F, and spans at most lcap (above); at a
+          // fresh start the pending particle at Ta bounds it by its own gamma h
+          float Uh_lim = lcap;
+          if (fresh) {
+            float l2 = __int_as_float(0x7f800000);
+            for (int e = lane; e < n_tab; e += 32) {
+              int kn = meta_kn(T.meta[e]);
+              if (kn > K) continue;
+              float tn = T.tnext[e], gh = p.window_h * T.hh[e];
+              l2 = fminf(l2, fmaxf(tn - Ta.hi, gh));
+            }
+            Uh_lim = warp_min(l2);
+          }
           const bool finF = F < __int_as_float(0x7f800000);
           float Ulim = finF ? ((F - Ta.hi) - Ta.lo) : __int_as_float(0x7f800000);
           const bool capped = Uh_lim < Ulim;
-          if (capped) Ulim = Uh_lim;
-          const float Fpre = F + 1e-3f * fabsf(F) + 1e-30f;  // prefilter on the approximate next-knot position
-          int cnt = 0, pend = 0;
+          if (capped) {
+            Ulim = Uh_lim;
+            ++st_capped;
+          }
+          // prefilter on the approximate next-knot position (absolute FP32)
+          const float Wend = fminf(F, Ta.hi + Ulim);
+          const float Fpre = Wend + 1e-3f * fabsf(Wend) + 1e-30f;
+          int cnt = 0;
           float umax = 0.f;
           for (int e = lane; e < n_tab; e += 32) {
+            if (!(T.fst[e] < Fpre)) break;  // this and all later entries start beyond the window
             int mt = T.meta[e], kn = meta_kn(mt);
-            if (kn > K) continue;
-            pend += K + 1 - kn;
-            if (!(T.tnext[e] < Fpre)) continue;
+            if (kn > K || !(T.tnext[e] < Fpre)) continue;
             float2 th = __ldg(p.theta + meta_j(mt));
             float base = (T.tc_hi[e] - Ta.hi) + (T.tc_lo[e] - Ta.lo), hh = T.hh[e];
             for (int k = kn; k <= K; ++k) {
@@ -789,7 +823,6 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             }
           }
           cnt = warp_sum_i(cnt);
-          pend = warp_sum_i(pend);
           umax = warp_max(umax);
           // no knot below the bound: wait for more particles, unless the window
           // was capped -- then the current polynomial alone spans it
@@ -807,6 +840,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
               __syncwarp();
               float sc = kNb / Uh;
               for (int e = lane; e < n_tab; e += 32) {
+                if (!(T.fst[e] < Fpre)) break;
                 int mt = T.meta[e], kn = meta_kn(mt);
                 if (kn > K || !(T.tnext[e] < Fpre)) continue;
                 float2 th = __ldg(p.theta + meta_j(mt));
@@ -850,8 +884,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             }
             Ub = (bstar >= kNb) ? Uh : Uh * ((float)bstar / kNb);
           }
-          // the window holds the ray's last knot: nothing is composited beyond it
-          const bool final_w = !finF && !by_bucket && cnt == pend;
+
           // anchor: exact coefficients of the field at Ta
           S A[D + 1];
           bool do_anchor = p.anchor_every > 0 && (fresh || (win_count % p.anchor_every) == 0);
@@ -863,6 +896,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
 #pragma unroll
             for (int d = 0; d <= D; ++d) acc[d] = 0.f;
             for (int e = lane; e < n_tab; e += 32) {
+              if (!(T.fst[e] < Ta.hi + 1e-6f * fabsf(Ta.hi))) break;  // later entries have not started
               int kn = meta_kn(T.meta[e]);
               if (kn < 1 || kn > K) continue;
               float Ae[D + 1];
@@ -880,9 +914,15 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           if (lane == 0) T.misc[0] = 0;
           __syncwarp();
           const float scb = by_bucket ? kNb / Uh : 0.f;
+          int act_after = 0;  // particles still active after this window's knots
           for (int e = lane; e < n_tab; e += 32) {
+            if (!(T.fst[e] < Fpre)) break;
             int mt = T.meta[e], kn = meta_kn(mt);
-            if (kn > K || !(T.tnext[e] < Fpre)) continue;
+            if (kn > K) continue;
+            if (!(T.tnext[e] < Fpre)) {
+              act_after += kn >= 1;
+              continue;
+            }
             float2 th = __ldg(p.theta + meta_j(mt));
             float base = (T.tc_hi[e] - Ta.hi) + (T.tc_lo[e] - Ta.lo), hh = T.hh[e];
             int k = kn;
@@ -902,10 +942,16 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
               T.meta[e] = meta_j(mt) | (k << 16);
               T.tnext[e] = k <= K ? T.tc_hi[e] + knot_sigma(K, m, th, k) * hh : __int_as_float(0x7f800000);
             }
+            act_after += (k >= 1 && k <= K);
           }
+          act_after = warp_sum_i(act_after);
           __syncwarp();
           int nwin = min(T.misc[0], kW);
           if (T.misc[0] > kW) st_flags |= 2;
+          // no particle is active after the window's last knot: the field is
+          // identically zero from there on, so the window ends at that knot (a
+          // later knot starts a new segment; the gap is composited only then)
+          const bool final_w = nwin > 0 && act_after == 0;
           my_knots += nwin;
           ++st_win;
           ++win_count;
@@ -1150,17 +1196,14 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             n_tab = 0;
             break;
           }
-          // compact the table when a quarter is finished
+          // compact the table when a quarter was finished at the window start
           {
-            int fin = 0;
-            for (int e = lane; e < n_tab; e += 32) fin += meta_kn(T.meta[e]) > K ? 1 : 0;
-            fin = warp_sum_i(fin);
-            if (fin * 4 >= n_tab || final_w) {
+            if (n_fin * 4 >= n_tab || final_w) {
               int wr = 0;
               for (int b0 = 0; b0 < n_tab; b0 += 32) {
                 int e = b0 + lane;
                 bool keep = e < n_tab && meta_kn(T.meta[e]) <= K;
-                float a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+                float a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0, a7 = 0;
                 int a6 = 0;
                 if (keep) {
                   a1 = T.tc_hi[e];
@@ -1169,6 +1212,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
                   a4 = T.cc[e];
                   a5 = T.tnext[e];
                   a6 = T.meta[e];
+                  a7 = T.fst[e];
                 }
                 unsigned km = __ballot_sync(kFull, keep);
                 __syncwarp();
@@ -1180,6 +1224,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
                   T.cc[d] = a4;
                   T.tnext[d] = a5;
                   T.meta[d] = a6;
+                  T.fst[d] = a7;
                 }
                 wr += __popc(km);
                 __syncwarp();
@@ -1229,6 +1274,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     atomicMax(p.stats + 6, (unsigned long long)st_maxtab);
     atomicOr(p.stats + 7, (unsigned long long)st_flags);
     atomicAdd(p.stats + 8, st_ert);
+    atomicMax(p.stats + 11, (unsigned long long)st_maxact);
+    atomicAdd(p.stats + 12, st_capped);
   }
 }
 

@@ -262,7 +262,7 @@ def sphdvr_frame_stats(ctx):
     s = (ctypes.c_int64 * 16)()
     _check(_lib.sphdvr_frame_stats(ctx, s), ctx)
     keys = ["rays", "segments", "knots", "windows", "pairs", "tests", "max_table", "overflow", "ert_rays",
-            "render_ns", "launches"]
+            "render_ns", "launches", "max_active", "capped_windows"]
     return {k: int(s[i]) for i, k in enumerate(keys)}
 
 
