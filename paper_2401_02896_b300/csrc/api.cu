@@ -443,6 +443,18 @@ sphdvr_status sphdvr_frame_stats(sphdvr_ctx* ctx, int64_t out[16]) {
   return SPHDVR_OK;
 }
 
+#ifdef SPHDVR_PHASE_TIMING
+// Instrumented builds only: per-phase clock64 totals of the last frame's render kernel.
+sphdvr_status sphdvr_phase_times(sphdvr_ctx* ctx, int64_t out[10]) {
+  if (!ctx || !out || !ctx->stats.p) return SPHDVR_EINVAL;
+  unsigned long long h[10];
+  cudaError_t e = cudaMemcpy(h, (unsigned long long*)ctx->stats.p + 16, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "phase times");
+  for (int i = 0; i < 10; ++i) out[i] = (int64_t)h[i];
+  return SPHDVR_OK;
+}
+#endif
+
 sphdvr_status sphdvr_debug_rays(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
                                 const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
                                 int n_pix, const int* pix, float* rgba, int64_t* counts, int64_t* cand_ids,

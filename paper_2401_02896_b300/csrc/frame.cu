@@ -229,7 +229,7 @@ sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st
       (s = ensure(ctx, ctx->chunk_ntile, (size_t)nc * sizeof(uint32_t) + 16)) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->chunk_off, (size_t)nc * sizeof(uint32_t) + 16)) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->tile_range, (size_t)tiles * sizeof(int2))) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->stats, 16 * sizeof(unsigned long long))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->stats, 32 * sizeof(unsigned long long))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->scan_tmp, scan_tmp_words(nc) * sizeof(uint32_t))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->tf, (size_t)a.tf_n * sizeof(float4))) != SPHDVR_OK)
     return s;
@@ -303,7 +303,7 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
     ++ctx->launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(ctx, e, "k_tile_ranges");
   }
-  if ((e = cudaMemsetAsync(stats, 0, 16 * sizeof(unsigned long long), st)) != cudaSuccess ||
+  if ((e = cudaMemsetAsync(stats, 0, 32 * sizeof(unsigned long long), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(w.work, 0, sizeof(unsigned), st)) != cudaSuccess)
     return cuda_err(ctx, e, "stats memset");
 

@@ -29,6 +29,16 @@
 #include "device_common.cuh"
 #include "sphdvr_internal.h"
 
+#ifdef SPHDVR_PHASE_TIMING
+#define PT_DECL long long pt_acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0}; long long pt_t0 = 0;
+#define PT_BEGIN pt_t0 = clock64();
+#define PT_END(ph) pt_acc[ph] += clock64() - pt_t0;
+#else
+#define PT_DECL
+#define PT_BEGIN
+#define PT_END(ph)
+#endif
+
 namespace sphdvr {
 
 constexpr int kCap = 4096;        // candidate table entries per ray (global scratch, L1-cached)
@@ -392,6 +402,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
   TfCtx tfc{s_tf, p.tf_n, p.tf_lo, p.tf_inv_dv, p.tf_dv};
   unsigned long long st_cand = 0, st_tests = 0, st_knots = 0, st_win = 0, st_rays = 0, st_ert = 0, st_capped = 0;
   int st_maxtab = 0, st_flags = 0, st_maxact = 0;
+  PT_DECL
   const int K = p.K, m = p.m;
   const float q = p.q;
   const float t_near = (float)p.cam.t_near;
@@ -489,6 +500,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
 
     for (;;) {
       // ------------------------------------------------------------------ plan
+      PT_BEGIN
       __syncthreads();
       if (wid == 0) {
         int taken = 0;
@@ -570,8 +582,10 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
       }
       __syncthreads();
       if (__syncthreads_and(done ? 1 : 0)) break;
+      PT_END(0)
 
       if (!done) {
+        PT_BEGIN
         // ---------------------------------------- chunks this ray can meet
         unsigned cmask = 0;
         {
@@ -683,6 +697,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
         }
         st_maxtab = max(st_maxtab, n_tab);
         __syncwarp();
+        PT_END(1)
 
         // ------------------------------------------------------ windows
         // process once enough knots are final, at the end of the stream, or
@@ -690,7 +705,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
         const bool go = !(F < __int_as_float(0x7f800000)) || new_cands >= kDefer || n_tab > kCap - 2 * kStage;
         if (go) new_cands = 0;
         while (go && !done) {
-          // active count, first pending knot, smallest pending h
+          PT_BEGIN
           // lcap: longest window for which FP32 round-off stays small relative to
           // every particle with a knot in it -- gamma h for an active particle; for
           // a pending one, the window may run up to its first knot or gamma h
@@ -717,6 +732,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           st_maxact = max(st_maxact, n_act);
           tmin = warp_min(tmin);
           lcap = warp_min(lcap);
+          PT_END(2)
+          PT_BEGIN
           if (tmin == __int_as_float(0x7f800000)) {
             n_tab = 0;
             break;
@@ -885,6 +902,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             Ub = (bstar >= kNb) ? Uh : Uh * ((float)bstar / kNb);
           }
 
+          PT_END(3)
+          PT_BEGIN
           // anchor: exact coefficients of the field at Ta
           S A[D + 1];
           bool do_anchor = p.anchor_every > 0 && (fresh || (win_count % p.anchor_every) == 0);
@@ -910,6 +929,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
 #pragma unroll
             for (int d = 0; d <= D; ++d) A[d] = carry[d];
           }
+          PT_END(4)
+          PT_BEGIN
           // emission of the window's knots
           if (lane == 0) T.misc[0] = 0;
           __syncwarp();
@@ -955,6 +976,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           my_knots += nwin;
           ++st_win;
           ++win_count;
+          PT_END(5)
+          PT_BEGIN
           // bucket sort of the window by position
           {
             float wmax = 0.f;
@@ -1014,6 +1037,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             }
             __syncwarp();
           }
+          PT_END(6)
+          PT_BEGIN
           // ---- segmented scan of the difference coefficients (Sec. 2)
           const float Uend = final_w ? (nwin > 0 ? T.sk[nwin - 1] : 0.f) : Ub;
           float ul[kKpl];
@@ -1196,6 +1221,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             n_tab = 0;
             break;
           }
+          PT_END(7)
+          PT_BEGIN
           // compact the table when a quarter was finished at the window start
           {
             if (n_fin * 4 >= n_tab || final_w) {
@@ -1232,6 +1259,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
               n_tab = wr;
             }
           }
+          PT_END(8)
           if (final_w && n_tab == 0) break;
         }
       }
@@ -1276,6 +1304,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     atomicAdd(p.stats + 8, st_ert);
     atomicMax(p.stats + 11, (unsigned long long)st_maxact);
     atomicAdd(p.stats + 12, st_capped);
+#ifdef SPHDVR_PHASE_TIMING
+    for (int ph = 0; ph < 10; ++ph) atomicAdd(p.stats + 16 + ph, (unsigned long long)pt_acc[ph]);
+#endif
   }
 }
 
