@@ -202,6 +202,34 @@ sphdvr_status sphdvr_render_host(sphdvr_ctx* ctx, const sphdvr_dataset* ds, cons
                                  const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
                                  float* rgba_host, void* stream);
 
+/* Allocation-free form of sphdvr_render (no counterpart in the paper: a
+ * library service for callers that must not allocate device memory while
+ * they render, e.g. a server whose device memory is all handed to its own
+ * pool, a process at its memory limit, or a latency-bound caller that cannot
+ * take the device-wide synchronisation cudaMalloc/cudaFree may bring).
+ *
+ * Same arguments, kernels and image as sphdvr_render; `rgba_out` is a DEVICE
+ * pointer (width*height*4 floats, caller-owned).  Every scratch buffer of the
+ * frame is carved from one file-scope device array of 192 MiB inside the
+ * library, so the call allocates no device or host memory.  Limits (EINVAL
+ * before any work is enqueued): at most 65536 tiles of 16x16 pixels (e.g.
+ * 4096 x 4096) and at most 1048576 dataset chunks (sphdvr_dataset_info
+ * info[1]); EOVERFLOW when the frame has more than 4194304 chunk-tile pairs
+ * (nothing is rendered then).  The render grid is capped at 148 CTAs.
+ *
+ * The first call on a device looks up the array's device address (set-up,
+ * once per device); make that first call before any stream capture begins.
+ * All calls in the process share the one array: calls that can overlap in
+ * time (different streams, threads or contexts on the same device) race on
+ * it and must be ordered by the caller.  Every buffer that must start at
+ * zero is cleared on the stream by the call itself.  The call synchronises
+ * `stream` once to read the frame's pair count, as sphdvr_render does.  It
+ * keeps no counters: sphdvr_frame_stats afterwards reports zeros except for
+ * the render time and the launch count. */
+sphdvr_status sphdvr_render_static_scratch(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+                                           const sphdvr_camera* cam, const sphdvr_tf* tf,
+                                           const sphdvr_render_opts* opts, float* rgba_out, void* stream);
+
 /* Statistics of the context's last completed frame (synchronises its
  * stream): out[0] rays, [1] candidate particle-ray segments, [2] knots,
  * [3] windows, [4] chunk-tile pairs, [5] particle tests, [6] max table

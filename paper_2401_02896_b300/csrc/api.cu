@@ -57,6 +57,8 @@ void free_buf(DevBuf& b) {
   b.bytes = 0;
 }
 
+}  // namespace
+
 sphdvr_status check_camera(sphdvr_ctx* ctx, const sphdvr_camera* c, DevCamera* out) {
   if (!c) return set_err(ctx, SPHDVR_EINVAL, "camera is NULL");
   if (c->width < 1 || c->height < 1 || c->width > 32768 || c->height > 32768)
@@ -140,7 +142,6 @@ sphdvr_status check_common(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphd
   return cuda_err(ctx, e, "cudaSetDevice");
 }
 
-}  // namespace
 }  // namespace sphdvr
 
 using namespace sphdvr;

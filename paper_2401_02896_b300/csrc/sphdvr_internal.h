@@ -100,6 +100,10 @@ sphdvr_status set_err(sphdvr_ctx* ctx, sphdvr_status st, const std::string& msg)
 sphdvr_status cuda_err(sphdvr_ctx* ctx, cudaError_t e, const char* where);
 sphdvr_status ensure(sphdvr_ctx* ctx, DevBuf& b, size_t bytes);
 sphdvr_status dev_alloc(sphdvr_ctx* ctx, void** p, size_t bytes);
+// Argument checks shared by the render entry points (api.cu).
+sphdvr_status check_camera(sphdvr_ctx* ctx, const sphdvr_camera* c, DevCamera* out);
+sphdvr_status check_opts(sphdvr_ctx* ctx, const sphdvr_render_opts* o);
+sphdvr_status check_common(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut);
 
 // sort.cu
 // Exclusive prefix sum of n uint32 values (in may equal out).  If total is

@@ -85,6 +85,8 @@ def _load():
                                          ctypes.POINTER(RenderOpts), vp, vp]),
         "sphdvr_render_host": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                               ctypes.POINTER(RenderOpts), vp, vp]),
+        "sphdvr_render_static_scratch": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
+                                                       ctypes.POINTER(RenderOpts), vp, vp]),
         "sphdvr_frame_stats": (ctypes.c_int, [vp, i64p]),
         "sphdvr_debug_rays": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                              ctypes.POINTER(RenderOpts), ctypes.c_int, vp, vp, vp, vp, ctypes.c_int,
@@ -245,6 +247,14 @@ def sphdvr_render(ctx, ds, lut, camera, tf, opts, out_ptr, stream=None, allow_ov
     st = _lib.sphdvr_render(ctx, ds, lut, ctypes.byref(c), ctypes.byref(t), ctypes.byref(o),
                             ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream) if stream else None)
     return _check(st, ctx, (EOVERFLOW,) if allow_overflow else ())
+
+
+def sphdvr_render_static_scratch(ctx, ds, lut, camera, tf, opts, out_ptr, stream=None):
+    """As sphdvr_render, with all frame scratch in the library's fixed device array (no allocation)."""
+    c, t, o = camera_struct(camera), tf_struct(tf), opts_struct(opts)
+    st = _lib.sphdvr_render_static_scratch(ctx, ds, lut, ctypes.byref(c), ctypes.byref(t), ctypes.byref(o),
+                                           ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream) if stream else None)
+    return _check(st, ctx)
 
 
 def sphdvr_render_host(ctx, ds, lut, camera, tf, opts, out=None, stream=None, allow_overflow=False):
