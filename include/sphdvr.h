@@ -214,8 +214,8 @@ sphdvr_status sphdvr_render_host(sphdvr_ctx* ctx, const sphdvr_dataset* ds, cons
  * library, so the call allocates no device or host memory.  Limits (EINVAL
  * before any work is enqueued): at most 65536 tiles of 16x16 pixels (e.g.
  * 4096 x 4096) and at most 1048576 dataset chunks (sphdvr_dataset_info
- * info[1]); EOVERFLOW when the frame has more than 4194304 chunk-tile pairs
- * (nothing is rendered then).  The render grid is capped at 148 CTAs.
+ * info[1]); EOVERFLOW when the frame has more than 2097152 chunk-tile pairs
+ * (nothing is rendered then).  The render grid is capped at 64 CTAs.
  *
  * The first call on a device looks up the array's device address (set-up,
  * once per device); make that first call before any stream capture begins.

@@ -188,7 +188,7 @@ int render_grid(sphdvr_ctx* ctx, const RenderArgs& a) {
     items = a.n_dbg;
   } else {
     const int tiles = ((a.cam.width + kTile - 1) / kTile) * ((a.cam.height + kTile - 1) / kTile);
-    items = tiles * (kTile / 2) * (kTile / 2);
+    items = (tiles * kTile * kTile + kRenderWarps - 1) / kRenderWarps;
   }
   int grid = std::max(1, nb) * ctx->num_sms;
   return std::max(1, std::min(grid, items));
@@ -356,7 +356,7 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
   const int grid = std::min(render_grid(ctx, a), w.table_ctas);
   p.scratch = w.table;
   p.work = w.work;
-  p.n_items = n_tiles * (kTile / 2) * (kTile / 2);
+  p.n_items = n_tiles * kTile * kTile;
   p.dynamic = (o && o->persistent) ? 1 : 0;
   size_t smem = render_smem_bytes(a.tf_n, dbg ? 1 : kRenderWarps);
   return dispatch_render(ctx, L->D, f64, dbg, p, grid, smem, st);

@@ -1,26 +1,32 @@
 // Per-ray field reconstruction and compositing kernel.
 //
-// One warp owns one viewing ray; a CTA of NW warps owns an NW-ray sub-tile of a
-// 16x16 binning tile and streams that tile's chunk list (sorted by a lower
-// bound F of every knot position a chunk's particles can produce) through
-// shared memory.  Per ray:
-//   1. candidate gathering: every staged particle is tested against the ray in
-//      FP32, and in double-float (hi+lo FP32 pairs) near the decision; a
-//      candidate has d < q h and its support ends after t_near (Sec. 3.1);
+// Every warp is an independent persistent worker that owns one viewing ray at
+// a time (no block-wide barriers).  The ray's 16x16 binning tile lists its
+// chunks sorted by a lower bound F of every knot position a chunk's particles
+// can produce.  Per ray:
+//   1. candidate gathering: the warp walks the tile's chunk list, keeps the
+//      chunks whose screen rectangle covers the pixel and whose bounding
+//      sphere (grown by q h_max) meets the ray, and tests their particles
+//      (one per lane) in FP32, and in double-float (hi + lo FP32 pairs) near
+//      the decision; a candidate has d < q h and its support ends after
+//      t_near (Sec. 3.1);
 //   2. per-particle approximation: L = d/h picks the nearest table entry; the
-//      particle's knots are t_chi + h * (+-theta_k, 0) with localized
-//      difference coefficients a h^-3 * s_kd / h^d (Sec. 2, Sec. 3.1);
-//      candidates are kept in a per-warp table in shared memory;
-//   3. windows: all knots below the current bound F are final; up to W of them
-//      (the window) are emitted from the table, bucket-sorted by position and
-//      insertion-sorted within buckets;
-//   4. segmented prefix sum: the coefficient-update recurrence of Sec. 2
-//      (eq. Piecewise-Coefficients-Update) as an associative scan over the warp
-//      -- (A, e_A) (+) (B, e_B) = (Shift(A, e_B - e_A) + B, e_B) -- seeded with
-//      the field's exact coefficients at the window start, summed over the
-//      active particles' own pieces (re-anchoring bounds the FP32 drift that
-//      Sec. 4.1 describes);
-//   5. classification + compositing per piece: pieces are split where the
+//      particle's K+1 knots are t_chi + h * sigma_k with localized difference
+//      coefficients a h^-3 * s_kd / h^d (Sec. 2, Sec. 3.1); the particle goes
+//      to the ray's entry table and its knots to a buffer of new knots;
+//   3. knot sort and merge: new knots are radix-sorted (warp LSD sort) and
+//      merged into the ray's sorted list of pending knots; all pending knots
+//      below the bound F of the next chunk are final;
+//   4. windows: a window is a prefix of the pending list (at most W knots,
+//      shortened so that FP32 round-off stays small for the particles it
+//      touches);
+//   5. segmented prefix sum: the coefficient-update recurrence of Sec. 2 as an
+//      associative scan over the warp -- (A, e_A) (+) (B, e_B) =
+//      (Shift(A, e_B - e_A) + B, e_B) -- seeded with the field's exact
+//      coefficients at the window start, summed over the active particles'
+//      own pieces (re-anchoring bounds the FP32 drift that Sec. 4.1
+//      describes);
+//   6. classification + compositing per piece: pieces are split where the
 //      field crosses transfer-function nodes, optical depth is integrated in
 //      closed form, emission by 2-point Gauss-Legendre; transmittance is kept
 //      as accumulated optical depth; early ray termination.
@@ -41,15 +47,23 @@
 
 namespace sphdvr {
 
-constexpr int kCap = 4096;        // candidate table entries per ray (global scratch, L1-cached)
-constexpr int kKpl = 8;           // knots per lane in a window
-constexpr int kW = 32 * kKpl;     // window capacity (knots)
-constexpr int kNb = 64;           // buckets of the window sort
-constexpr int kStageChunks = 16;  // chunks staged per batch
-constexpr int kStage = kStageChunks * kChunk;
-constexpr int kDefer = 48;        // new candidates that trigger window processing
-constexpr int kRenderWarps = 4;   // rays (warps) per CTA in normal rendering
-constexpr int kTableWords = 7 * kCap;  // per-ray table: 7 arrays of kCap words
+constexpr int kCap = 4096;          // particle entries per ray
+constexpr int kPL = 3 * kCap;       // pending knots per ray (sorted list)
+constexpr int kNK = 512;            // new knots awaiting a merge (shared memory)
+constexpr int kKpl = 8;             // knots per lane in a window
+constexpr int kW = 32 * kKpl;       // window capacity (knots)
+constexpr int kLevels = 128;        // smoothing-length bins (quarter octaves) for the window limit
+constexpr int kLevelBase = (127 - 28) << 2;  // bin 0 starts at h = 2^-28
+constexpr int kRenderWarps = 4;     // rays (warps) per CTA in normal rendering
+// per-ray global scratch (32-bit words): 5 entry arrays, processed-knot
+// counts, active list, free stack, two pending-knot buffers (key, value)
+constexpr int kTableWords = 8 * kCap + 4 * kPL;
+// per-warp shared memory (bytes): radix histogram, smoothing-length histogram,
+// and a work area shared in time by the new-knot buffers (two key/value
+// buffers, the second also stages pending knots during a merge) and the
+// window's difference coefficients
+constexpr int kWorkBytes = 4 * kNK * 4;  // >= the window: kW * (D + 1) floats for D <= 7
+constexpr int kWarpSmem = 256 * 4 + kLevels * 4 + kWorkBytes;
 
 struct RenderParams {
   DevCamera cam;
@@ -78,13 +92,13 @@ struct RenderParams {
   const float4* tf;
   // options
   int anchor_every;  // 0: never (naive recurrence)
-  float window_h;    // window length limit in units of the smallest pending h
+  float window_h;    // window length limit in units of the smallest h it touches
   float tau_ert;     // stop when accumulated optical depth exceeds this
   float* out;
   unsigned long long* stats;
-  float* scratch;       // per-ray tables: (grid * NW) * kTableWords words
+  float* scratch;       // per-ray scratch: (grid * NW) * kTableWords words
   unsigned* work;       // work-queue counter (dynamic scheduling), zeroed per frame
-  int n_items;          // sub-tiles
+  int n_items;          // rays (tile-major, 256 per tile)
   int dynamic;          // 1: atomic work queue, 0: static stride
   // debug
   int n_dbg;
@@ -180,6 +194,7 @@ __device__ __forceinline__ void composite_cell(const float* Q, float L, int c, c
   float h = L / ns;
   const float x0 = 0.21132486540518713f, x1 = 0.78867513459481287f;
   float Gprev = 0.f;
+#pragma unroll 1
   for (int s = 0; s < ns; ++s) {
     float ya = s * h;
     float y0 = ya + x0 * h, y1 = ya + x1 * h;
@@ -265,29 +280,52 @@ __device__ __noinline__ void composite_piece_slow(const float* P, float L, float
   }
 }
 
+
+template <int D>
+struct Poly {
+  float c[D + 1];
+};
+// optical depth and un-attenuated colour accumulated by one lane
+struct Acc {
+  float tau, r, g, b;
+};
+
+// Out of line, with value arguments, so that the render kernel holds a
+// single copy of the compositing code.
+template <int D>
+__device__ __noinline__ Acc composite_piece_v(Poly<D> P, float L, TfCtx t, Acc a) {
+  float C[3] = {a.r, a.g, a.b};
+  float tau = a.tau;
+  composite_piece<D>(P.c, L, t, tau, C);
+  return Acc{tau, C[0], C[1], C[2]};
+}
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
 
-struct WarpTable {
-  float* tc_hi;
+// Per-ray scratch: entry arrays, lists and knot buffers in global memory
+// (L1/L2-resident while the ray is live); masks and histograms in shared memory.
+struct RayScratch {
+  float* tc_hi;  // t_chi (double-float)
   float* tc_lo;
-  float* hh;
-  float* cc;
-  float* tnext;
-  float* fst;  // lower bound on the particle's first knot when it was staged;
-               // non-decreasing along the table (batches arrive in bound order)
-  int* meta;  // j | kn << 16 (kn = knots of this particle already passed)
-  float* wk;  // emission buffer: position
-  int* wv;    //                  entry | knot << 16
-  float* sk;  // sorted buffer
-  int* sv;
-  int* hist;  // kNb bucket counts, then kNb offsets
-  int* misc;  // [0] emission counter
+  float* hh;     // h
+  float* cc;     // a / h^3
+  int* jj;       // table entry (Lambda index)
+  int* kn;       // knots processed so far (atomic max; read through L2)
+  int* act;      // active list: entries whose first knot has been processed
+  int* fre;      // free stack of entry slots
+  float* pk0;    // pending knots, sorted: FP32 absolute position (two buffers)
+  int* pv0;      //                        entry | k << 16
+  float* pk1;
+  int* pv1;
+  int* rh;       // shared: radix histogram (256 bins)
+  int* lvl;      // shared: active particles per smoothing-length bin
+  float* nk0;    // shared: new knots (unsorted, then radix ping-pong)
+  int* nv0;
+  float* nk1;
+  int* nv1;
+  float* wdl;    // shared: the window's difference coefficients (aliases the new-knot buffers)
 };
-
-__device__ __forceinline__ int meta_j(int m) { return m & 0xffff; }
-__device__ __forceinline__ int meta_kn(int m) { return (m >> 16) & 0xff; }
 
 // normalised knot offset of sorted knot k of an entry with knots (theta_1, theta_2)
 __device__ __forceinline__ float knot_sigma(int K, int m, float2 th, int k) {
@@ -310,26 +348,27 @@ __device__ __forceinline__ int knot_slot(int K, int m, int k, bool& mirror) {
   return k - m;  // 0 for the middle knot
 }
 
+// localized difference coefficients of knot k of a particle with table entry
+// j, smoothing length h and amplitude c = a / h^3 (Sec. 2, Sec. 3.1)
 template <int D>
-__device__ __forceinline__ void knot_delta(const RenderParams& p, const WarpTable& T, int e, int k, float* dl) {
-  int j = meta_j(T.meta[e]);
+__device__ __forceinline__ void knot_delta(const RenderParams& p, int j, float h, float c, int k, float* dl) {
   bool mir;
   int slot = knot_slot(p.K, p.m, k, mir);
   const float* jr = p.jump + (size_t)j * 3 * D + slot * D;
-  float ih = 1.f / T.hh[e], s = T.cc[e];
-  dl[0] = 0.f;
+  float ih = 1.f / h, s = c;
 #pragma unroll
   for (int d = 1; d <= D; ++d) {
     s *= ih;
     float v = __ldg(jr + d - 1) * s;
-    dl[d] = (mir && !(d & 1)) ? -v : v;
+    dl[d - 1] = (mir && !(d & 1)) ? -v : v;
   }
 }
 
-// Exact coefficients at Ta of entry e's current piece (the one after its kn-1-th knot).
+// Exact coefficients at Ta of entry e's piece after its first kn knots.
 template <int D>
-__device__ __forceinline__ void entry_piece_at(const RenderParams& p, const WarpTable& T, int e, df Ta, float* A) {
-  int mt = T.meta[e], j = meta_j(mt), kn = meta_kn(mt), pc = kn - 1;
+__device__ __forceinline__ void entry_piece_at(const RenderParams& p, const RayScratch& T, int e, int kn, df Ta,
+                                               float* A) {
+  int j = T.jj[e], pc = kn - 1;
   int K = p.K, m = p.m, kp;
   float sg;
   if (!(K & 1)) {
@@ -357,56 +396,268 @@ __device__ __forceinline__ void entry_piece_at(const RenderParams& p, const Warp
   }
 }
 
-// Per-warp window buffers live in shared memory; the candidate table of the
-// ray lives in global scratch (L1-cached) so that dense regions never run out
-// of room.
+// bin of h > 0: exponent and the two leading mantissa bits (quarter octaves)
+__device__ __forceinline__ int h_level(float h) {
+  return min(kLevels - 1, max(0, (__float_as_int(h) >> 21) - kLevelBase));
+}
+// lower edge of bin l
+__device__ __forceinline__ float level_lo(int l) { return __int_as_float((l + kLevelBase) << 21); }
+
+// order-preserving map of an FP32 value to an unsigned key
+__device__ __forceinline__ unsigned f2key(float x) {
+  unsigned b = __float_as_uint(x);
+  return b ^ ((unsigned)((int)b >> 31) | 0x80000000u);
+}
+
+// Stable LSD radix sort (8-bit digits) of n (key, value) pairs by FP32 key,
+// one warp; digits that every key shares are skipped.  Returns which buffer
+// (0 or 1) holds the result.
+__device__ __forceinline__ int warp_radix_sort(float* k0, int* v0, float* k1, int* v1, int n, int* rh) {
+  const int lane = threadIdx.x & 31;
+  int cur = 0;
+#pragma unroll 1
+  for (int pass = 0; pass < 4; ++pass) {
+    const int sh = 8 * pass;
+    const float* kc = cur ? k1 : k0;
+    const int* vc = cur ? v1 : v0;
+    float* kd = cur ? k0 : k1;
+    int* vd = cur ? v0 : v1;
+    for (int b = lane; b < 256; b += 32) rh[b] = 0;
+    __syncwarp();
+#pragma unroll 1
+    for (int i = lane; i < n; i += 32) atomicAdd(&rh[(f2key(kc[i]) >> sh) & 255], 1);
+    __syncwarp();
+    int c[8], s = 0;
+    bool all_one = false;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      c[r] = rh[lane * 8 + r];
+      s += c[r];
+      all_one |= c[r] == n;
+    }
+    if (__any_sync(kFull, all_one)) continue;  // every key has this digit
+    int x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    int ex = x - s;
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      rh[lane * 8 + r] = ex;
+      ex += c[r];
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int base = 0; base < n; base += 32) {
+      const int i = base + lane;
+      const bool valid = i < n;
+      const float kk = valid ? kc[i] : 0.f;
+      const int vv = valid ? vc[i] : 0;
+      const int d = valid ? (int)((f2key(kk) >> sh) & 255) : 256 + lane;
+      const unsigned peers = __match_any_sync(kFull, d);
+      const int rank = __popc(peers & lanemask_lt());
+      const int pos = valid ? rh[d] + rank : 0;
+      __syncwarp();
+      if (valid && rank == 0) rh[d] += __popc(peers);
+      __syncwarp();
+      if (valid) {
+        kd[pos] = kk;
+        vd[pos] = vv;
+      }
+    }
+    __syncwarp();
+    cur ^= 1;
+  }
+  return cur;
+}
+
+// Merge the sorted pending knots a[0, na) (global) with the sorted new knots
+// b[0, nb) (shared) into o[0, nout), nout <= na + nb (the largest keys are
+// dropped when it is smaller); equal keys take a first.  The output is made
+// in tiles of 32 * 16: the next 512 elements of a are staged in shared memory
+// (st, sv), each lane finds its 16-element slice by a merge-path search and
+// merges it sequentially.
+__device__ __forceinline__ void warp_tile_merge(const float* ak, const int* av, int na, const float* bk,
+                                                const int* bv, int nb, float* ok, int* ov, int nout, float* stk,
+                                                int* stv) {
+  constexpr int kPer = 16, kTileOut = 32 * kPer;
+  const int lane = threadIdx.x & 31;
+  int ia0 = 0, ib0 = 0;  // consumed so far
+#pragma unroll 1
+  for (int o0 = 0; o0 < nout; o0 += kTileOut) {
+    const int ta = min(kTileOut, na - ia0);  // staged part of a
+    const int tb = nb - ib0;
+#pragma unroll 4
+    for (int i = lane; i < ta; i += 32) {
+      stk[i] = ak[ia0 + i];
+      stv[i] = av[ia0 + i];
+    }
+    __syncwarp();
+    const int tout = min(kTileOut, nout - o0);
+    const float* bt = bk + ib0;
+    const int* bvt = bv + ib0;
+    // merge path: a elements among the first d outputs of this tile
+    auto path = [&](int d) -> int {
+      int lo = max(0, d - tb), hi = min(d, ta);
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (!(bt[d - 1 - mid] < stk[mid])) lo = mid + 1;
+        else hi = mid;
+      }
+      return lo;
+    };
+    const int d0 = min(lane * kPer, tout), d1 = min(d0 + kPer, tout);
+    int ia = path(d0), ib = d0 - ia;
+#pragma unroll 1
+    for (int d = d0; d < d1; ++d) {
+      const bool take_a = ib >= tb || (ia < ta && stk[ia] <= bt[ib]);
+      if (take_a) {
+        ok[o0 + d] = stk[ia];
+        ov[o0 + d] = stv[ia];
+        ++ia;
+      } else {
+        ok[o0 + d] = bt[ib];
+        ov[o0 + d] = bvt[ib];
+        ++ib;
+      }
+    }
+    // elements of a consumed by the whole tile
+    const int used_a = path(tout);
+    __syncwarp();
+    ia0 += used_a;
+    ib0 += tout - used_a;
+  }
+  __syncwarp();
+}
+
+// Number of keys below w in the sorted range k[lo, hi) (32-ary search).
+__device__ __forceinline__ int warp_count_below(const float* k, int lo, int hi, float w) {
+  const int lane = threadIdx.x & 31;
+  int n = hi - lo, base = lo;
+  if (n <= 0) return 0;
+  while (n > 32) {
+    const int step = (n + 31) / 32;
+    const int idx = base + lane * step;
+    const unsigned mb = __ballot_sync(kFull, idx < hi && k[idx] < w);
+    const int c = __popc(mb);
+    if (c == 0) return base - lo;
+    base += (c - 1) * step;
+    n = min(step, hi - base);
+  }
+  const unsigned mb = __ballot_sync(kFull, lane < n && k[base + lane] < w);
+  return base + __popc(mb) - lo;
+}
+
+// One pass over the active list: drops particles whose last knot has been
+// processed (their slots go to the free stack) and, if `sum`, adds every
+// remaining particle's own piece at Ta (the anchor).  Two entries per lane
+// per step so that their loads overlap.
+template <int D>
+__device__ __forceinline__ void active_pass(const RenderParams& p, const RayScratch& T, int& nal, int& nfree, df Ta,
+                                            bool sum, float* acc) {
+  const int lane = threadIdx.x & 31;
+  const int K = p.K;
+  int wr = 0;
+#pragma unroll 1
+  for (int b0 = 0; b0 < nal; b0 += 64) {
+    int e[2], kn[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = b0 + 32 * u + lane;
+      e[u] = i < nal ? T.act[i] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) kn[u] = e[u] >= 0 ? __ldcg(T.kn + e[u]) : 0;
+    bool keep[2], fin[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      fin[u] = e[u] >= 0 && kn[u] > K;
+      keep[u] = e[u] >= 0 && !fin[u];
+    }
+    if (sum) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (keep[u]) {
+          float Ae[D + 1];
+          entry_piece_at<D>(p, T, e[u], kn[u], Ta, Ae);
+#pragma unroll
+          for (int d = 0; d <= D; ++d) acc[d] += Ae[d];
+        }
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const unsigned km = __ballot_sync(kFull, keep[u]), fm = __ballot_sync(kFull, fin[u]);
+      if (keep[u]) T.act[wr + __popc(km & lanemask_lt())] = e[u];
+      if (fin[u]) T.fre[nfree + __popc(fm & lanemask_lt())] = e[u];
+      wr += __popc(km);
+      nfree += __popc(fm);
+    }
+  }
+  __syncwarp();
+  nal = wr;
+}
+
+// Nearest Lambda entry decided in FP64 from the double-float components of the
+// ray-to-particle vector (used near a midpoint between entries).
+static __device__ __noinline__ int nearest_entry_fp64(const df* wv, float h, int n_lambda, float q) {
+  double d2d = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double wk = (double)wv[k].hi + (double)wv[k].lo;
+    d2d += wk * wk;
+  }
+  const double xd = sqrt(d2d) / (double)h * ((double)(n_lambda - 1) / (double)q);
+  return (int)floor(xd + 0.5);
+}
+
+// Each warp is an independent worker; the only shared state of a CTA is the
+// transfer function.
 template <int D, typename S, int NW, bool DBG>
 __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // ---- shared memory carve-up
   float4* s_tf = (float4*)smem;
-  unsigned char* ptr = smem + sizeof(float4) * p.tf_n;
-  float4* s_pos = (float4*)ptr;
-  ptr += sizeof(float4) * kStage;
-  float4* s_sph = (float4*)ptr;  // bounding sphere (centre, radius + q h_max) per staged chunk
-  ptr += sizeof(float4) * kStageChunks;
-  float* s_amp = (float*)ptr;
-  ptr += sizeof(float) * kStage;
-  int* s_idx = (int*)ptr;
-  ptr += sizeof(int) * kStage;
-  int* s_plan = (int*)ptr;  // [0..kStageChunks-1] chunk ids, [kStageChunks] count, [+1] work item
-  ptr += sizeof(int) * (kStageChunks + 4);
-  float* s_F = (float*)ptr;
-  ptr += sizeof(float) * 4;
-  const size_t per_warp = (sizeof(float) + sizeof(int)) * 2 * kW + sizeof(int) * (2 * kNb + 4);
-  WarpTable T;
+  RayScratch T;
   {
-    unsigned char* b = ptr + per_warp * wid;
-    T.wk = (float*)b; b += sizeof(float) * kW;
-    T.wv = (int*)b; b += sizeof(int) * kW;
-    T.sk = (float*)b; b += sizeof(float) * kW;
-    T.sv = (int*)b; b += sizeof(int) * kW;
-    T.hist = (int*)b; b += sizeof(int) * 2 * kNb;
-    T.misc = (int*)b;
+    unsigned char* b = smem + sizeof(float4) * p.tf_n + (size_t)kWarpSmem * wid;
+    T.rh = (int*)b;
+    T.lvl = (int*)(b + 256 * 4);
+    float* w = (float*)(b + 256 * 4 + kLevels * 4);
+    T.nk0 = w;
+    T.nv0 = (int*)(w + kNK);
+    T.nk1 = w + 2 * kNK;
+    T.nv1 = (int*)(w + 3 * kNK);
+    T.wdl = w;
     float* g = p.scratch + (size_t)(blockIdx.x * NW + wid) * kTableWords;
     T.tc_hi = g;
     T.tc_lo = g + kCap;
     T.hh = g + 2 * kCap;
     T.cc = g + 3 * kCap;
-    T.tnext = g + 4 * kCap;
-    T.fst = g + 5 * kCap;
-    T.meta = (int*)(g + 6 * kCap);
+    T.jj = (int*)(g + 4 * kCap);
+    T.kn = (int*)(g + 5 * kCap);
+    T.act = (int*)(g + 6 * kCap);
+    T.fre = (int*)(g + 7 * kCap);
+    float* q0 = g + 8 * kCap;
+    T.pk0 = q0;
+    T.pv0 = (int*)(q0 + kPL);
+    T.pk1 = q0 + 2 * kPL;
+    T.pv1 = (int*)(q0 + 3 * kPL);
   }
   for (int i = threadIdx.x; i < p.tf_n; i += blockDim.x) s_tf[i] = p.tf[i];
-  TfCtx tfc{s_tf, p.tf_n, p.tf_lo, p.tf_inv_dv, p.tf_dv};
+  __syncthreads();
+  const TfCtx tfc{s_tf, p.tf_n, p.tf_lo, p.tf_inv_dv, p.tf_dv};
   unsigned long long st_cand = 0, st_tests = 0, st_knots = 0, st_win = 0, st_rays = 0, st_ert = 0, st_capped = 0;
   int st_maxtab = 0, st_flags = 0, st_maxact = 0;
   PT_DECL
-  const int K = p.K, m = p.m;
-  const float q = p.q;
+  const int K = p.K, m = p.m, KP1 = K + 1;
+  const float q = p.q, gam = p.window_h;
   const float t_near = (float)p.cam.t_near;
   const df t_near_df = df_from_double(p.cam.t_near);
+  const float kInf = __int_as_float(0x7f800000);
 
   for (int it = 0;; ++it) {
     // ------------------------------------------------------------ work item
@@ -414,41 +665,29 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     if (DBG) {
       item = blockIdx.x + it * gridDim.x;
     } else if (p.dynamic) {
-      __syncthreads();
-      if (threadIdx.x == 0) s_plan[kStageChunks + 1] = (int)atomicAdd(p.work, 1u);
-      __syncthreads();
-      item = s_plan[kStageChunks + 1];
+      unsigned v = 0;
+      if (lane == 0) v = atomicAdd(p.work, 1u);
+      item = (int)__shfl_sync(kFull, v, 0);
     } else {
-      item = blockIdx.x + it * gridDim.x;
+      item = (blockIdx.x * NW + wid) + it * gridDim.x * NW;
     }
     if (item >= (DBG ? p.n_dbg : p.n_items)) break;
-
-    // ---- which rays
-    int tile, px, py, sx0, sy0, sx1, sy1;
+    int tile, px, py;
     long long dbg_row = -1;
     if (DBG) {
       dbg_row = item;
-      int pix = p.dbg_pix[item];
+      const int pix = p.dbg_pix[item];
       px = pix % p.cam.width;
       py = pix / p.cam.width;
       tile = (py / kTile) * p.tiles_x + px / kTile;
-      sx0 = sx1 = px;
-      sy0 = sy1 = py;
     } else {
-      constexpr int SW = NW == 8 ? 4 : (NW == 4 ? 2 : 1);
-      constexpr int SH = NW / SW;
-      constexpr int SUB = (kTile / SW) * (kTile / SH);
-      tile = item / SUB;
-      int sub = item % SUB;
-      int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
-      sx0 = tx * kTile + (sub % (kTile / SW)) * SW;
-      sy0 = ty * kTile + (sub / (kTile / SW)) * SH;
-      sx1 = sx0 + SW - 1;
-      sy1 = sy0 + SH - 1;
-      px = sx0 + wid % SW;
-      py = sy0 + wid / SW;
+      tile = item >> 8;
+      const int sub = item & 255;
+      px = (tile % p.tiles_x) * kTile + (sub & 15);
+      py = (tile / p.tiles_x) * kTile + (sub >> 4);
     }
-    const bool in_img = px < p.cam.width && py < p.cam.height;
+    if (px >= p.cam.width || py >= p.cam.height) continue;
+    const float pxf = (float)px, pyf = (float)py;
 
     // ---- the ray, FP64 -> double-float
     df o[3], v[3];
@@ -481,290 +720,103 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     }
 
     // ---- per-ray state
-    bool done = !in_img;
-    bool started = false;
+    bool done = false, started = false;
     df Ta = {0.f, 0.f}, t_start = {0.f, 0.f};
     float tau_ray = 0.f, col[3] = {0.f, 0.f, 0.f};
-    int n_tab = 0, win_count = 0, new_cands = 0;
     S carry[D + 1];
 #pragma unroll
     for (int d = 0; d <= D; ++d) carry[d] = (S)0;
-    long long dbg_np = 0;  // field pieces written
-    long long dbg_nc = 0;  // candidate ids written
+    int hwm = 0, nfree = 0, nal = 0, n_act = 0, head = 0, npl = 0, pb = 0, nnk = 0, win_count = 0;
+    long long dbg_np = 0, dbg_nc = 0;
     unsigned long long my_knots = 0;
+    for (int b = lane; b < kLevels; b += 32) T.lvl[b] = 0;
+    __syncwarp();
 
     const int2 tr = p.tile_range[tile];
-    int ci = tr.x;
     const int ce = tr.y;
-    float Fprev = -__int_as_float(0x7f800000);  // bound that held before the current batch
-
-    for (;;) {
-      // ------------------------------------------------------------------ plan
-      PT_BEGIN
-      __syncthreads();
-      if (wid == 0) {
-        int taken = 0;
-        float Fnext = __int_as_float(0x7f800000);  // +inf
-        bool fset = false;
-        while (ci < ce && taken < kStageChunks) {
-          int idx = ci + lane;
-          bool valid = idx < ce;
-          int cid = valid ? (int)p.pair_val[idx] : -1;
-          bool ok = false;
-          if (valid) {
-            float4 r = __ldg(p.chunk_rect + cid);
-            ok = r.x <= (float)sx1 + 0.5f && r.z >= (float)sx0 - 0.5f && r.y <= (float)sy1 + 0.5f &&
-                 r.w >= (float)sy0 - 0.5f;
-          }
-          unsigned mk = __ballot_sync(kFull, ok);
-          int need = kStageChunks - taken;
-          int avail = __popc(mk);
-          int rank = __popc(mk & lanemask_lt());
-          if (ok && rank < need) s_plan[taken + rank] = cid;
-          if (avail >= need) {
-            // last taken lane, then the next overlapping one in this batch
-            unsigned mm = mk;
-            for (int i = 0; i < need - 1; ++i) mm &= mm - 1;
-            int last = __ffs(mm) - 1;
-            unsigned rest = mk & ~((2u << last) - 1u);
-            if (rest) {
-              int nl = __ffs(rest) - 1;
-              uint64_t key = p.pair_key[ci + nl];
-              unsigned ob = (unsigned)(key & 0xffffffffu);
-              unsigned b = (ob & 0x80000000u) ? (ob & 0x7fffffffu) : ~ob;
-              Fnext = __uint_as_float(b);
-              fset = true;
-              ci += nl;  // resume at the next overlapping chunk
-            } else {
-              ci += last + 1;
-            }
-            taken = kStageChunks;
-          } else {
-            taken += avail;
-            ci += min(32, ce - ci);
-          }
-        }
-        if (!fset && ci < ce) {
-          uint64_t key = p.pair_key[ci];
-          unsigned ob = (unsigned)(key & 0xffffffffu);
-          unsigned b = (ob & 0x80000000u) ? (ob & 0x7fffffffu) : ~ob;
-          Fnext = __uint_as_float(b);
-        }
-        if (lane == 0) {
-          s_plan[kStageChunks] = taken;
-          s_F[0] = Fnext;
-        }
-      }
-      __syncthreads();
-      const int nplan = s_plan[kStageChunks];
-      const float F = s_F[0];
-      const float Fbatch = Fprev;  // every knot of this batch's particles lies at or beyond it
-      Fprev = F;
-      // ---------------------------------------------------------------- stage
-      for (int i = threadIdx.x; i < nplan * kChunk; i += blockDim.x) {
-        int c = s_plan[i / kChunk], r = i % kChunk;
-        int2 ch = __ldg(p.chunk + c);
-        if (r < ch.y) {
-          s_pos[i] = __ldg(p.pos + ch.x + r);
-          s_amp[i] = __ldg(p.amp + ch.x + r);
-          s_idx[i] = ch.x + r;
-        } else {
-          s_pos[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-          s_amp[i] = 0.f;
-          s_idx[i] = -1;
-        }
-      }
-      for (int c = threadIdx.x; c < nplan; c += blockDim.x) {
-        int cid = s_plan[c];
-        float4 lo = __ldg(p.chunk_lo + cid), hi = __ldg(p.chunk_hi + cid);
-        float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y), hz = 0.5f * (hi.z - lo.z);
-        s_sph[c] = make_float4(lo.x + hx, lo.y + hy, lo.z + hz, sqrtf(hx * hx + hy * hy + hz * hz) + q * lo.w);
-      }
-      __syncthreads();
-      if (__syncthreads_and(done ? 1 : 0)) break;
-      PT_END(0)
-
-      if (!done) {
-        PT_BEGIN
-        // ---------------------------------------- chunks this ray can meet
-        unsigned cmask = 0;
-        {
+    // the tile list is read 32 entries at a time; each lane keeps its
+    // entry's chunk, particle range and bound F for when the chunk is processed
+    int gcur = -64, g_cid = 0, g_first = 0, g_cnt = 0;
+    unsigned gmask = 0;
+    float g_F = 0.f;
+    const float oxh = o[0].hi, oyh = o[1].hi, ozh = o[2].hi, vxh = v[0].hi, vyh = v[1].hi, vzh = v[2].hi;
+    // next chunk of the tile list at or after `from` that can reach this ray
+    auto next_hit = [&](int from) -> int {
+      for (;;) {
+        if (from >= ce) return ce;
+        if (from < gcur || from >= gcur + 32) {
+          gcur = from;
+          const int idx = from + lane;
           bool hit = false;
-          if (lane < nplan) {
-            float4 sp = s_sph[lane];
-            float cx = sp.x - o[0].hi, cy = sp.y - o[1].hi, cz = sp.z - o[2].hi;
-            float t = cx * v[0].hi + cy * v[1].hi + cz * v[2].hi;
-            float wx = cx - t * v[0].hi, wy = cy - t * v[1].hi, wz = cz - t * v[2].hi;
-            float rr = sp.w + 1e-5f * (fabsf(t) + fabsf(cx) + fabsf(cy) + fabsf(cz) + 1e-2f);
-            hit = wx * wx + wy * wy + wz * wz <= rr * rr;
-          }
-          cmask = __ballot_sync(kFull, hit);
-        }
-        // ------------------------------------------------------ candidates
-        while (cmask) {
-          const int cidx = __ffs(cmask) - 1;
-          cmask &= cmask - 1;
-          const int i = cidx * kChunk + lane;
-          bool cand = false;
-          df tc = {0.f, 0.f};
-          float h = 0.f, d2 = 0.f, a = 0.f;
-          df wv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-          {
-            float4 P = s_pos[i];
-            h = P.w;
-            if (h > 0.f) {
-              ++st_tests;
-              float R = q * h;
-              float px_ = P.x - o[0].hi, py_ = P.y - o[1].hi, pz_ = P.z - o[2].hi;
-              float t = px_ * v[0].hi + py_ * v[1].hi + pz_ * v[2].hi;
-              float wx = px_ - t * v[0].hi, wy = py_ - t * v[1].hi, wz = pz_ - t * v[2].hi;
-              float d2f = wx * wx + wy * wy + wz * wz;
-              float tol = 4e-6f * (fabsf(t) + fabsf(px_) + fabsf(py_) + fabsf(pz_) + 1e-3f);
-              float Rt = R + tol;
-              if (d2f < Rt * Rt) {
-                // double-float: p = chi - o, t = p.v, w = p - t v
-                df pp[3];
-                float pc3[3] = {P.x, P.y, P.z};
-#pragma unroll
-                for (int k = 0; k < 3; ++k) pp[k] = df_add(df{pc3[k], 0.f}, df_neg(o[k]));
-                df tt = df_add(df_add(df_mul(pp[0], v[0]), df_mul(pp[1], v[1])), df_mul(pp[2], v[2]));
-                float dd = 0.f;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                  df w = df_add(pp[k], df_neg(df_mul(tt, v[k])));
-                  dd = fmaf(w.hi, w.hi, fmaf(2.f * w.hi, w.lo, dd));
-                  wv[k] = w;
-                }
-                float R2 = R * R;
-                if (dd < R2) {
-                  float ex = tt.hi + sqrtf(fmaxf(R2 - dd, 0.f));
-                  if (ex > t_near) {
-                    cand = true;
-                    tc = tt;
-                    d2 = dd;
-                    a = s_amp[i];
-                  }
-                }
-              }
+          if (idx < ce) {
+            g_cid = (int)__ldg(p.pair_val + idx);
+            const unsigned ob = (unsigned)(__ldg(p.pair_key + idx) & 0xffffffffu);
+            g_F = __uint_as_float((ob & 0x80000000u) ? (ob & 0x7fffffffu) : ~ob);
+            const float4 r = __ldg(p.chunk_rect + g_cid);
+            if (r.x <= pxf + 0.5f && r.z >= pxf - 0.5f && r.y <= pyf + 0.5f && r.w >= pyf - 0.5f) {
+              const float4 lo = __ldg(p.chunk_lo + g_cid), hi = __ldg(p.chunk_hi + g_cid);
+              const int2 chk = __ldg(p.chunk + g_cid);
+              g_first = chk.x;
+              g_cnt = chk.y;
+              const float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y), hz = 0.5f * (hi.z - lo.z);
+              const float rad = sqrtf(hx * hx + hy * hy + hz * hz) + q * lo.w;
+              const float cx = lo.x + hx - oxh, cy = lo.y + hy - oyh, cz = lo.z + hz - ozh;
+              const float t = cx * vxh + cy * vyh + cz * vzh;
+              const float wx = cx - t * vxh, wy = cy - t * vyh, wz = cz - t * vzh;
+              const float rr = rad + 1e-5f * (fabsf(t) + fabsf(cx) + fabsf(cy) + fabsf(cz) + 1e-2f);
+              hit = wx * wx + wy * wy + wz * wz <= rr * rr;
             }
           }
-          unsigned mk = __ballot_sync(kFull, cand);
-          if (!mk) continue;
-          int rank = __popc(mk & lanemask_lt());
-          int slot = n_tab + rank;
-          if (cand) {
-            if (slot < kCap) {
-              // table entry: nearest L entry (FP64 re-check near a midpoint)
-              float x = sqrtf(d2) / h * p.lam_scale;
-              int j = (int)floorf(x + 0.5f);
-              float fr = x - floorf(x);
-              if (fabsf(fr - 0.5f) < 2e-3f) {
-                // near a midpoint: decide in FP64 from the double-float components
-                double d2d = 0.0;
-                for (int k = 0; k < 3; ++k) {
-                  double wk = (double)wv[k].hi + (double)wv[k].lo;
-                  d2d += wk * wk;
-                }
-                double xd = sqrt(d2d) / (double)h * ((double)(p.n_lambda - 1) / (double)q);
-                j = (int)floor(xd + 0.5);
-              }
-              j = min(max(j, 0), p.n_lambda - 1);
-              T.tc_hi[slot] = tc.hi;
-              T.tc_lo[slot] = tc.lo;
-              T.hh[slot] = h;
-              T.cc[slot] = a / (h * h * h);
-              T.meta[slot] = j;
-              float2 th = __ldg(p.theta + j);
-              float tn = tc.hi + knot_sigma(K, m, th, 0) * h;
-              T.tnext[slot] = tn;
-              T.fst[slot] = Fbatch;
-              // a first knot before the processed part of the ray would mean the
-              // ordering bound was violated: report it
-              if (started && tn < Ta.hi - 1e-6f * fabsf(Ta.hi)) st_flags |= 8;
-              if (DBG && p.dbg_cands) {
-                long long ci2 = dbg_nc + rank;
-                if (ci2 < p.cand_cap) p.dbg_cands[dbg_row * p.cand_cap + ci2] = p.orig[s_idx[i]];
-              }
-            } else {
-              st_flags |= 1;
-            }
-          }
-          int added = __popc(mk);
-          st_cand += added;
-          dbg_nc += added;
-          new_cands += added;
-          n_tab = min(kCap, n_tab + added);
+          gmask = __ballot_sync(kFull, hit);
         }
-        st_maxtab = max(st_maxtab, n_tab);
-        __syncwarp();
-        PT_END(1)
+        const unsigned mk = gmask & (0xffffffffu << (from - gcur));
+        if (mk) return gcur + __ffs(mk) - 1;
+        from = gcur + 32;
+      }
+    };
 
-        // ------------------------------------------------------ windows
-        // process once enough knots are final, at the end of the stream, or
-        // when the table fills up
-        const bool go = !(F < __int_as_float(0x7f800000)) || new_cands >= kDefer || n_tab > kCap - 2 * kStage;
-        if (go) new_cands = 0;
-        while (go && !done) {
+    PT_BEGIN
+    int cur = next_hit(tr.x);
+    PT_END(0)
+    for (;;) {
+      const bool last = cur >= ce;
+      const int src = cur - gcur;  // this lane group holds entry `cur`
+      const float F = last ? kInf : __shfl_sync(kFull, g_F, src & 31);
+      const int room = nfree + (kCap - hwm);
+      if (last || nnk + 32 * KP1 > kNK || room < 32) {
+        PT_BEGIN
+        // ---- sort the new knots and merge them into the pending list
+        if (nnk > 0) {
+          const int rb = warp_radix_sort(T.nk0, T.nv0, T.nk1, T.nv1, nnk, T.rh);
+          const int na = npl - head;
+          const int nout = min(na + nnk, kPL);
+          if (na + nnk > kPL) st_flags |= 1;
+          warp_tile_merge((pb ? T.pk1 : T.pk0) + head, (pb ? T.pv1 : T.pv0) + head, na, rb ? T.nk1 : T.nk0,
+                          rb ? T.nv1 : T.nv0, nnk, pb ? T.pk0 : T.pk1, pb ? T.pv0 : T.pv1, nout, rb ? T.nk0 : T.nk1,
+                          rb ? T.nv0 : T.nv1);
+          pb ^= 1;
+          head = 0;
+          npl = nout;
+          nnk = 0;
+        }
+        PT_END(2)
+
+        // ---- windows: every pending knot below F is final
+        while (!done) {
           PT_BEGIN
-          // lcap: longest window for which FP32 round-off stays small relative to
-          // every particle with a knot in it -- gamma h for an active particle; for
-          // a pending one, the window may run up to its first knot or gamma h
-          // beyond Ta, whichever is farther
-          int n_act = 0, n_fin = 0;
-          float tmin = __int_as_float(0x7f800000), lcap = __int_as_float(0x7f800000);
-          for (int e = lane; e < n_tab; e += 32) {
-            int kn = meta_kn(T.meta[e]);
-            if (kn > K) {
-              ++n_fin;
-              continue;
-            }
-            float tn = T.tnext[e], gh = p.window_h * T.hh[e];
-            tmin = fminf(tmin, tn);
-            if (kn >= 1) {
-              ++n_act;
-              lcap = fminf(lcap, gh);
-            } else {
-              lcap = fminf(lcap, fmaxf(tn - Ta.hi, gh));
-            }
-          }
-          n_act = warp_sum_i(n_act);
-          n_fin = warp_sum_i(n_fin);
-          st_maxact = max(st_maxact, n_act);
-          tmin = warp_min(tmin);
-          lcap = warp_min(lcap);
-          PT_END(2)
-          PT_BEGIN
-          if (tmin == __int_as_float(0x7f800000)) {
-            n_tab = 0;
-            break;
-          }
+          const float* PK = pb ? T.pk1 : T.pk0;
+          const int* PV = pb ? T.pv1 : T.pv0;
           bool fresh = false;
           if (n_act == 0) {
-            if (!(tmin < F)) break;
-            // exact position of the first pending knot
-            int ebest = -1;
-            for (int e0 = 0; e0 < n_tab; e0 += 32) {
-              int e = e0 + lane;
-              bool hitm = e < n_tab && meta_kn(T.meta[e]) <= K && T.tnext[e] == tmin;
-              unsigned who = __ballot_sync(kFull, hitm);
-              if (who) {
-                ebest = e0 + __ffs(who) - 1;
-                break;
-              }
-            }
-            if (ebest < 0) {  // cannot happen: tmin is one of the entries' values
-              st_flags |= 4;
-              done = true;
-              n_tab = 0;
-              break;
-            }
-            int mt = T.meta[ebest];
-            float2 th = __ldg(p.theta + meta_j(mt));
-            float sgm = knot_sigma(K, m, th, meta_kn(mt));
-            df kp = df{T.tc_hi[ebest], T.tc_lo[ebest]};
+            // the field is zero at Ta: restart at the first pending knot
+            if (head >= npl) break;
+            if (!(PK[head] < F)) break;
+            const int v0 = PV[head], e0 = v0 & 0xffff, k0 = v0 >> 16;
+            const float sg = knot_sigma(K, m, __ldg(p.theta + T.jj[e0]), k0);
+            df kp = df{T.tc_hi[e0], T.tc_lo[e0]};
             {
-              float pr = sgm * T.hh[ebest];
-              float pe = fmaf(sgm, T.hh[ebest], -pr);
+              const float pr = sg * T.hh[e0];
+              const float pe = fmaf(sg, T.hh[e0], -pr);
               kp = df_add(kp, df{pr, pe});
             }
             if (started) {
@@ -774,16 +826,15 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
               df gl = df_add(kp, df_neg(Ta));
               float L = gl.hi + gl.lo - from;
               if (L > 0.f) {
-                float z0[D + 1];
+                Poly<D> z0;
 #pragma unroll
-                for (int d = 0; d <= D; ++d) z0[d] = 0.f;
-                float tl = 0.f, Cg[3] = {0.f, 0.f, 0.f};
-                composite_cell<D>(z0, L, tf_cell(tfc, 0.f), tfc, tl, Cg);
+                for (int d = 0; d <= D; ++d) z0.c[d] = 0.f;
+                const Acc g = composite_piece_v<D>(z0, L, tfc, Acc{0.f, 0.f, 0.f, 0.f});
                 float w = __expf(-tau_ray);
-                col[0] += w * Cg[0];
-                col[1] += w * Cg[1];
-                col[2] += w * Cg[2];
-                tau_ray += tl;
+                col[0] += w * g.r;
+                col[1] += w * g.g;
+                col[2] += w * g.b;
+                tau_ray += g.tau;
               }
               if (DBG && p.dbg_field && lane == 0 && dbg_np < p.field_cap) {
                 double* fo = p.dbg_field + ((size_t)dbg_row * p.field_cap + dbg_np) * (D + 3);
@@ -801,271 +852,169 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
 #pragma unroll
             for (int d = 0; d <= D; ++d) carry[d] = (S)0;
           }
-          // a window ends at the bound F, and spans at most lcap (above); at a
-          // fresh start the pending particle at Ta bounds it by its own gamma h
-          float Uh_lim = lcap;
-          if (fresh) {
-            float l2 = __int_as_float(0x7f800000);
-            for (int e = lane; e < n_tab; e += 32) {
-              int kn = meta_kn(T.meta[e]);
-              if (kn > K) continue;
-              float tn = T.tnext[e], gh = p.window_h * T.hh[e];
-              l2 = fminf(l2, fmaxf(tn - Ta.hi, gh));
-            }
-            Uh_lim = warp_min(l2);
-          }
-          const bool finF = F < __int_as_float(0x7f800000);
-          float Ulim = finF ? ((F - Ta.hi) - Ta.lo) : __int_as_float(0x7f800000);
-          const bool capped = Uh_lim < Ulim;
-          if (capped) {
-            Ulim = Uh_lim;
-            ++st_capped;
-          }
-          // prefilter on the approximate next-knot position (absolute FP32)
-          const float Wend = fminf(F, Ta.hi + Ulim);
-          const float Fpre = Wend + 1e-3f * fabsf(Wend) + 1e-30f;
-          int cnt = 0;
-          float umax = 0.f;
-          for (int e = lane; e < n_tab; e += 32) {
-            if (!(T.fst[e] < Fpre)) break;  // this and all later entries start beyond the window
-            int mt = T.meta[e], kn = meta_kn(mt);
-            if (kn > K || !(T.tnext[e] < Fpre)) continue;
-            float2 th = __ldg(p.theta + meta_j(mt));
-            float base = (T.tc_hi[e] - Ta.hi) + (T.tc_lo[e] - Ta.lo), hh = T.hh[e];
-            for (int k = kn; k <= K; ++k) {
-              float u = fmaf(knot_sigma(K, m, th, k), hh, base);
-              if (!(u < Ulim)) break;
-              ++cnt;
-              umax = fmaxf(umax, u);
+          // window end (relative to Ta): the bound F, and gamma times the
+          // lower edge of the smallest octave of h among the active particles
+          float U = kInf;
+          if (F < kInf) U = (F - Ta.hi) - Ta.lo;
+          bool capped = false;
+          if (n_act > 0) {
+            // smallest occupied bin (4 per lane)
+            const int4 c4 = *(const int4*)(T.lvl + 4 * lane);
+            const int mine = c4.x > 0 ? 0 : (c4.y > 0 ? 1 : (c4.z > 0 ? 2 : (c4.w > 0 ? 3 : 4)));
+            const unsigned mb = __ballot_sync(kFull, mine < 4);
+            const int l0 = mb ? __ffs(mb) - 1 : 31;
+            const int lv = mb ? 4 * l0 + __shfl_sync(kFull, mine, l0) : kLevels - 1;
+            const float lim = gam * level_lo(lv);
+            if (lim < U) {
+              U = lim;
+              capped = true;
             }
           }
-          cnt = warp_sum_i(cnt);
-          umax = warp_max(umax);
-          // no knot below the bound: wait for more particles, unless the window
-          // was capped -- then the current polynomial alone spans it
-          if (cnt == 0 && !capped) break;
-          // choose the window: all knots below Ulim, or a bucket prefix of them
-          float Ub = Ulim, Uh = 0.f;
-          int bstar = kNb;
-          bool by_bucket = false;
-          if (cnt > kW) {
-            by_bucket = true;
-            Uh = umax > 0.f ? umax : 1e-30f;
-            bool fixed = false;
-            for (int zoom = 0; zoom < 6 && !fixed; ++zoom) {
-              for (int b = lane; b < kNb; b += 32) T.hist[b] = 0;
-              __syncwarp();
-              float sc = kNb / Uh;
-              for (int e = lane; e < n_tab; e += 32) {
-                if (!(T.fst[e] < Fpre)) break;
-                int mt = T.meta[e], kn = meta_kn(mt);
-                if (kn > K || !(T.tnext[e] < Fpre)) continue;
-                float2 th = __ldg(p.theta + meta_j(mt));
-                float base = (T.tc_hi[e] - Ta.hi) + (T.tc_lo[e] - Ta.lo), hh = T.hh[e];
-                for (int k = kn; k <= K; ++k) {
-                  float u = fmaf(knot_sigma(K, m, th, k), hh, base);
-                  if (!(u < Ulim)) break;
-                  int b = min(kNb - 1, max(0, (int)fminf(u * sc, (float)kNb)));
-                  if (u <= Uh) atomicAdd(&T.hist[b], 1);
-                }
-              }
-              __syncwarp();
-              // inclusive scan over the 64 buckets (2 per lane)
-              int h0 = T.hist[2 * lane], h1 = T.hist[2 * lane + 1];
-              int s2 = h0 + h1, x = s2;
-#pragma unroll
-              for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                int y = __shfl_up_sync(kFull, x, o2);
-                if (lane >= o2) x += y;
-              }
-              int ex = x - s2;  // count in buckets < 2 lane
-              // largest b with count(bucket < b) <= kW
-              int bl = -1;
-              if (ex + h0 <= kW) bl = 2 * lane + 1;
-              if (ex + h0 + h1 <= kW) bl = 2 * lane + 2;
-              if (ex > kW) bl = -1;
-              int bbest = bl;
-#pragma unroll
-              for (int o2 = 16; o2; o2 >>= 1) bbest = max(bbest, __shfl_xor_sync(kFull, bbest, o2));
-              if (bbest >= 1) {
-                bstar = bbest;
-                fixed = true;
-              } else {
-                Uh = Uh / kNb;  // first bucket too full: zoom into it
-              }
-              __syncwarp();
-            }
-            if (!fixed) {
-              st_flags |= 2;
-              bstar = 1;
-            }
-            Ub = (bstar >= kNb) ? Uh : Uh * ((float)bstar / kNb);
+          // the window is a prefix of the pending list
+          const int nb_ = warp_count_below(PK, head, npl, Ta.hi + U);
+          int nc = min(nb_, kW);
+          if (nc < nb_) {  // full: it ends at the first knot left out
+            U = (PK[head + nc] - Ta.hi) - Ta.lo;
+            capped = false;
           }
-
           PT_END(3)
+          PT_BEGIN
+          // load it lane-major (lane l holds knots l*kKpl ... l*kKpl+kKpl-1,
+          // kept in shared memory at r * 32 + l), positions relative to Ta
+          // from the double-float centre
+          float* su = T.wdl + kW * D;
+          int* sv = (int*)(su + kW);
+          float cap2 = kInf;
+#pragma unroll 2
+          for (int r = 0; r < kKpl; ++r) {
+            const int i = lane * kKpl + r;
+            int vv = -1;
+            float u = 0.f;
+            if (i < nc) {
+              vv = PV[head + i];
+              const int e = vv & 0xffff, k = vv >> 16;
+              const float hh = T.hh[e], c = T.cc[e];
+              const int j = T.jj[e];
+              const float base = (T.tc_hi[e] - Ta.hi) + (T.tc_lo[e] - Ta.lo);
+              u = fmaf(knot_sigma(K, m, __ldg(p.theta + j), k), hh, base);
+              float dl[D];
+              knot_delta<D>(p, j, hh, c, k, dl);
+#pragma unroll
+              for (int d = 0; d < D; ++d) T.wdl[(r * D + d) * 32 + lane] = dl[d];
+              // a particle starting inside the window bounds it by its own
+              // gamma h, or by its first knot when that lies farther
+              if (k == 0) cap2 = fminf(cap2, fmaxf(u, gam * hh));
+            }
+            su[r * 32 + lane] = u;
+            sv[r * 32 + lane] = vv;
+          }
+          cap2 = warp_min(cap2);
+          if (cap2 < U) {
+            U = cap2;
+            capped = true;
+            int first_out = kKpl;
+#pragma unroll 1
+            for (int r = 0; r < kKpl; ++r)
+              if (sv[r * 32 + lane] >= 0 && !(su[r * 32 + lane] < U)) {
+                first_out = r;
+                break;
+              }
+            const unsigned lm = __ballot_sync(kFull, first_out < kKpl);
+            if (lm) {
+              const int l0 = __ffs(lm) - 1;
+              const int r0 = __shfl_sync(kFull, first_out, l0);
+              nc = min(nc, l0 * kKpl + r0);
+            }
+          }
+          if (nc == 0 && !capped) {
+            PT_END(5)
+            break;  // nothing final below F: wait for more particles
+          }
+          const int cnt_l = min(max(nc - lane * kKpl, 0), kKpl);  // this lane's knots (a prefix)
+          int nf = 0, nl = 0;
+          float umax = 0.f;
+#pragma unroll 1
+          for (int r = 0; r < cnt_l; ++r) {
+            const int k = sv[r * 32 + lane] >> 16;
+            nf += k == 0;
+            nl += k == K;
+            umax = fmaxf(umax, su[r * 32 + lane]);
+          }
+          nf = warp_sum_i(nf);
+          nl = warp_sum_i(nl);
+          umax = warp_max(umax);
+          const int act_after = n_act + nf - nl;
+          // no particle is active after the window's last knot: the field is
+          // identically zero from there on, so the window ends at that knot
+          const bool final_w = nc > 0 && act_after == 0;
+          float Uend = final_w ? fminf(umax, U) : U;
+          if (!(Uend < kInf)) {
+            st_flags |= 4;
+            Uend = umax;
+          }
+          Uend = fmaxf(Uend, 0.f);
+#pragma unroll 1
+          for (int r = 0; r < kKpl; ++r)
+            su[r * 32 + lane] = r < cnt_l ? fminf(fmaxf(su[r * 32 + lane], 0.f), Uend) : Uend;
+          PT_END(5)
+
           PT_BEGIN
           // anchor: exact coefficients of the field at Ta
           S A[D + 1];
-          bool do_anchor = p.anchor_every > 0 && (fresh || (win_count % p.anchor_every) == 0);
-          if (fresh) {
-#pragma unroll
-            for (int d = 0; d <= D; ++d) A[d] = (S)0;
-          } else if (do_anchor) {
+          const bool do_anchor = p.anchor_every > 0 && !fresh && (win_count % p.anchor_every) == 0;
+          if (do_anchor) {
             float acc[D + 1];
 #pragma unroll
             for (int d = 0; d <= D; ++d) acc[d] = 0.f;
-            for (int e = lane; e < n_tab; e += 32) {
-              if (!(T.fst[e] < Ta.hi + 1e-6f * fabsf(Ta.hi))) break;  // later entries have not started
-              int kn = meta_kn(T.meta[e]);
-              if (kn < 1 || kn > K) continue;
-              float Ae[D + 1];
-              entry_piece_at<D>(p, T, e, Ta, Ae);
-#pragma unroll
-              for (int d = 0; d <= D; ++d) acc[d] += Ae[d];
-            }
+            active_pass<D>(p, T, nal, nfree, Ta, true, acc);
 #pragma unroll
             for (int d = 0; d <= D; ++d) A[d] = (S)warp_sum(acc[d]);
           } else {
 #pragma unroll
-            for (int d = 0; d <= D; ++d) A[d] = carry[d];
+            for (int d = 0; d <= D; ++d) A[d] = fresh ? (S)0 : carry[d];
           }
           PT_END(4)
+
           PT_BEGIN
-          // emission of the window's knots
-          if (lane == 0) T.misc[0] = 0;
-          __syncwarp();
-          const float scb = by_bucket ? kNb / Uh : 0.f;
-          int act_after = 0;  // particles still active after this window's knots
-          for (int e = lane; e < n_tab; e += 32) {
-            if (!(T.fst[e] < Fpre)) break;
-            int mt = T.meta[e], kn = meta_kn(mt);
-            if (kn > K) continue;
-            if (!(T.tnext[e] < Fpre)) {
-              act_after += kn >= 1;
-              continue;
-            }
-            float2 th = __ldg(p.theta + meta_j(mt));
-            float base = (T.tc_hi[e] - Ta.hi) + (T.tc_lo[e] - Ta.lo), hh = T.hh[e];
-            int k = kn;
-            for (; k <= K; ++k) {
-              float u = fmaf(knot_sigma(K, m, th, k), hh, base);
-              bool take;
-              if (by_bucket) take = u < Ulim && u <= Uh && min(kNb - 1, max(0, (int)fminf(u * scb, (float)kNb))) < bstar;
-              else take = u < Ulim;
-              if (!take) break;
-              int pos = atomicAdd(&T.misc[0], 1);
-              if (pos < kW) {
-                T.wk[pos] = fmaxf(u, 0.f);
-                T.wv[pos] = e | (k << 16);
-              }
-            }
-            if (k != kn) {
-              T.meta[e] = meta_j(mt) | (k << 16);
-              T.tnext[e] = k <= K ? T.tc_hi[e] + knot_sigma(K, m, th, k) * hh : __int_as_float(0x7f800000);
-            }
-            act_after += (k >= 1 && k <= K);
+          // mark the window's knots processed; active list and octave counts
+#pragma unroll 1
+          for (int r = 0; r < kKpl; ++r) {
+            const bool valid = r < cnt_l;
+            const int vv = sv[r * 32 + lane];
+            const int e = vv & 0xffff, k = vv >> 16;
+            if (valid) atomicMax(T.kn + e, k + 1);
+            const bool first = valid && k == 0;
+            const unsigned mm = __ballot_sync(kFull, first);
+            if (first) T.act[nal + __popc(mm & lanemask_lt())] = e;
+            nal += __popc(mm);
+            if (valid && (k == 0 || k == K)) atomicAdd(&T.lvl[h_level(T.hh[e])], k == 0 ? 1 : -1);
           }
-          act_after = warp_sum_i(act_after);
           __syncwarp();
-          int nwin = min(T.misc[0], kW);
-          if (T.misc[0] > kW) st_flags |= 2;
-          // no particle is active after the window's last knot: the field is
-          // identically zero from there on, so the window ends at that knot (a
-          // later knot starts a new segment; the gap is composited only then)
-          const bool final_w = nwin > 0 && act_after == 0;
-          my_knots += nwin;
+          n_act = act_after;
+          st_maxact = max(st_maxact, n_act);
+          head += nc;
+          my_knots += nc;
           ++st_win;
           ++win_count;
-          PT_END(5)
-          PT_BEGIN
-          // bucket sort of the window by position
-          {
-            float wmax = 0.f;
-            for (int i = lane; i < nwin; i += 32) wmax = fmaxf(wmax, T.wk[i]);
-            wmax = warp_max(wmax);
-            float sc = wmax > 0.f ? kNb / wmax : 0.f;
-            for (int b = lane; b < kNb; b += 32) T.hist[b] = 0;
-            __syncwarp();
-            int bk[kKpl], rk[kKpl];
-#pragma unroll
-            for (int r = 0; r < kKpl; ++r) {
-              int i = lane + 32 * r;
-              if (i < nwin) {
-                bk[r] = min(kNb - 1, max(0, (int)fminf(T.wk[i] * sc, (float)kNb)));
-                rk[r] = atomicAdd(&T.hist[bk[r]], 1);
-              }
-            }
-            __syncwarp();
-            int h0 = T.hist[2 * lane], h1 = T.hist[2 * lane + 1];
-            int s2 = h0 + h1, x = s2;
-#pragma unroll
-            for (int o2 = 1; o2 < 32; o2 <<= 1) {
-              int y = __shfl_up_sync(kFull, x, o2);
-              if (lane >= o2) x += y;
-            }
-            int ex = x - s2;
-            T.hist[kNb + 2 * lane] = ex;
-            T.hist[kNb + 2 * lane + 1] = ex + h0;
-            __syncwarp();
-#pragma unroll
-            for (int r = 0; r < kKpl; ++r) {
-              int i = lane + 32 * r;
-              if (i < nwin) {
-                int dst = T.hist[kNb + bk[r]] + rk[r];
-                T.sk[dst] = T.wk[i];
-                T.sv[dst] = T.wv[i];
-              }
-            }
-            __syncwarp();
-            // insertion sort inside the two buckets of this lane
-#pragma unroll
-            for (int bb = 0; bb < 2; ++bb) {
-              int b = 2 * lane + bb;
-              int lo = T.hist[kNb + b], n = T.hist[b];
-              for (int i = lo + 1; i < lo + n; ++i) {
-                float kk = T.sk[i];
-                int vv = T.sv[i];
-                int jj = i - 1;
-                while (jj >= lo && T.sk[jj] > kk) {
-                  T.sk[jj + 1] = T.sk[jj];
-                  T.sv[jj + 1] = T.sv[jj];
-                  --jj;
-                }
-                T.sk[jj + 1] = kk;
-                T.sv[jj + 1] = vv;
-              }
-            }
-            __syncwarp();
-          }
+          if (capped) ++st_capped;
           PT_END(6)
+
           PT_BEGIN
+          const float ufirst = su[lane];
           // ---- segmented scan of the difference coefficients (Sec. 2)
-          const float Uend = final_w ? (nwin > 0 ? T.sk[nwin - 1] : 0.f) : Ub;
-          float ul[kKpl];
-          int pl[kKpl];
-#pragma unroll
-          for (int r = 0; r < kKpl; ++r) {
-            int g = lane * kKpl + r;
-            ul[r] = g < nwin ? T.sk[g] : Uend;
-            pl[r] = g < nwin ? T.sv[g] : -1;
-          }
           S agg[D + 1];
 #pragma unroll
           for (int d = 0; d <= D; ++d) agg[d] = (S)0;
-          bool has = false;
-          float ufirst = ul[0], ulast = ul[0];
+          float ulast = ufirst;
+#pragma unroll 1
+          for (int r = 0; r < cnt_l; ++r) {
+            const float ur = su[r * 32 + lane];
+            if (r > 0) taylor_shift<D, S>(agg, (S)(ur - ulast));
 #pragma unroll
-          for (int r = 0; r < kKpl; ++r) {
-            if (pl[r] >= 0) {
-              float dl[D + 1];
-              knot_delta<D>(p, T, pl[r] & 0xffff, pl[r] >> 16, dl);
-              if (has) taylor_shift<D, S>(agg, (S)(ul[r] - ulast));
-#pragma unroll
-              for (int d = 1; d <= D; ++d) agg[d] += (S)dl[d];
-              ulast = ul[r];
-              has = true;
-            }
+            for (int d = 1; d <= D; ++d) agg[d] += (S)T.wdl[(r * D + d - 1) * 32 + lane];
+            ulast = ur;
           }
+          const bool has = cnt_l > 0;
           // inclusive warp scan of (agg, ulast, has)
           S sa[D + 1];
 #pragma unroll
@@ -1111,40 +1060,24 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             for (int d = 0; d <= D; ++d) P[d] += pa[d];
           }
           // next lane's first knot (piece end for this lane's last knot)
-          float unext = __shfl_down_sync(kFull, ul[0], 1);
+          float unext = __shfl_down_sync(kFull, ufirst, 1);
           if (lane == 31) unext = Uend;
-          // ---- composite this lane's pieces
-          float tau_l = 0.f, Cl[3] = {0.f, 0.f, 0.f};
+          const float ulane_end = cnt_l == kKpl ? unext : Uend;
+          // ---- composite this lane's pieces: lane 0 first takes the leading
+          // piece [0, u_0] (the whole window if it has no knot) with the
+          // window's incoming polynomial, then every lane one piece per knot
+          Acc acc_l{0.f, 0.f, 0.f, 0.f};
           const df rs = df_add(t_start, df_neg(Ta));
           const float ystart = rs.hi + rs.lo;  // window-relative start of compositing
-          if (lane == 0) {
-            // leading piece [0, u_0] (or the whole window if it has no knot) with the anchor polynomial
-            float Pf[D + 1];
-#pragma unroll
-            for (int d = 0; d <= D; ++d) Pf[d] = (float)A[d];
-            float a0 = fmaxf(0.f, ystart), b0 = ul[0];
-            if (b0 > a0) {
-              if (a0 > 0.f) taylor_shift<D, float>(Pf, a0);
-              composite_piece<D>(Pf, b0 - a0, tfc, tau_l, Cl);
-            }
-            if (DBG && p.dbg_field && ul[0] > 0.f && dbg_np < p.field_cap) {
-              double* fo = p.dbg_field + ((size_t)dbg_row * p.field_cap + dbg_np) * (D + 3);
-              fo[0] = df_to_double(Ta);
-              fo[1] = df_to_double(Ta) + (double)ul[0];
-              for (int d = 0; d <= D; ++d) fo[2 + d] = (double)A[d];
-            }
-          }
-          // count pieces per lane for debug output ordering
           long long dbg_base = 0, npieces = 0;
           if (DBG) {
             int cntp = 0;
-#pragma unroll
-            for (int r = 0; r < kKpl; ++r) {
-              if (pl[r] < 0) continue;
-              float en = (r + 1 < kKpl && pl[r + 1] >= 0) ? ul[r + 1] : (r + 1 < kKpl ? Uend : unext);
-              if (en > ul[r]) ++cntp;
+#pragma unroll 1
+            for (int r = 0; r < cnt_l; ++r) {
+              const float en = r + 1 < cnt_l ? su[(r + 1) * 32 + lane] : ulane_end;
+              if (en > su[r * 32 + lane]) ++cntp;
             }
-            int lead = (lane == 0 && ul[0] > 0.f) ? 1 : 0;
+            int lead = (lane == 0 && ufirst > 0.f) ? 1 : 0;
             int tot = cntp + lead, xx = tot;
 #pragma unroll
             for (int o2 = 1; o2 < 32; o2 <<= 1) {
@@ -1155,37 +1088,38 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             npieces = __shfl_sync(kFull, xx, 31);
           }
           float lastu = ufirst;
-          bool any = false;
+#pragma unroll 1
+          for (int sp = lane == 0 ? -1 : 0; sp < cnt_l; ++sp) {
+            Poly<D> Pf;
+            float ua, ub;
+            if (sp < 0) {
 #pragma unroll
-          for (int r = 0; r < kKpl; ++r) {
-            if (pl[r] < 0) continue;
-            if (any) taylor_shift<D, S>(P, (S)(ul[r] - lastu));
-            float dl[D + 1];
-            knot_delta<D>(p, T, pl[r] & 0xffff, pl[r] >> 16, dl);
+              for (int d = 0; d <= D; ++d) Pf.c[d] = (float)A[d];
+              ua = 0.f;
+              ub = ufirst;
+            } else {
+              ua = su[sp * 32 + lane];
+              if (sp > 0) taylor_shift<D, S>(P, (S)(ua - lastu));
 #pragma unroll
-            for (int d = 1; d <= D; ++d) P[d] += (S)dl[d];
-            any = true;
-            lastu = ul[r];
-            float en = (r + 1 < kKpl && pl[r + 1] >= 0) ? ul[r + 1] : (r + 1 < kKpl ? Uend : unext);
-            float Pf[D + 1];
+              for (int d = 1; d <= D; ++d) P[d] += (S)T.wdl[(sp * D + d - 1) * 32 + lane];
+              lastu = ua;
+              ub = sp + 1 < cnt_l ? su[(sp + 1) * 32 + lane] : ulane_end;
 #pragma unroll
-            for (int d = 0; d <= D; ++d) Pf[d] = (float)P[d];
-            float a0 = fmaxf(ul[r], ystart);
-            if (en > a0) {
-              float Q[D + 1];
-#pragma unroll
-              for (int d = 0; d <= D; ++d) Q[d] = Pf[d];
-              if (a0 > ul[r]) taylor_shift<D, float>(Q, a0 - ul[r]);
-              composite_piece<D>(Q, en - a0, tfc, tau_l, Cl);
+              for (int d = 0; d <= D; ++d) Pf.c[d] = (float)P[d];
             }
-            if (DBG && p.dbg_field && en > ul[r]) {
-              if (dbg_base < p.field_cap) {
-                double* fo = p.dbg_field + ((size_t)dbg_row * p.field_cap + dbg_base) * (D + 3);
-                fo[0] = df_to_double(Ta) + (double)ul[r];
-                fo[1] = df_to_double(Ta) + (double)en;
-                for (int d = 0; d <= D; ++d) fo[2 + d] = (double)Pf[d];
+            const float a0 = fmaxf(ua, ystart);
+            if (ub > a0) {
+              if (a0 > ua) taylor_shift<D, float>(Pf.c, a0 - ua);
+              acc_l = composite_piece_v<D>(Pf, ub - a0, tfc, acc_l);
+            }
+            if (DBG && p.dbg_field && ub > ua) {
+              const long long row = sp < 0 ? dbg_np : dbg_base++;
+              if (row < p.field_cap) {
+                double* fo = p.dbg_field + ((size_t)dbg_row * p.field_cap + row) * (D + 3);
+                fo[0] = df_to_double(Ta) + (double)ua;
+                fo[1] = df_to_double(Ta) + (double)ub;
+                for (int d = 0; d <= D; ++d) fo[2 + d] = sp < 0 ? (double)A[d] : (double)P[d];
               }
-              ++dbg_base;
             }
           }
           if (DBG) dbg_np += npieces;
@@ -1194,85 +1128,159 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             S cpy[D + 1];
 #pragma unroll
             for (int d = 0; d <= D; ++d) cpy[d] = P[d];
-            if (any) taylor_shift<D, S>(cpy, (S)(Uend - lastu));
-            unsigned anym = __ballot_sync(kFull, any);
-            int lastlane = anym ? 31 - __clz(anym) : 0;
+            if (has) taylor_shift<D, S>(cpy, (S)(Uend - lastu));
+            unsigned anym = __ballot_sync(kFull, has);
+            if (anym) {
+              int lastlane = 31 - __clz(anym);
 #pragma unroll
-            for (int d = 0; d <= D; ++d) carry[d] = __shfl_sync(kFull, cpy[d], lastlane);
+              for (int d = 0; d <= D; ++d) carry[d] = __shfl_sync(kFull, cpy[d], lastlane);
+            } else {
+              // no knot in the window: the anchor polynomial spans it
+#pragma unroll
+              for (int d = 0; d <= D; ++d) carry[d] = A[d];
+              taylor_shift<D, S>(carry, (S)Uend);
+            }
           }
           // combine lanes: transmittance as accumulated optical depth
-          float tx = tau_l;
+          float tx = acc_l.tau;
 #pragma unroll
           for (int o2 = 1; o2 < 32; o2 <<= 1) {
             float y = __shfl_up_sync(kFull, tx, o2);
             if (lane >= o2) tx += y;
           }
-          float tex = tx - tau_l;
+          float tex = tx - acc_l.tau;
           float w = __expf(-(tau_ray + tex));
-          float c0 = warp_sum(w * Cl[0]), c1 = warp_sum(w * Cl[1]), c2 = warp_sum(w * Cl[2]);
+          float c0 = warp_sum(w * acc_l.r), c1 = warp_sum(w * acc_l.g), c2 = warp_sum(w * acc_l.b);
           col[0] += c0;
           col[1] += c1;
           col[2] += c2;
           tau_ray += __shfl_sync(kFull, tx, 31);
           // advance
           Ta = df_add(Ta, df{Uend, 0.f});
+          PT_END(7)
           if (p.tau_ert > 0.f && tau_ray > p.tau_ert) {
             done = true;
-            n_tab = 0;
             break;
           }
-          PT_END(7)
-          PT_BEGIN
-          // compact the table when a quarter was finished at the window start
-          {
-            if (n_fin * 4 >= n_tab || final_w) {
-              int wr = 0;
-              for (int b0 = 0; b0 < n_tab; b0 += 32) {
-                int e = b0 + lane;
-                bool keep = e < n_tab && meta_kn(T.meta[e]) <= K;
-                float a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0, a7 = 0;
-                int a6 = 0;
-                if (keep) {
-                  a1 = T.tc_hi[e];
-                  a2 = T.tc_lo[e];
-                  a3 = T.hh[e];
-                  a4 = T.cc[e];
-                  a5 = T.tnext[e];
-                  a6 = T.meta[e];
-                  a7 = T.fst[e];
-                }
-                unsigned km = __ballot_sync(kFull, keep);
-                __syncwarp();
-                if (keep) {
-                  int d = wr + __popc(km & lanemask_lt());
-                  T.tc_hi[d] = a1;
-                  T.tc_lo[d] = a2;
-                  T.hh[d] = a3;
-                  T.cc[d] = a4;
-                  T.tnext[d] = a5;
-                  T.meta[d] = a6;
-                  T.fst[d] = a7;
-                }
-                wr += __popc(km);
-                __syncwarp();
-              }
-              n_tab = wr;
-            }
-          }
-          PT_END(8)
-          if (final_w && n_tab == 0) break;
+        }
+        if (done) break;
+        if (nfree + (kCap - hwm) < 32) {
+          // reclaim the slots of finished particles
+          float dummy[D + 1];
+          active_pass<D>(p, T, nal, nfree, Ta, false, dummy);
         }
       }
-      if (nplan == 0) break;
+      if (last) break;
+
+      // ------------------------------------------------ candidates of one chunk
+      PT_BEGIN
+      {
+        const int ch_first = __shfl_sync(kFull, g_first, src & 31);
+        const int ch_cnt = __shfl_sync(kFull, g_cnt, src & 31);
+        bool cand = false;
+        df tc = {0.f, 0.f};
+        float h = 0.f, d2 = 0.f, a = 0.f;
+        df wv[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        const int pidx = ch_first + lane;
+        if (lane < ch_cnt) {
+          const float4 P = __ldg(p.pos + pidx);
+          h = P.w;
+          if (h > 0.f) {
+            ++st_tests;
+            const float R = q * h;
+            const float px_ = P.x - o[0].hi, py_ = P.y - o[1].hi, pz_ = P.z - o[2].hi;
+            const float t = px_ * v[0].hi + py_ * v[1].hi + pz_ * v[2].hi;
+            const float wx = px_ - t * v[0].hi, wy = py_ - t * v[1].hi, wz = pz_ - t * v[2].hi;
+            const float d2f = wx * wx + wy * wy + wz * wz;
+            const float tol = 4e-6f * (fabsf(t) + fabsf(px_) + fabsf(py_) + fabsf(pz_) + 1e-3f);
+            const float Rt = R + tol;
+            if (d2f < Rt * Rt) {
+              // double-float: p = chi - o, t = p.v, w = p - t v
+              df pp[3];
+              const float pc3[3] = {P.x, P.y, P.z};
+#pragma unroll
+              for (int k = 0; k < 3; ++k) pp[k] = df_add(df{pc3[k], 0.f}, df_neg(o[k]));
+              const df tt = df_add(df_add(df_mul(pp[0], v[0]), df_mul(pp[1], v[1])), df_mul(pp[2], v[2]));
+              float dd = 0.f;
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                df w = df_add(pp[k], df_neg(df_mul(tt, v[k])));
+                dd = fmaf(w.hi, w.hi, fmaf(2.f * w.hi, w.lo, dd));
+                wv[k] = w;
+              }
+              const float R2 = R * R;
+              if (dd < R2) {
+                const float ex = tt.hi + sqrtf(fmaxf(R2 - dd, 0.f));
+                if (ex > t_near) {
+                  cand = true;
+                  tc = tt;
+                  d2 = dd;
+                  a = __ldg(p.amp + pidx);
+                }
+              }
+            }
+          }
+        }
+        const unsigned mk = __ballot_sync(kFull, cand);
+        if (mk) {
+          const int n_new = __popc(mk);
+          const int rank = __popc(mk & lanemask_lt());
+          const int from_free = min(n_new, nfree);
+          const int n_store = min(n_new, from_free + (kCap - hwm));
+          if (n_store < n_new) st_flags |= 1;
+          if (cand && rank < n_store) {
+            const int e = rank < from_free ? T.fre[nfree - 1 - rank] : hwm + (rank - from_free);
+            // nearest Lambda entry (FP64 re-check near a midpoint)
+            const float x = sqrtf(d2) / h * p.lam_scale;
+            int j = (int)floorf(x + 0.5f);
+            const float fr = x - floorf(x);
+            if (fabsf(fr - 0.5f) < 2e-3f) j = nearest_entry_fp64(wv, h, p.n_lambda, q);
+            j = min(max(j, 0), p.n_lambda - 1);
+            T.tc_hi[e] = tc.hi;
+            T.tc_lo[e] = tc.lo;
+            T.hh[e] = h;
+            T.cc[e] = a / (h * h * h);
+            T.jj[e] = j;
+            T.kn[e] = 0;
+            const float2 th = __ldg(p.theta + j);
+            float* nk = T.nk0 + nnk + rank * KP1;
+            int* nv = T.nv0 + nnk + rank * KP1;
+            float k0 = 0.f;
+#pragma unroll 1
+            for (int k = 0; k <= K; ++k) {
+              const float key = tc.hi + fmaf(knot_sigma(K, m, th, k), h, tc.lo);
+              if (k == 0) k0 = key;
+              nk[k] = key;
+              nv[k] = e | (k << 16);
+            }
+            // a first knot behind the processed part of the ray would mean the
+            // ordering bound was violated: report it
+            if (started && k0 < Ta.hi - 1e-6f * fabsf(Ta.hi)) st_flags |= 8;
+            if (DBG && p.dbg_cands) {
+              const long long ci2 = dbg_nc + rank;
+              if (ci2 < p.cand_cap) p.dbg_cands[dbg_row * p.cand_cap + ci2] = p.orig[pidx];
+            }
+          }
+          nfree -= from_free;
+          hwm += n_store - from_free;
+          nnk += n_store * KP1;
+          st_cand += n_new;
+          dbg_nc += n_new;
+          st_maxtab = max(st_maxtab, hwm - nfree);
+        }
+        __syncwarp();
+      }
+      PT_END(1)
+      PT_BEGIN
+      cur = next_hit(cur + 1);
+      PT_END(0)
     }
 
     // ---- output
-    if (in_img) {
-      ++st_rays;
-      if (p.tau_ert > 0.f && tau_ray > p.tau_ert) ++st_ert;
-    }
+    ++st_rays;
+    if (p.tau_ert > 0.f && tau_ray > p.tau_ert) ++st_ert;
     st_knots += my_knots;
-    if (in_img && lane == 0) {
+    if (lane == 0) {
       float alpha = -expm1f(-tau_ray);
       if (DBG) {
         p.dbg_rgba[4 * dbg_row + 0] = col[0];
@@ -1310,10 +1318,6 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
   }
 }
 
-inline size_t render_smem_bytes(int tf_n, int nw) {
-  size_t per_warp = (sizeof(float) + sizeof(int)) * 2 * kW + sizeof(int) * (2 * kNb + 4);
-  return sizeof(float4) * tf_n + (sizeof(float4) + sizeof(float) + sizeof(int)) * kStage +
-         sizeof(float4) * kStageChunks + sizeof(int) * (kStageChunks + 4) + sizeof(float) * 4 + per_warp * nw;
-}
+inline size_t render_smem_bytes(int tf_n, int nw) { return sizeof(float4) * tf_n + (size_t)kWarpSmem * nw; }
 
 }  // namespace sphdvr

@@ -20,8 +20,8 @@ namespace {
 // Limits of the static scratch.
 constexpr int64_t kStMaxChunks = int64_t(1) << 20;  // dataset chunks (<= 32 particles each)
 constexpr int kStMaxTiles = 1 << 16;                // 16x16-pixel tiles (4096 x 4096 pixels)
-constexpr size_t kStMaxPairs = size_t(1) << 22;     // chunk-tile pairs of one frame
-constexpr int kStTableCtas = 148;                   // render CTAs whose per-ray tables fit
+constexpr size_t kStMaxPairs = size_t(1) << 21;     // chunk-tile pairs of one frame
+constexpr int kStTableCtas = 64;                    // render CTAs whose per-ray scratch fits
 constexpr size_t kStBytes = size_t(192) << 20;      // 192 MiB
 constexpr int kStMaxDevices = 64;
 
@@ -141,6 +141,6 @@ extern "C" sphdvr_status sphdvr_render_static_scratch(sphdvr_ctx* ctx, const sph
   s = render_frame_ws(ctx, a, w, nullptr, nullptr, (cudaStream_t)stream);
   if (s == SPHDVR_EOVERFLOW && ctx->last_pairs > (int64_t)kStMaxPairs)
     return set_err(ctx, SPHDVR_EOVERFLOW, "render_static_scratch: frame has " + std::to_string(ctx->last_pairs) +
-                                              " chunk-tile pairs; the static scratch holds at most 4194304");
+                                              " chunk-tile pairs; the static scratch holds at most 2097152");
   return s;
 }
