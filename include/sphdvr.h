@@ -187,7 +187,7 @@ sphdvr_status sphdvr_dataset_info(const sphdvr_dataset* ds, int64_t info[8]);
  * caller-owned), enqueued on `stream` (cudaStream_t, NULL = legacy default).
  * The call returns when the frame has been enqueued and its work buffers
  * are in place; it synchronises the stream only to size those buffers.
- * `opts` may be NULL (defaults: FP32_ANCHORED, anchor_every 1, ert_eps 1e-5,
+ * `opts` may be NULL (defaults: FP32_ANCHORED, anchor_every 2, ert_eps 1e-5,
  * non-persistent).  The kernel w (and its support q) is the one the table
  * was built for.  Returns EOVERFLOW
  * (image still written, possibly wrong) if a per-ray buffer overflowed. */

@@ -55,15 +55,15 @@ constexpr int kW = 32 * kKpl;       // window capacity (knots)
 constexpr int kLevels = 128;        // smoothing-length bins (quarter octaves) for the window limit
 constexpr int kLevelBase = (127 - 28) << 2;  // bin 0 starts at h = 2^-28
 constexpr int kRenderWarps = 4;     // rays (warps) per CTA in normal rendering
-// per-ray global scratch (32-bit words): 5 entry arrays, processed-knot
-// counts, active list, free stack, two pending-knot buffers (key, value)
-constexpr int kTableWords = 8 * kCap + 4 * kPL;
+// per-ray global scratch (32-bit words): particle records (4 words), table
+// entries, active list, free stack, two pending-knot buffers (key, value)
+constexpr int kTableWords = 7 * kCap + 4 * kPL;
 // per-warp shared memory (bytes): radix histogram, smoothing-length histogram,
-// and a work area shared in time by the new-knot buffers (two key/value
+// processed-knot counts (4 bits per entry), and a work area shared in time by the new-knot buffers (two key/value
 // buffers, the second also stages pending knots during a merge) and the
 // window's difference coefficients
 constexpr int kWorkBytes = 4 * kNK * 4;  // >= the window: kW * (D + 1) floats for D <= 7
-constexpr int kWarpSmem = 256 * 4 + kLevels * 4 + kWorkBytes;
+constexpr int kWarpSmem = 256 * 4 + kLevels * 4 + kCap / 2 + kWorkBytes;
 
 struct RenderParams {
   DevCamera cam;
@@ -238,48 +238,65 @@ __device__ __forceinline__ void composite_piece(const float* P, float L, const T
 }
 
 // Pieces that may cross transfer-function nodes: 8 sub-intervals, node
-// crossings by bisection inside each (kept out of line: rare on dense data).
+// crossings found inside each by a bracketed root search (kept out of line).
 template <int D>
 __device__ __noinline__ void composite_piece_slow(const float* P, float L, float f0, const TfCtx& t, float& tau_l,
                                                    float* C) {
   const int NS = 8;
-  float step = L / NS, ya = 0.f, fa = f0;
+  const float step = L / NS;
+  float ya = 0.f, fa = f0;
 #pragma unroll 1
   for (int s = 1; s <= NS; ++s) {
-    float yb = (s == NS) ? L : s * step;
-    float fb = horner<D>(P, yb);
-    int c0 = tf_cell(t, fa), c1 = tf_cell(t, fb);
-    float ycur = ya;
-    int ccur = c0;
-    while (ccur != c1) {
-      int cn = c1 > ccur ? ccur + 1 : ccur - 1;
-      float v = t.lo + (c1 > ccur ? cn : ccur) * t.dv;  // boundary between ccur and cn
-      float lo_y = ycur, hi_y = yb;
-      bool up = c1 > ccur;
-      for (int it = 0; it < 24; ++it) {
-        float mid = 0.5f * (lo_y + hi_y);
-        float fm = horner<D>(P, mid);
-        if ((fm < v) == up) lo_y = mid; else hi_y = mid;
+    const float yb = (s == NS) ? L : s * step;
+    const float fb = horner<D>(P, yb);
+    const int c1 = tf_cell(t, fb);
+    float ycur = ya, fcur = fa;
+    int ccur = tf_cell(t, fa);
+#pragma unroll 1
+    for (;;) {
+      float yend = yb;
+      int cnext = ccur;
+      if (ccur != c1) {
+        // crossing of the node between ccur and the next cell towards c1:
+        // Illinois (modified regula falsi) on P(y) - v, bracketed in [ycur, yb]
+        cnext = c1 > ccur ? ccur + 1 : ccur - 1;
+        const float v = t.lo + (c1 > ccur ? cnext : ccur) * t.dv;
+        float a = ycur, b = yb, ga = fcur - v, gb = fb - v, c = 0.5f * (a + b);
+        int side = 0;
+#pragma unroll 1
+        for (int it = 0; it < 20 && b - a > 1e-7f * L; ++it) {
+          c = (gb != ga) ? (a * gb - b * ga) / (gb - ga) : 0.5f * (a + b);
+          if (!(c > a && c < b)) c = 0.5f * (a + b);
+          const float gc = horner<D>(P, c) - v;
+          if (gc == 0.f) break;
+          if ((gc > 0.f) == (gb > 0.f)) {
+            b = c;
+            gb = gc;
+            if (side == -1) ga *= 0.5f;
+            side = -1;
+          } else {
+            a = c;
+            ga = gc;
+            if (side == 1) gb *= 0.5f;
+            side = 1;
+          }
+        }
+        yend = c;
       }
-      float yc = 0.5f * (lo_y + hi_y);
       float Q[D + 1];
 #pragma unroll
       for (int d = 0; d <= D; ++d) Q[d] = P[d];
       taylor_shift<D, float>(Q, ycur);
-      composite_cell<D>(Q, yc - ycur, ccur, t, tau_l, C);
-      ycur = yc;
-      ccur = cn;
+      composite_cell<D>(Q, yend - ycur, ccur, t, tau_l, C);
+      if (cnext == ccur) break;
+      ycur = yend;
+      fcur = t.lo + (c1 > ccur ? cnext : ccur) * t.dv;
+      ccur = cnext;
     }
-    float Q[D + 1];
-#pragma unroll
-    for (int d = 0; d <= D; ++d) Q[d] = P[d];
-    taylor_shift<D, float>(Q, ycur);
-    composite_cell<D>(Q, yb - ycur, ccur, t, tau_l, C);
     ya = yb;
     fa = fb;
   }
 }
-
 
 template <int D>
 struct Poly {
@@ -306,12 +323,8 @@ __device__ __noinline__ Acc composite_piece_v(Poly<D> P, float L, TfCtx t, Acc a
 // Per-ray scratch: entry arrays, lists and knot buffers in global memory
 // (L1/L2-resident while the ray is live); masks and histograms in shared memory.
 struct RayScratch {
-  float* tc_hi;  // t_chi (double-float)
-  float* tc_lo;
-  float* hh;     // h
-  float* cc;     // a / h^3
+  float4* ent;   // (t_chi hi, t_chi lo, h, a / h^3)
   int* jj;       // table entry (Lambda index)
-  int* kn;       // knots processed so far (atomic max; read through L2)
   int* act;      // active list: entries whose first knot has been processed
   int* fre;      // free stack of entry slots
   float* pk0;    // pending knots, sorted: FP32 absolute position (two buffers)
@@ -320,6 +333,7 @@ struct RayScratch {
   int* pv1;
   int* rh;       // shared: radix histogram (256 bins)
   int* lvl;      // shared: active particles per smoothing-length bin
+  unsigned* knc; // shared: knots processed so far per entry (4-bit counts, 8 per word)
   float* nk0;    // shared: new knots (unsorted, then radix ping-pong)
   int* nv0;
   float* nk1;
@@ -355,7 +369,7 @@ __device__ __forceinline__ void knot_delta(const RenderParams& p, int j, float h
   bool mir;
   int slot = knot_slot(p.K, p.m, k, mir);
   const float* jr = p.jump + (size_t)j * 3 * D + slot * D;
-  float ih = 1.f / h, s = c;
+  float ih = __fdividef(1.f, h), s = c;
 #pragma unroll
   for (int d = 1; d <= D; ++d) {
     s *= ih;
@@ -364,11 +378,13 @@ __device__ __forceinline__ void knot_delta(const RenderParams& p, int j, float h
   }
 }
 
-// Exact coefficients at Ta of entry e's piece after its first kn knots.
+__device__ __forceinline__ int knots_done(const RayScratch& T, int e) { return (T.knc[e >> 3] >> (4 * (e & 7))) & 15; }
+
+// Exact coefficients at Ta of the piece after the first kn knots of a particle
+// (entry record E, table entry j).
 template <int D>
-__device__ __forceinline__ void entry_piece_at(const RenderParams& p, const RayScratch& T, int e, int kn, df Ta,
-                                               float* A) {
-  int j = T.jj[e], pc = kn - 1;
+__device__ __forceinline__ void entry_piece_at(const RenderParams& p, float4 E, int j, int kn, df Ta, float* A) {
+  int pc = kn - 1;
   int K = p.K, m = p.m, kp;
   float sg;
   if (!(K & 1)) {
@@ -380,15 +396,15 @@ __device__ __forceinline__ void entry_piece_at(const RenderParams& p, const RayS
   }
   float2 th = __ldg(p.theta + j);
   float th0 = kp == 1 ? 0.f : th.x;
-  float h = T.hh[e];
-  float rel = (Ta.hi - T.tc_hi[e]) + (Ta.lo - T.tc_lo[e]);
-  float z = sg * rel / h - th0;
+  const float h = E.z, ih = __fdividef(1.f, h);
+  float rel = (Ta.hi - E.x) + (Ta.lo - E.y);
+  float z = sg * rel * ih - th0;
   const float* pr = p.piece + (size_t)j * 2 * (D + 1) + (kp - 1) * (D + 1);
   float q[D + 1];
 #pragma unroll
   for (int d = 0; d <= D; ++d) q[d] = __ldg(pr + d);
   taylor_shift<D, float>(q, z);
-  float s = T.cc[e], f = sg / h;
+  float s = E.w, f = sg * ih;
 #pragma unroll
   for (int d = 0; d <= D; ++d) {
     A[d] = q[d] * s;
@@ -415,9 +431,19 @@ __device__ __forceinline__ unsigned f2key(float x) {
 __device__ __forceinline__ int warp_radix_sort(float* k0, int* v0, float* k1, int* v1, int n, int* rh) {
   const int lane = threadIdx.x & 31;
   int cur = 0;
+  // digits above the highest bit in which the keys differ are shared by all
+  unsigned kmin = 0xffffffffu, kmax = 0u;
+#pragma unroll 1
+  for (int i = lane; i < n; i += 32) {
+    const unsigned kk = f2key(k0[i]);
+    kmin = min(kmin, kk);
+    kmax = max(kmax, kk);
+  }
+  const unsigned diff = __reduce_min_sync(kFull, kmin) ^ __reduce_max_sync(kFull, kmax);
 #pragma unroll 1
   for (int pass = 0; pass < 4; ++pass) {
     const int sh = 8 * pass;
+    if ((diff >> sh) == 0u) break;
     const float* kc = cur ? k1 : k0;
     const int* vc = cur ? v1 : v0;
     float* kd = cur ? k0 : k1;
@@ -425,7 +451,12 @@ __device__ __forceinline__ int warp_radix_sort(float* k0, int* v0, float* k1, in
     for (int b = lane; b < 256; b += 32) rh[b] = 0;
     __syncwarp();
 #pragma unroll 1
-    for (int i = lane; i < n; i += 32) atomicAdd(&rh[(f2key(kc[i]) >> sh) & 255], 1);
+    for (int base = 0; base < n; base += 32) {
+      const int i = base + lane;
+      const int d = i < n ? (int)((f2key(kc[i]) >> sh) & 255) : 256 + lane;
+      const unsigned peers = __match_any_sync(kFull, d);
+      if (i < n && (peers & lanemask_lt()) == 0u) atomicAdd(&rh[d], __popc(peers));
+    }
     __syncwarp();
     int c[8], s = 0;
     bool all_one = false;
@@ -477,23 +508,35 @@ __device__ __forceinline__ int warp_radix_sort(float* k0, int* v0, float* k1, in
 // Merge the sorted pending knots a[0, na) (global) with the sorted new knots
 // b[0, nb) (shared) into o[0, nout), nout <= na + nb (the largest keys are
 // dropped when it is smaller); equal keys take a first.  The output is made
-// in tiles of 32 * 16: the next 512 elements of a are staged in shared memory
-// (st, sv), each lane finds its 16-element slice by a merge-path search and
-// merges it sequentially.
+// in tiles of 32 * 8: the next 256 elements of a are staged in shared memory
+// (stk, stv; loaded into registers while the previous tile is merged), each
+// lane finds its 8-element slice by a merge-path search and merges it
+// sequentially.
 __device__ __forceinline__ void warp_tile_merge(const float* ak, const int* av, int na, const float* bk,
                                                 const int* bv, int nb, float* ok, int* ov, int nout, float* stk,
                                                 int* stv) {
-  constexpr int kPer = 16, kTileOut = 32 * kPer;
+  constexpr int kPer = 8, kTileOut = 32 * kPer;
   const int lane = threadIdx.x & 31;
+  float pk_[kPer];
+  int pv_[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = u * 32 + lane;
+    pk_[u] = i < na ? ak[i] : 0.f;
+    pv_[u] = i < na ? av[i] : 0;
+  }
   int ia0 = 0, ib0 = 0;  // consumed so far
 #pragma unroll 1
   for (int o0 = 0; o0 < nout; o0 += kTileOut) {
     const int ta = min(kTileOut, na - ia0);  // staged part of a
     const int tb = nb - ib0;
-#pragma unroll 4
-    for (int i = lane; i < ta; i += 32) {
-      stk[i] = ak[ia0 + i];
-      stv[i] = av[ia0 + i];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int i = u * 32 + lane;
+      if (i < ta) {
+        stk[i] = pk_[u];
+        stv[i] = pv_[u];
+      }
     }
     __syncwarp();
     const int tout = min(kTileOut, nout - o0);
@@ -509,6 +552,15 @@ __device__ __forceinline__ void warp_tile_merge(const float* ak, const int* av, 
       }
       return lo;
     };
+    const int used_a = path(tout);
+    // next tile of a, in flight while this one is merged
+    const int nx = ia0 + used_a;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int i = nx + u * 32 + lane;
+      pk_[u] = i < na ? ak[i] : 0.f;
+      pv_[u] = i < na ? av[i] : 0;
+    }
     const int d0 = min(lane * kPer, tout), d1 = min(d0 + kPer, tout);
     int ia = path(d0), ib = d0 - ia;
 #pragma unroll 1
@@ -524,8 +576,6 @@ __device__ __forceinline__ void warp_tile_merge(const float* ak, const int* av, 
         ++ib;
       }
     }
-    // elements of a consumed by the whole tile
-    const int used_a = path(tout);
     __syncwarp();
     ia0 += used_a;
     ib0 += tout - used_a;
@@ -570,7 +620,7 @@ __device__ __forceinline__ void active_pass(const RenderParams& p, const RayScra
       e[u] = i < nal ? T.act[i] : -1;
     }
 #pragma unroll
-    for (int u = 0; u < 2; ++u) kn[u] = e[u] >= 0 ? __ldcg(T.kn + e[u]) : 0;
+    for (int u = 0; u < 2; ++u) kn[u] = e[u] >= 0 ? knots_done(T, e[u]) : 0;
     bool keep[2], fin[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -582,7 +632,7 @@ __device__ __forceinline__ void active_pass(const RenderParams& p, const RayScra
       for (int u = 0; u < 2; ++u) {
         if (keep[u]) {
           float Ae[D + 1];
-          entry_piece_at<D>(p, T, e[u], kn[u], Ta, Ae);
+          entry_piece_at<D>(p, T.ent[e[u]], T.jj[e[u]], kn[u], Ta, Ae);
 #pragma unroll
           for (int d = 0; d <= D; ++d) acc[d] += Ae[d];
         }
@@ -626,22 +676,19 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     unsigned char* b = smem + sizeof(float4) * p.tf_n + (size_t)kWarpSmem * wid;
     T.rh = (int*)b;
     T.lvl = (int*)(b + 256 * 4);
-    float* w = (float*)(b + 256 * 4 + kLevels * 4);
+    T.knc = (unsigned*)(b + 256 * 4 + kLevels * 4);
+    float* w = (float*)(b + 256 * 4 + kLevels * 4 + kCap / 2);
     T.nk0 = w;
     T.nv0 = (int*)(w + kNK);
     T.nk1 = w + 2 * kNK;
     T.nv1 = (int*)(w + 3 * kNK);
     T.wdl = w;
     float* g = p.scratch + (size_t)(blockIdx.x * NW + wid) * kTableWords;
-    T.tc_hi = g;
-    T.tc_lo = g + kCap;
-    T.hh = g + 2 * kCap;
-    T.cc = g + 3 * kCap;
+    T.ent = (float4*)g;
     T.jj = (int*)(g + 4 * kCap);
-    T.kn = (int*)(g + 5 * kCap);
-    T.act = (int*)(g + 6 * kCap);
-    T.fre = (int*)(g + 7 * kCap);
-    float* q0 = g + 8 * kCap;
+    T.act = (int*)(g + 5 * kCap);
+    T.fre = (int*)(g + 6 * kCap);
+    float* q0 = g + 7 * kCap;
     T.pk0 = q0;
     T.pv0 = (int*)(q0 + kPL);
     T.pk1 = q0 + 2 * kPL;
@@ -813,10 +860,11 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             if (!(PK[head] < F)) break;
             const int v0 = PV[head], e0 = v0 & 0xffff, k0 = v0 >> 16;
             const float sg = knot_sigma(K, m, __ldg(p.theta + T.jj[e0]), k0);
-            df kp = df{T.tc_hi[e0], T.tc_lo[e0]};
+            const float4 E0 = T.ent[e0];
+            df kp = df{E0.x, E0.y};
             {
-              const float pr = sg * T.hh[e0];
-              const float pe = fmaf(sg, T.hh[e0], -pr);
+              const float pr = sg * E0.z;
+              const float pe = fmaf(sg, E0.z, -pr);
               kp = df_add(kp, df{pr, pe});
             }
             if (started) {
@@ -893,9 +941,10 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             if (i < nc) {
               vv = PV[head + i];
               const int e = vv & 0xffff, k = vv >> 16;
-              const float hh = T.hh[e], c = T.cc[e];
+              const float4 E = T.ent[e];
+              const float hh = E.z, c = E.w;
               const int j = T.jj[e];
-              const float base = (T.tc_hi[e] - Ta.hi) + (T.tc_lo[e] - Ta.lo);
+              const float base = (E.x - Ta.hi) + (E.y - Ta.lo);
               u = fmaf(knot_sigma(K, m, __ldg(p.theta + j), k), hh, base);
               float dl[D];
               knot_delta<D>(p, j, hh, c, k, dl);
@@ -982,12 +1031,12 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             const bool valid = r < cnt_l;
             const int vv = sv[r * 32 + lane];
             const int e = vv & 0xffff, k = vv >> 16;
-            if (valid) atomicMax(T.kn + e, k + 1);
+            if (valid) atomicAdd(T.knc + (e >> 3), 1u << (4 * (e & 7)));
             const bool first = valid && k == 0;
             const unsigned mm = __ballot_sync(kFull, first);
             if (first) T.act[nal + __popc(mm & lanemask_lt())] = e;
             nal += __popc(mm);
-            if (valid && (k == 0 || k == K)) atomicAdd(&T.lvl[h_level(T.hh[e])], k == 0 ? 1 : -1);
+            if (valid && (k == 0 || k == K)) atomicAdd(&T.lvl[h_level(T.ent[e].z)], k == 0 ? 1 : -1);
           }
           __syncwarp();
           n_act = act_after;
@@ -1021,7 +1070,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           for (int d = 0; d <= D; ++d) sa[d] = agg[d];
           float se = ulast;
           int sh = has ? 1 : 0;
-#pragma unroll
+#pragma unroll 1
           for (int o2 = 1; o2 < 32; o2 <<= 1) {
             S oa[D + 1];
 #pragma unroll
@@ -1231,17 +1280,14 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           if (cand && rank < n_store) {
             const int e = rank < from_free ? T.fre[nfree - 1 - rank] : hwm + (rank - from_free);
             // nearest Lambda entry (FP64 re-check near a midpoint)
-            const float x = sqrtf(d2) / h * p.lam_scale;
+            const float x = (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f) * __fdividef(p.lam_scale, h);
             int j = (int)floorf(x + 0.5f);
             const float fr = x - floorf(x);
             if (fabsf(fr - 0.5f) < 2e-3f) j = nearest_entry_fp64(wv, h, p.n_lambda, q);
             j = min(max(j, 0), p.n_lambda - 1);
-            T.tc_hi[e] = tc.hi;
-            T.tc_lo[e] = tc.lo;
-            T.hh[e] = h;
-            T.cc[e] = a / (h * h * h);
+            T.ent[e] = make_float4(tc.hi, tc.lo, h, __fdividef(a, h * h * h));
             T.jj[e] = j;
-            T.kn[e] = 0;
+            atomicAnd(T.knc + (e >> 3), ~(15u << (4 * (e & 7))));
             const float2 th = __ldg(p.theta + j);
             float* nk = T.nk0 + nnk + rank * KP1;
             int* nv = T.nv0 + nnk + rank * KP1;
