@@ -162,8 +162,13 @@ def main():
     ap.add_argument("--cpu-pixels", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp32_anchored")
+    ap.add_argument("--res", type=int, default=0, help="override the workload's image size (square)")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.res > 0:
+        w["res"] = args.res
+        r0 = WORKLOADS[args.workload]["res"]
+        w["desc"] = w["desc"].replace("%dx%d" % (r0, r0), "%dx%d" % (args.res, args.res))
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))

@@ -241,6 +241,50 @@ sphdvr_status sphdvr_render_static_scratch(sphdvr_ctx* ctx, const sphdvr_dataset
  * shortened by the window_h limit, [13..15] 0. */
 sphdvr_status sphdvr_frame_stats(sphdvr_ctx* ctx, int64_t out[16]);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of frames (a library service; the paper
+ * renders single frames).
+ *
+ * A server owns `max_inflight` (1..8) worker threads, each with its own CUDA
+ * stream and frame buffers; submitted requests are rendered in submission
+ * order by whichever worker is free, so frames overlap on the GPU.  The
+ * device memory all workers hold for frame buffers stays within `hbm_budget`
+ * bytes (datasets and tables are not counted: they belong to the caller's
+ * context): a worker whose frame does not fit beside the others' holdings
+ * frees what it holds and waits until they release enough.
+ * ------------------------------------------------------------------------- */
+typedef struct sphdvr_server sphdvr_server;
+
+sphdvr_status sphdvr_server_create(sphdvr_ctx* ctx, size_t hbm_budget, int max_inflight, sphdvr_server** out);
+
+/* Queue one frame: arguments as sphdvr_render (`rgba_out` a DEVICE pointer
+ * that must stay valid, and `ds`, `lut` alive, until the request completes).
+ * The camera, transfer function and options are copied.  Returns at once
+ * with a ticket; SPHDVR_EBUSY if the frame's fixed buffers alone exceed the
+ * budget.  A frame whose pair buffers make it exceed the budget fails later
+ * with SPHDVR_EBUSY (reported by sphdvr_server_wait). */
+sphdvr_status sphdvr_server_submit(sphdvr_server* srv, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+                                   const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
+                                   float* rgba_out, uint64_t* ticket);
+
+/* Wait for a ticket: returns the frame's status once it has completed (its
+ * image is then in rgba_out and the ticket is retired), SPHDVR_ETIMEOUT if
+ * it has not completed within timeout_ms (the ticket stays valid; a negative
+ * timeout waits until completion), SPHDVR_ENOTFOUND for an unknown or
+ * retired ticket. */
+sphdvr_status sphdvr_server_wait(sphdvr_server* srv, uint64_t ticket, int timeout_ms);
+
+/* out[0] p50 and out[1] p99 latency (ms, submission to completion) of the
+ * completed frames, out[2] rays per second over the time from the first
+ * submission to the last completion, out[3] frames completed, out[4] frames
+ * failed, out[5] device bytes the workers hold, out[6] largest latency (ms),
+ * out[7] frames queued and not yet started. */
+sphdvr_status sphdvr_server_stats(sphdvr_server* srv, double out[8]);
+
+/* Finish every queued frame, then stop the workers and free their buffers.
+ * Tickets not waited for are retired. */
+sphdvr_status sphdvr_server_destroy(sphdvr_server* srv);
+
 /* Parity hook: render the listed pixels with the same kernels and return,
  * per pixel r (all HOST pointers):
  *   rgba[4r..4r+3]

@@ -144,6 +144,29 @@ sphdvr_status check_common(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphd
 
 }  // namespace sphdvr
 
+namespace sphdvr {
+
+size_t ctx_held_bytes(const sphdvr_ctx* c) {
+  const DevBuf* bufs[] = {&c->chunk_rect, &c->chunk_front, &c->chunk_ntile, &c->chunk_off, &c->pair_key,
+                          &c->pair_val, &c->pair_key2, &c->pair_val2, &c->tile_range, &c->scan_tmp, &c->sort_tmp,
+                          &c->stats, &c->tf, &c->img, &c->dbg_pix, &c->dbg_rgba, &c->dbg_counts, &c->dbg_cands,
+                          &c->dbg_field, &c->table, &c->work};
+  size_t t = 0;
+  for (const DevBuf* b : bufs) t += b->bytes;
+  return t;
+}
+
+void ctx_release_buffers(sphdvr_ctx* c) {
+  DevBuf* bufs[] = {&c->chunk_rect, &c->chunk_front, &c->chunk_ntile, &c->chunk_off, &c->pair_key, &c->pair_val,
+                    &c->pair_key2, &c->pair_val2, &c->tile_range, &c->scan_tmp, &c->sort_tmp, &c->stats,
+                    &c->tf, &c->img, &c->dbg_pix, &c->dbg_rgba, &c->dbg_counts, &c->dbg_cands, &c->dbg_field,
+                    &c->table, &c->work};
+  for (DevBuf* b : bufs) free_buf(*b);
+  c->stats_pending = false;
+}
+
+}  // namespace sphdvr
+
 using namespace sphdvr;
 
 extern "C" {
@@ -187,11 +210,7 @@ sphdvr_status sphdvr_create(int device, sphdvr_ctx** out) {
 sphdvr_status sphdvr_destroy(sphdvr_ctx* c) {
   if (!c) return SPHDVR_EINVAL;
   cudaSetDevice(c->device);
-  DevBuf* bufs[] = {&c->chunk_rect, &c->chunk_front, &c->chunk_ntile, &c->chunk_off, &c->pair_key, &c->pair_val,
-                    &c->pair_key2, &c->pair_val2, &c->tile_range, &c->scan_tmp, &c->sort_tmp, &c->stats,
-                    &c->tf, &c->img, &c->dbg_pix, &c->dbg_rgba, &c->dbg_counts, &c->dbg_cands, &c->dbg_field,
-                    &c->table, &c->work};
-  for (DevBuf* b : bufs) free_buf(*b);
+  ctx_release_buffers(c);
   if (c->ev_ready) {
     cudaEventDestroy(c->ev_render0);
     cudaEventDestroy(c->ev_render1);

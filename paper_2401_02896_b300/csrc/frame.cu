@@ -198,8 +198,6 @@ size_t render_table_floats(int grid, bool dbg) { return (size_t)grid * (dbg ? 1 
 
 
 
-namespace {
-
 // grow the context's pair buffers once the pair count is known
 sphdvr_status ctx_pair_sizer(sphdvr_ctx* ctx, FrameWork& w, size_t pairs, void*) {
   const size_t np = std::max<size_t>(pairs, 1);
@@ -218,9 +216,25 @@ sphdvr_status ctx_pair_sizer(sphdvr_ctx* ctx, FrameWork& w, size_t pairs, void*)
   return SPHDVR_OK;
 }
 
-}  // namespace
+size_t pair_bytes(size_t pairs) {
+  const size_t np = std::max<size_t>(pairs, 1);
+  return np * 24 + sort_tmp_words((int64_t)np) * sizeof(uint32_t);
+}
+
+size_t frame_fixed_bytes(sphdvr_ctx* ctx, const RenderArgs& a) {
+  const size_t tiles = (size_t)((a.cam.width + kTile - 1) / kTile) * ((a.cam.height + kTile - 1) / kTile);
+  const size_t nc = a.ds->n_chunks;
+  const int grid = render_grid(ctx, a);
+  return nc * (sizeof(float4) + sizeof(unsigned) + 2 * sizeof(uint32_t)) + 32 + tiles * sizeof(int2) +
+         32 * sizeof(unsigned long long) + scan_tmp_words(nc) * sizeof(uint32_t) + (size_t)a.tf_n * sizeof(float4) +
+         render_table_floats(grid, a.n_dbg > 0) * sizeof(float) + 4 * sizeof(unsigned);
+}
 
 sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st) {
+  return render_frame_sized(ctx, a, st, ctx_pair_sizer, nullptr);
+}
+
+sphdvr_status render_frame_sized(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st, PairSizer sizer, void* user) {
   const int tiles = ((a.cam.width + kTile - 1) / kTile) * ((a.cam.height + kTile - 1) / kTile);
   const int nc = a.ds->n_chunks;
   sphdvr_status s;
@@ -250,7 +264,7 @@ sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st
   w.tf = (float4*)ctx->tf.p;
   w.tmp = (uint32_t*)ctx->scan_tmp.p;
   w.tmp_words = ctx->scan_tmp.bytes / sizeof(uint32_t);
-  return render_frame_ws(ctx, a, w, ctx_pair_sizer, nullptr, st);
+  return render_frame_ws(ctx, a, w, sizer, user, st);
 }
 
 sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w, PairSizer sizer, void* user,

@@ -104,6 +104,8 @@ sphdvr_status dev_alloc(sphdvr_ctx* ctx, void** p, size_t bytes);
 sphdvr_status check_camera(sphdvr_ctx* ctx, const sphdvr_camera* c, DevCamera* out);
 sphdvr_status check_opts(sphdvr_ctx* ctx, const sphdvr_render_opts* o);
 sphdvr_status check_common(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut);
+// Validate a transfer function and pack it as (r, g, b, sigma_scale * A).
+sphdvr_status pack_tf(sphdvr_ctx* ctx, const sphdvr_tf* tf, std::vector<float4>& out);
 
 // sort.cu
 // Exclusive prefix sum of n uint32 values (in may equal out).  If total is
@@ -174,5 +176,16 @@ sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st
 typedef sphdvr_status (*PairSizer)(sphdvr_ctx* ctx, FrameWork& w, size_t pairs, void* user);
 sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w, PairSizer sizer, void* user,
                               cudaStream_t st);
+// As render_frame, with the pair buffers sized by `sizer`.
+sphdvr_status render_frame_sized(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st, PairSizer sizer, void* user);
+// The sizer of render_frame: grows the context's pair buffers.
+sphdvr_status ctx_pair_sizer(sphdvr_ctx* ctx, FrameWork& w, size_t pairs, void* user);
+// Device bytes a frame needs besides its pair buffers, and the pair buffers'
+// bytes for a given pair count (both without the grow-only headroom).
+size_t frame_fixed_bytes(sphdvr_ctx* ctx, const RenderArgs& a);
+size_t pair_bytes(size_t pairs);
+// api.cu: frame buffers a context holds; release them all.
+size_t ctx_held_bytes(const sphdvr_ctx* ctx);
+void ctx_release_buffers(sphdvr_ctx* ctx);
 
 }  // namespace sphdvr

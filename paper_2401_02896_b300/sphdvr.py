@@ -88,6 +88,12 @@ def _load():
         "sphdvr_render_static_scratch": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                                        ctypes.POINTER(RenderOpts), vp, vp]),
         "sphdvr_frame_stats": (ctypes.c_int, [vp, i64p]),
+        "sphdvr_server_create": (ctypes.c_int, [vp, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]),
+        "sphdvr_server_submit": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
+                                                ctypes.POINTER(RenderOpts), vp, ctypes.POINTER(ctypes.c_uint64)]),
+        "sphdvr_server_wait": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_int]),
+        "sphdvr_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "sphdvr_server_destroy": (ctypes.c_int, [vp]),
         "sphdvr_debug_rays": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                              ctypes.POINTER(RenderOpts), ctypes.c_int, vp, vp, vp, vp, ctypes.c_int,
                                              vp, ctypes.c_int]),
@@ -291,6 +297,43 @@ def sphdvr_debug_rays(ctx, ds, lut, camera, tf, opts, pixels, cand_cap=0, field_
                                 _p(rgba), _p(counts), _p(cands), int(cand_cap), _p(field), int(field_cap))
     _check(st, ctx, (EOVERFLOW,))
     return dict(rgba=rgba, counts=counts, cand_ids=cands, field=field, overflow=st == EOVERFLOW)
+
+
+class Server:
+    """Frame server (continuous batching over worker streams, device-memory budget)."""
+
+    def __init__(self, ctx, hbm_budget, max_inflight=2):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        _check(_lib.sphdvr_server_create(ctx, int(hbm_budget), int(max_inflight), ctypes.byref(h)), ctx)
+        self.h = h
+
+    def submit(self, ds, lut, camera, tf, opts, out_ptr):
+        """Queue one frame into a device buffer; returns its ticket."""
+        c, t, o = camera_struct(camera), tf_struct(tf), opts_struct(opts)
+        tk = ctypes.c_uint64()
+        _check(_lib.sphdvr_server_submit(self.h, ds, lut, ctypes.byref(c), ctypes.byref(t), ctypes.byref(o),
+                                         ctypes.c_void_p(out_ptr), ctypes.byref(tk)), self.ctx)
+        return tk.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        """True once the frame completed, False on timeout; raises on a failed frame."""
+        st = _lib.sphdvr_server_wait(self.h, ctypes.c_uint64(ticket), int(timeout_ms))
+        if st == ETIMEOUT:
+            return False
+        _check(st, self.ctx)
+        return True
+
+    def stats(self):
+        o = (ctypes.c_double * 8)()
+        _check(_lib.sphdvr_server_stats(self.h, o), self.ctx)
+        keys = ["p50_ms", "p99_ms", "rays_per_s", "completed", "failed", "held_bytes", "max_ms", "queued"]
+        return dict(zip(keys, list(o)))
+
+    def destroy(self):
+        if self.h is not None:
+            _check(_lib.sphdvr_server_destroy(self.h))
+            self.h = None
 
 
 def header_functions():
