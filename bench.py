@@ -163,6 +163,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp32_anchored")
     ap.add_argument("--res", type=int, default=0, help="override the workload's image size (square)")
+    ap.add_argument("--serve-requests", type=int, default=12,
+                    help="frames pushed through the frame server after the timed region (0: skip)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.res > 0:
@@ -250,6 +252,29 @@ def main():
     if dist:
         dist.barrier()
 
+    # ---- serving: seeded orbit cameras of mixed sizes, Poisson arrivals, two worker streams
+    serving = None
+    if args.serve_requests > 0:
+        rng = np.random.default_rng(1234 + rank)
+        sizes = [s_ for s_ in (256, 512, 1024) if s_ <= W] or [W]
+        srv = S.Server(ctx, 16 << 30, max_inflight=2)
+        outs, tickets = [], []
+        for i in range(args.serve_requests):
+            r_ = int(rng.choice(sizes))
+            c_ = SY.orbit_camera(r_, r_, azimuth_deg=360 * rng.random(), elevation_deg=-40 + 80 * rng.random())
+            o_ = torch.empty((r_, r_, 4), dtype=torch.float32, device=dev)
+            outs.append(o_)
+            tickets.append(srv.submit(ds, lut, c_, tf, opts, o_.data_ptr()))
+            time.sleep(float(rng.exponential(0.25)))
+        for t_ in tickets:
+            srv.wait(t_, -1)
+        sv = srv.stats()
+        srv.destroy()
+        serving = dict(requests=args.serve_requests, sizes=sizes, arrivals="Poisson, mean gap 250 ms", workers=2,
+                       p50_ms=sv["p50_ms"], p99_ms=sv["p99_ms"], mrays_per_s=sv["rays_per_s"] / 1e6,
+                       failed=int(sv["failed"]))
+        del outs
+
     if rank == 0:
         seg_per_frame = segs / args.steps
         fps = flops_per_segment(w["K"], w["D"])
@@ -277,6 +302,8 @@ def main():
             gpu_launches=int(launches),
             clocks=clocks,
         )
+        if serving:
+            line["serving"] = serving
         if not args.no_cpu_baseline:
             cb = cpu_oracle_rate(P, w, tf, args.cpu_pixels, seed=77)
             line["cpu_baseline"] = dict(value=cb["rays_per_s"] / 1e6, unit="Mrays/s", cores=cb["cores"], kind="oracle",
