@@ -505,6 +505,88 @@ __device__ __forceinline__ int warp_radix_sort(float* k0, int* v0, float* k1, in
   return cur;
 }
 
+// Sort n <= 512 (key, value) pairs by FP32 key, one warp: 256 buckets over
+// [min, max] of the keys (bucket index monotone in the key), a counting pass,
+// a scatter (order inside a bucket arbitrary), then insertion sort inside each
+// bucket (8 buckets per lane).  Falls back to the radix sort when a bucket
+// holds more than 32 keys.  Returns which buffer (0 or 1) holds the result.
+__device__ __forceinline__ int warp_bucket_sort(float* k0, int* v0, float* k1, int* v1, int n, int* rh) {
+  const int lane = threadIdx.x & 31;
+  float lo = __int_as_float(0x7f800000), hi = -lo;
+#pragma unroll 1
+  for (int i = lane; i < n; i += 32) {
+    lo = fminf(lo, k0[i]);
+    hi = fmaxf(hi, k0[i]);
+  }
+  lo = warp_min(lo);
+  hi = warp_max(hi);
+  if (!(hi > lo)) return 0;  // all keys equal (or n <= 1)
+  const float sc = 256.f / (hi - lo);
+  if (!(sc < 1e30f)) return warp_radix_sort(k0, v0, k1, v1, n, rh);  // keys closer than FP32 resolves here
+  for (int b = lane; b < 256; b += 32) rh[b] = 0;
+  __syncwarp();
+#pragma unroll 1
+  for (int i = lane; i < n; i += 32) atomicAdd(&rh[min(255, (int)((k0[i] - lo) * sc))], 1);
+  __syncwarp();
+  int c[8], s = 0, cmax = 0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    c[r] = rh[lane * 8 + r];
+    s += c[r];
+    cmax = max(cmax, c[r]);
+  }
+  if (__any_sync(kFull, cmax > 32)) return warp_radix_sort(k0, v0, k1, v1, n, rh);
+  int x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  const int base = x - s;
+  __syncwarp();
+  {
+    int ex = base;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      rh[lane * 8 + r] = ex;
+      ex += c[r];
+    }
+  }
+  __syncwarp();
+#pragma unroll 1
+  for (int i = lane; i < n; i += 32) {
+    const float kk = k0[i];
+    const int pos = atomicAdd(&rh[min(255, (int)((kk - lo) * sc))], 1);
+    k1[pos] = kk;
+    v1[pos] = v0[i];
+  }
+  __syncwarp();
+  // insertion sort inside this lane's 8 buckets [base, base + s)
+  {
+    int b0 = base;
+#pragma unroll 1
+    for (int r = 0; r < 8; ++r) {
+      const int cnt = c[r];
+#pragma unroll 1
+      for (int i = b0 + 1; i < b0 + cnt; ++i) {
+        const float kk = k1[i];
+        const int vv = v1[i];
+        int j = i - 1;
+        while (j >= b0 && k1[j] > kk) {
+          k1[j + 1] = k1[j];
+          v1[j + 1] = v1[j];
+          --j;
+        }
+        k1[j + 1] = kk;
+        v1[j + 1] = vv;
+      }
+      b0 += cnt;
+    }
+  }
+  __syncwarp();
+  return 1;
+}
+
 // Merge the sorted pending knots a[0, na) (global) with the sorted new knots
 // b[0, nb) (shared) into o[0, nout), nout <= na + nb (the largest keys are
 // dropped when it is smaller); equal keys take a first.  The output is made
@@ -834,7 +916,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
         PT_BEGIN
         // ---- sort the new knots and merge them into the pending list
         if (nnk > 0) {
-          const int rb = warp_radix_sort(T.nk0, T.nv0, T.nk1, T.nv1, nnk, T.rh);
+          const int rb = warp_bucket_sort(T.nk0, T.nv0, T.nk1, T.nv1, nnk, T.rh);
           const int na = npl - head;
           const int nout = min(na + nnk, kPL);
           if (na + nnk > kPL) st_flags |= 1;
