@@ -12,14 +12,17 @@
 //      t_near (Sec. 3.1);
 //   2. per-particle approximation: L = d/h picks the nearest table entry; the
 //      particle's K+1 knots are t_chi + h * sigma_k with localized difference
-//      coefficients a h^-3 * s_kd / h^d (Sec. 2, Sec. 3.1); the particle goes
-//      to the ray's entry table and its knots to a buffer of new knots;
-//   3. knot sort and merge: new knots are radix-sorted (warp LSD sort) and
-//      merged into the ray's sorted list of pending knots; all pending knots
-//      below the bound F of the next chunk are final;
-//   4. windows: a window is a prefix of the pending list (at most W knots,
-//      shortened so that FP32 round-off stays small for the particles it
-//      touches);
+//      coefficients a h^-3 * s_kd / h^d (Sec. 2, Sec. 3.1); the particle gets a
+//      slot in the ray's particle table;
+//   3. waiting list: new particles are sorted by their first knot (warp bucket
+//      sort in shared memory) and merged into the ray's list of particles that
+//      have not started yet; every knot below the bound F of the next chunk is
+//      final;
+//   4. windows: the knots of a window are generated from the active particles
+//      (their next knots) and the waiting particles that start inside it, all
+//      below the window end, and sorted in shared memory; a window holds at most
+//      W knots and is shortened so that FP32 round-off stays small for the
+//      particles it touches;
 //   5. segmented prefix sum: the coefficient-update recurrence of Sec. 2 as an
 //      associative scan over the warp -- (A, e_A) (+) (B, e_B) =
 //      (Shift(A, e_B - e_A) + B, e_B) -- seeded with the field's exact
@@ -48,7 +51,6 @@
 namespace sphdvr {
 
 constexpr int kCap = 4096;          // particle entries per ray
-constexpr int kPL = 3 * kCap;       // pending knots per ray (sorted list)
 constexpr int kNK = 512;            // new knots awaiting a merge (shared memory)
 constexpr int kKpl = 8;             // knots per lane in a window
 constexpr int kW = 32 * kKpl;       // window capacity (knots)
@@ -56,8 +58,8 @@ constexpr int kLevels = 128;        // smoothing-length bins (quarter octaves) f
 constexpr int kLevelBase = (127 - 28) << 2;  // bin 0 starts at h = 2^-28
 constexpr int kRenderWarps = 4;     // rays (warps) per CTA in normal rendering
 // per-ray global scratch (32-bit words): particle records (4 words), table
-// entries, active list, free stack, two pending-knot buffers (key, value)
-constexpr int kTableWords = 7 * kCap + 4 * kPL;
+// entries, active list, free stack, two buffers of the waiting list (key, value)
+constexpr int kTableWords = 11 * kCap;
 // per-warp shared memory (bytes): radix histogram, smoothing-length histogram,
 // processed-knot counts (4 bits per entry), and a work area shared in time by the new-knot buffers (two key/value
 // buffers, the second also stages pending knots during a merge) and the
@@ -327,10 +329,10 @@ struct RayScratch {
   int* jj;       // table entry (Lambda index)
   int* act;      // active list: entries whose first knot has been processed
   int* fre;      // free stack of entry slots
-  float* pk0;    // pending knots, sorted: FP32 absolute position (two buffers)
-  int* pv0;      //                        entry | k << 16
-  float* pk1;
-  int* pv1;
+  float* wk0;    // waiting particles (first knot not yet composited), sorted by
+  int* wv0;      // the FP32 position of their first knot: key, slot (two buffers)
+  float* wk1;
+  int* wv1;
   int* rh;       // shared: radix histogram (256 bins)
   int* lvl;      // shared: active particles per smoothing-length bin
   unsigned* knc; // shared: knots processed so far per entry (4-bit counts, 8 per word)
@@ -508,7 +510,7 @@ __device__ __forceinline__ int warp_radix_sort(float* k0, int* v0, float* k1, in
 // Sort n <= 512 (key, value) pairs by FP32 key, one warp: 256 buckets over
 // [min, max] of the keys (bucket index monotone in the key), a counting pass,
 // a scatter (order inside a bucket arbitrary), then insertion sort inside each
-// bucket (8 buckets per lane).  Falls back to the radix sort when a bucket
+// bucket (8 buckets per lane; equal keys by value).  Falls back to the radix sort when a bucket
 // holds more than 32 keys.  Returns which buffer (0 or 1) holds the result.
 __device__ __forceinline__ int warp_bucket_sort(float* k0, int* v0, float* k1, int* v1, int n, int* rh) {
   const int lane = threadIdx.x & 31;
@@ -572,7 +574,7 @@ __device__ __forceinline__ int warp_bucket_sort(float* k0, int* v0, float* k1, i
         const float kk = k1[i];
         const int vv = v1[i];
         int j = i - 1;
-        while (j >= b0 && k1[j] > kk) {
+        while (j >= b0 && (k1[j] > kk || (k1[j] == kk && v1[j] > vv))) {
           k1[j + 1] = k1[j];
           v1[j + 1] = v1[j];
           --j;
@@ -771,10 +773,10 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     T.act = (int*)(g + 5 * kCap);
     T.fre = (int*)(g + 6 * kCap);
     float* q0 = g + 7 * kCap;
-    T.pk0 = q0;
-    T.pv0 = (int*)(q0 + kPL);
-    T.pk1 = q0 + 2 * kPL;
-    T.pv1 = (int*)(q0 + 3 * kPL);
+    T.wk0 = q0;
+    T.wv0 = (int*)(q0 + kCap);
+    T.wk1 = q0 + 2 * kCap;
+    T.wv1 = (int*)(q0 + 3 * kCap);
   }
   for (int i = threadIdx.x; i < p.tf_n; i += blockDim.x) s_tf[i] = p.tf[i];
   __syncthreads();
@@ -782,7 +784,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
   unsigned long long st_cand = 0, st_tests = 0, st_knots = 0, st_win = 0, st_rays = 0, st_ert = 0, st_capped = 0;
   int st_maxtab = 0, st_flags = 0, st_maxact = 0;
   PT_DECL
-  const int K = p.K, m = p.m, KP1 = K + 1;
+  const int K = p.K, m = p.m;
   const float q = p.q, gam = p.window_h;
   const float t_near = (float)p.cam.t_near;
   const df t_near_df = df_from_double(p.cam.t_near);
@@ -855,7 +857,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     S carry[D + 1];
 #pragma unroll
     for (int d = 0; d <= D; ++d) carry[d] = (S)0;
-    int hwm = 0, nfree = 0, nal = 0, n_act = 0, head = 0, npl = 0, pb = 0, nnk = 0, win_count = 0;
+    int hwm = 0, nfree = 0, nal = 0, n_act = 0, whead = 0, nwait = 0, wb = 0, nnk = 0, win_count = 0;
     long long dbg_np = 0, dbg_nc = 0;
     unsigned long long my_knots = 0;
     for (int b = lane; b < kLevels; b += 32) T.lvl[b] = 0;
@@ -912,36 +914,45 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
       const int src = cur - gcur;  // this lane group holds entry `cur`
       const float F = last ? kInf : __shfl_sync(kFull, g_F, src & 31);
       const int room = nfree + (kCap - hwm);
-      if (last || nnk + 32 * KP1 > kNK || room < 32) {
+      if (last || nnk + 32 > kNK || room < 32) {
         PT_BEGIN
-        // ---- sort the new knots and merge them into the pending list
+        // ---- sort the new particles by first knot and merge them into the waiting list
         if (nnk > 0) {
           const int rb = warp_bucket_sort(T.nk0, T.nv0, T.nk1, T.nv1, nnk, T.rh);
-          const int na = npl - head;
-          const int nout = min(na + nnk, kPL);
-          if (na + nnk > kPL) st_flags |= 1;
-          warp_tile_merge((pb ? T.pk1 : T.pk0) + head, (pb ? T.pv1 : T.pv0) + head, na, rb ? T.nk1 : T.nk0,
-                          rb ? T.nv1 : T.nv0, nnk, pb ? T.pk0 : T.pk1, pb ? T.pv0 : T.pv1, nout, rb ? T.nk0 : T.nk1,
+          const int na = nwait - whead;
+          const int nout = min(na + nnk, kCap);
+          warp_tile_merge((wb ? T.wk1 : T.wk0) + whead, (wb ? T.wv1 : T.wv0) + whead, na, rb ? T.nk1 : T.nk0,
+                          rb ? T.nv1 : T.nv0, nnk, wb ? T.wk0 : T.wk1, wb ? T.wv0 : T.wv1, nout, rb ? T.nk0 : T.nk1,
                           rb ? T.nv0 : T.nv1);
-          pb ^= 1;
-          head = 0;
-          npl = nout;
+          wb ^= 1;
+          whead = 0;
+          nwait = nout;
           nnk = 0;
         }
         PT_END(2)
 
-        // ---- windows: every pending knot below F is final
+        // ---- windows: every knot below F is final
         while (!done) {
           PT_BEGIN
-          const float* PK = pb ? T.pk1 : T.pk0;
-          const int* PV = pb ? T.pv1 : T.pv0;
+          const float* WK = wb ? T.wk1 : T.wk0;
+          const int* WV = wb ? T.wv1 : T.wv0;
+          // waiting particles that have already started (FP32 ties) leave the list
+          while (whead < nwait) {
+            const int i = whead + lane;
+            const unsigned st_ = __ballot_sync(kFull, i < nwait && knots_done(T, WV[i]) > 0);
+            const int run = __ffs(~st_) - 1;  // leading started entries
+            whead += run < 0 ? 32 : run;
+            if (run >= 0) break;
+          }
+          whead = min(whead, nwait);
           bool fresh = false;
+          float h_fresh = kInf;
           if (n_act == 0) {
-            // the field is zero at Ta: restart at the first pending knot
-            if (head >= npl) break;
-            if (!(PK[head] < F)) break;
-            const int v0 = PV[head], e0 = v0 & 0xffff, k0 = v0 >> 16;
-            const float sg = knot_sigma(K, m, __ldg(p.theta + T.jj[e0]), k0);
+            // the field is zero at Ta: restart at the first waiting particle's first knot
+            if (whead >= nwait) break;
+            if (!(WK[whead] < F)) break;
+            const int e0 = WV[whead];
+            const float sg = knot_sigma(K, m, __ldg(p.theta + T.jj[e0]), 0);
             const float4 E0 = T.ent[e0];
             df kp = df{E0.x, E0.y};
             {
@@ -979,14 +990,20 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             }
             Ta = kp;
             fresh = true;
+            h_fresh = E0.z;
 #pragma unroll
             for (int d = 0; d <= D; ++d) carry[d] = (S)0;
           }
           // window end (relative to Ta): the bound F, and gamma times the
-          // lower edge of the smallest octave of h among the active particles
+          // lower edge of the smallest bin of h among the active particles
+          // (at a restart: gamma h of the particle restarted at)
           float U = kInf;
           if (F < kInf) U = (F - Ta.hi) - Ta.lo;
           bool capped = false;
+          if (gam * h_fresh < U) {
+            U = gam * h_fresh;
+            capped = true;
+          }
           if (n_act > 0) {
             // smallest occupied bin (4 per lane)
             const int4 c4 = *(const int4*)(T.lvl + 4 * lane);
@@ -1000,66 +1017,154 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
               capped = true;
             }
           }
-          // the window is a prefix of the pending list
-          const int nb_ = warp_count_below(PK, head, npl, Ta.hi + U);
-          int nc = min(nb_, kW);
-          if (nc < nb_) {  // full: it ends at the first knot left out
-            U = (PK[head + nc] - Ta.hi) - Ta.lo;
-            capped = false;
-          }
           PT_END(3)
           PT_BEGIN
-          // load it lane-major (lane l holds knots l*kKpl ... l*kKpl+kKpl-1,
-          // kept in shared memory at r * 32 + l), positions relative to Ta
-          // from the double-float centre
-          float* su = T.wdl + kW * D;
-          int* sv = (int*)(su + kW);
-          float cap2 = kInf;
-#pragma unroll 2
-          for (int r = 0; r < kKpl; ++r) {
-            const int i = lane * kKpl + r;
-            int vv = -1;
-            float u = 0.f;
-            if (i < nc) {
-              vv = PV[head + i];
-              const int e = vv & 0xffff, k = vv >> 16;
-              const float4 E = T.ent[e];
-              const float hh = E.z, c = E.w;
-              const int j = T.jj[e];
-              const float base = (E.x - Ta.hi) + (E.y - Ta.lo);
-              u = fmaf(knot_sigma(K, m, __ldg(p.theta + j), k), hh, base);
-              float dl[D];
-              knot_delta<D>(p, j, hh, c, k, dl);
+          // ---- the window's knots: every active particle's next knots and the
+          // knots of the waiting particles that start inside the window, all
+          // below U, into the generation buffer (shared); in the same pass the
+          // anchor (exact field coefficients at Ta, every 2nd window) and the
+          // removal of finished particles from the active list
+          S A[D + 1];
+          const bool do_anchor = p.anchor_every > 0 && !fresh && (win_count % p.anchor_every) == 0;
+          float acc[D + 1];
 #pragma unroll
-              for (int d = 0; d < D; ++d) T.wdl[(r * D + d) * 32 + lane] = dl[d];
-              // a particle starting inside the window bounds it by its own
-              // gamma h, or by its first knot when that lies farther
-              if (k == 0) cap2 = fminf(cap2, fmaxf(u, gam * hh));
+          for (int d = 0; d <= D; ++d) acc[d] = 0.f;
+          float cap2 = kInf;
+          int T_all = 0;
+          int* hist = T.rh;  // 64 buckets of [0, U) + the emission counter
+#pragma unroll 1
+          for (int gen = 0;; ++gen) {
+            for (int b = lane; b <= 64; b += 32) hist[b] = 0;
+            __syncwarp();
+            const float hsc = U < kInf ? 64.f / U : 0.f;
+            // active particles (lanes [0, nal)) and the waiting particles whose
+            // first knot lies below U (lanes [nal, nal + ns))
+            const int ns = warp_count_below(WK, whead, nwait, Ta.hi + U);
+            int wr = 0;
+#pragma unroll 1
+            for (int b0 = 0; b0 < nal + ns; b0 += 32) {
+              const int i = b0 + lane;
+              int e = -1, kstart = 0;
+              bool keep = false, fin = false;
+              if (i < nal) {
+                e = T.act[i];
+                kstart = knots_done(T, e);
+                fin = kstart > K;
+                keep = !fin;
+              } else if (i < nal + ns) {
+                e = WV[whead + i - nal];
+                if (knots_done(T, e) != 0) e = -1;  // started already (FP32 ties)
+              }
+              if (e >= 0 && !fin) {
+                const float4 E = T.ent[e];
+                const int j = T.jj[e];
+                if (gen == 0 && do_anchor && keep) {
+                  float Ae[D + 1];
+                  entry_piece_at<D>(p, E, j, kstart, Ta, Ae);
+#pragma unroll
+                  for (int d = 0; d <= D; ++d) acc[d] += Ae[d];
+                }
+                const float2 th = __ldg(p.theta + j);
+                const float base = (E.x - Ta.hi) + (E.y - Ta.lo);
+#pragma unroll 1
+                for (int k = kstart; k <= K; ++k) {
+                  const float u = fmaf(knot_sigma(K, m, th, k), E.z, base);
+                  if (!(u < U)) break;
+                  // a particle starting inside the window bounds it by its own
+                  // gamma h, or by its first knot when that lies farther
+                  if (k == 0) cap2 = fminf(cap2, fmaxf(u, gam * E.z));
+                  const int pos = atomicAdd(&hist[64], 1);
+                  if (pos < kNK) {
+                    T.nk0[pos] = u;
+                    T.nv0[pos] = e | (k << 16);
+                  }
+                  atomicAdd(&hist[min(63, max(0, (int)(u * hsc)))], 1);
+                }
+              }
+              if (gen == 0 && b0 < nal) {
+                // drop finished particles (their slots go to the free stack)
+                const unsigned km = __ballot_sync(kFull, keep), fm = __ballot_sync(kFull, fin);
+                __syncwarp();
+                if (keep) T.act[wr + __popc(km & lanemask_lt())] = e;
+                if (fin) T.fre[nfree + __popc(fm & lanemask_lt())] = e;
+                wr += __popc(km);
+                nfree += __popc(fm);
+              }
             }
-            su[r * 32 + lane] = u;
-            sv[r * 32 + lane] = vv;
+            if (gen == 0) nal = wr;
+            __syncwarp();
+            T_all = hist[64];
+            if (T_all <= kNK || gen >= 8) break;
+            // too many knots below U for the buffer: shrink U to a bucket
+            // boundary keeping at most kW of them, and generate again
+            int cnt0 = 0, bcut = 0;
+            for (int b = 0; b < 64; ++b) {
+              if (cnt0 + hist[b] > kW) break;
+              cnt0 += hist[b];
+              bcut = b + 1;
+            }
+            U = bcut > 0 ? U * (bcut / 64.f) : U / 64.f;
+            capped = false;
+            cap2 = kInf;
+            __syncwarp();
+          }
+          if (T_all > kNK) {
+            st_flags |= 2;
+            T_all = kNK;
           }
           cap2 = warp_min(cap2);
+          if (do_anchor) {
+#pragma unroll
+            for (int d = 0; d <= D; ++d) A[d] = (S)warp_sum(acc[d]);
+          } else {
+#pragma unroll
+            for (int d = 0; d <= D; ++d) A[d] = fresh ? (S)0 : carry[d];
+          }
+          // sort by position (ties: slot, then knot index)
+          const int rb = warp_bucket_sort(T.nk0, T.nv0, T.nk1, T.nv1, T_all, T.rh);
+          const float* GK = rb ? T.nk1 : T.nk0;
+          const int* GV = rb ? T.nv1 : T.nv0;
           if (cap2 < U) {
             U = cap2;
             capped = true;
-            int first_out = kKpl;
-#pragma unroll 1
-            for (int r = 0; r < kKpl; ++r)
-              if (sv[r * 32 + lane] >= 0 && !(su[r * 32 + lane] < U)) {
-                first_out = r;
-                break;
-              }
-            const unsigned lm = __ballot_sync(kFull, first_out < kKpl);
-            if (lm) {
-              const int l0 = __ffs(lm) - 1;
-              const int r0 = __shfl_sync(kFull, first_out, l0);
-              nc = min(nc, l0 * kKpl + r0);
-            }
           }
+          int nc = warp_count_below(GK, 0, T_all, U);
+          if (nc > kW) {  // full: it ends at the first knot left out
+            nc = kW;
+            U = GK[kW];
+            capped = false;
+          }
+          PT_END(4)
+          PT_BEGIN
           if (nc == 0 && !capped) {
             PT_END(5)
             break;  // nothing final below F: wait for more particles
+          }
+          // load the window lane-major (lane l holds knots l*kKpl ... l*kKpl+kKpl-1),
+          // then stage it in shared memory at r * 32 + l with its difference coefficients
+          float uu[kKpl];
+          int pl[kKpl];
+#pragma unroll
+          for (int r = 0; r < kKpl; ++r) {
+            const int i = lane * kKpl + r;
+            uu[r] = i < nc ? GK[i] : 0.f;
+            pl[r] = i < nc ? GV[i] : -1;
+          }
+          __syncwarp();
+          float* su = T.wdl + kW * D;
+          int* sv = (int*)(su + kW);
+#pragma unroll 2
+          for (int r = 0; r < kKpl; ++r) {
+            if (pl[r] >= 0) {
+              const int e = pl[r] & 0xffff, k = pl[r] >> 16;
+              const float4 E = T.ent[e];
+              float dl[D];
+              knot_delta<D>(p, T.jj[e], E.z, E.w, k, dl);
+#pragma unroll
+              for (int d = 0; d < D; ++d) T.wdl[(r * D + d) * 32 + lane] = dl[d];
+            }
+            su[r * 32 + lane] = uu[r];
+            sv[r * 32 + lane] = pl[r];
           }
           const int cnt_l = min(max(nc - lane * kKpl, 0), kKpl);  // this lane's knots (a prefix)
           int nf = 0, nl = 0;
@@ -1090,24 +1195,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           PT_END(5)
 
           PT_BEGIN
-          // anchor: exact coefficients of the field at Ta
-          S A[D + 1];
-          const bool do_anchor = p.anchor_every > 0 && !fresh && (win_count % p.anchor_every) == 0;
-          if (do_anchor) {
-            float acc[D + 1];
-#pragma unroll
-            for (int d = 0; d <= D; ++d) acc[d] = 0.f;
-            active_pass<D>(p, T, nal, nfree, Ta, true, acc);
-#pragma unroll
-            for (int d = 0; d <= D; ++d) A[d] = (S)warp_sum(acc[d]);
-          } else {
-#pragma unroll
-            for (int d = 0; d <= D; ++d) A[d] = fresh ? (S)0 : carry[d];
-          }
-          PT_END(4)
-
-          PT_BEGIN
-          // mark the window's knots processed; active list and octave counts
+          // mark the window's knots processed; active list and bin counts
 #pragma unroll 1
           for (int r = 0; r < kKpl; ++r) {
             const bool valid = r < cnt_l;
@@ -1123,7 +1211,6 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           __syncwarp();
           n_act = act_after;
           st_maxact = max(st_maxact, n_act);
-          head += nc;
           my_knots += nc;
           ++st_win;
           ++win_count;
@@ -1371,16 +1458,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             T.jj[e] = j;
             atomicAnd(T.knc + (e >> 3), ~(15u << (4 * (e & 7))));
             const float2 th = __ldg(p.theta + j);
-            float* nk = T.nk0 + nnk + rank * KP1;
-            int* nv = T.nv0 + nnk + rank * KP1;
-            float k0 = 0.f;
-#pragma unroll 1
-            for (int k = 0; k <= K; ++k) {
-              const float key = tc.hi + fmaf(knot_sigma(K, m, th, k), h, tc.lo);
-              if (k == 0) k0 = key;
-              nk[k] = key;
-              nv[k] = e | (k << 16);
-            }
+            const float k0 = tc.hi + fmaf(knot_sigma(K, m, th, 0), h, tc.lo);  // first knot
+            T.nk0[nnk + rank] = k0;
+            T.nv0[nnk + rank] = e;
             // a first knot behind the processed part of the ray would mean the
             // ordering bound was violated: report it
             if (started && k0 < Ta.hi - 1e-6f * fabsf(Ta.hi)) st_flags |= 8;
@@ -1391,7 +1471,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           }
           nfree -= from_free;
           hwm += n_store - from_free;
-          nnk += n_store * KP1;
+          nnk += n_store;
           st_cand += n_new;
           dbg_nc += n_new;
           st_maxtab = max(st_maxtab, hwm - nfree);
