@@ -107,7 +107,7 @@ typedef struct {
   int precision;     /* sphdvr_precision */
   int anchor_every;  /* FP32_ANCHORED: re-anchor every n-th window (>= 1) */
   float ert_eps;     /* stop a ray once its transmittance drops below this; 0 = never */
-  int persistent;    /* 1: persistent CTAs pulling sub-tiles from a device work queue */
+  int persistent;    /* 1: render warps pull rays from a device work queue; 0: static stride */
   float window_h;    /* a window of knots spans at most window_h times the smallest
                         smoothing length among the ray's pending particles (> 0);
                         0 selects the default 1.0 */
@@ -188,7 +188,7 @@ sphdvr_status sphdvr_dataset_info(const sphdvr_dataset* ds, int64_t info[8]);
  * The call returns when the frame has been enqueued and its work buffers
  * are in place; it synchronises the stream only to size those buffers.
  * `opts` may be NULL (defaults: FP32_ANCHORED, anchor_every 2, ert_eps 1e-5,
- * non-persistent).  The kernel w (and its support q) is the one the table
+ * work queue).  The kernel w (and its support q) is the one the table
  * was built for.  Returns EOVERFLOW
  * (image still written, possibly wrong) if a per-ray buffer overflowed. */
 sphdvr_status sphdvr_render(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,

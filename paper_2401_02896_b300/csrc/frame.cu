@@ -371,7 +371,7 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
   p.scratch = w.table;
   p.work = w.work;
   p.n_items = n_tiles * kTile * kTile;
-  p.dynamic = (o && o->persistent) ? 1 : 0;
+  p.dynamic = o ? (o->persistent ? 1 : 0) : 1;
   size_t smem = render_smem_bytes(a.tf_n, dbg ? 1 : kRenderWarps);
   return dispatch_render(ctx, L->D, f64, dbg, p, grid, smem, st);
 }

@@ -176,7 +176,7 @@ def opts_struct(opts=None):
         opts.get("precision", "fp32_anchored"), str) else int(opts["precision"])
     o.anchor_every = int(opts.get("anchor_every", 2))
     o.ert_eps = float(opts.get("ert_eps", 1e-5))
-    o.persistent = int(opts.get("persistent", 0))
+    o.persistent = int(opts.get("persistent", 1))
     o.window_h = float(opts.get("window_h", 0.0))
     return o
 
