@@ -52,8 +52,6 @@ namespace sphdvr {
 
 constexpr int kCap = 4096;          // particle entries per ray
 constexpr int kNK = 512;            // new knots awaiting a merge (shared memory)
-constexpr int kKpl = 8;             // knots per lane in a window
-constexpr int kW = 32 * kKpl;       // window capacity (knots)
 constexpr int kLevels = 128;        // smoothing-length bins (quarter octaves) for the window limit
 constexpr int kLevelBase = (127 - 28) << 2;  // bin 0 starts at h = 2^-28
 constexpr int kRenderWarps = 4;     // rays (warps) per CTA in normal rendering
@@ -64,7 +62,7 @@ constexpr int kTableWords = 11 * kCap;
 // processed-knot counts (4 bits per entry), and a work area shared in time by the new-knot buffers (two key/value
 // buffers, the second also stages pending knots during a merge) and the
 // window's difference coefficients
-constexpr int kWorkBytes = 4 * kNK * 4;  // >= the window: kW * (D + 1) floats for D <= 7
+constexpr int kWorkBytes = 4 * kNK * 4;
 constexpr int kWarpSmem = 256 * 4 + kLevels * 4 + kCap / 2 + kWorkBytes;
 
 struct RenderParams {
@@ -752,6 +750,11 @@ static __device__ __noinline__ int nearest_entry_fp64(const df* wv, float h, int
 // transfer function.
 template <int D, typename S, int NW, bool DBG>
 __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderParams p) {
+  // knots per lane in a window: as many as the shared work area holds with the
+  // window's D difference coefficients, its positions and its knot ids
+  constexpr int KPL = D <= 2 ? 16 : (D == 3 ? 12 : 8);
+  constexpr int WCAP = 32 * KPL;
+  static_assert(WCAP * (D + 2) * 4 <= kWorkBytes && WCAP <= kNK, "window does not fit the work area");
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float4* s_tf = (float4*)smem;
@@ -1096,10 +1099,10 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             T_all = hist[64];
             if (T_all <= kNK || gen >= 8) break;
             // too many knots below U for the buffer: shrink U to a bucket
-            // boundary keeping at most kW of them, and generate again
+            // boundary keeping at most WCAP of them, and generate again
             int cnt0 = 0, bcut = 0;
             for (int b = 0; b < 64; ++b) {
-              if (cnt0 + hist[b] > kW) break;
+              if (cnt0 + hist[b] > WCAP) break;
               cnt0 += hist[b];
               bcut = b + 1;
             }
@@ -1129,9 +1132,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             capped = true;
           }
           int nc = warp_count_below(GK, 0, T_all, U);
-          if (nc > kW) {  // full: it ends at the first knot left out
-            nc = kW;
-            U = GK[kW];
+          if (nc > WCAP) {  // full: it ends at the first knot left out
+            nc = WCAP;
+            U = GK[WCAP];
             capped = false;
           }
           PT_END(4)
@@ -1140,21 +1143,21 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             PT_END(5)
             break;  // nothing final below F: wait for more particles
           }
-          // load the window lane-major (lane l holds knots l*kKpl ... l*kKpl+kKpl-1),
+          // load the window lane-major (lane l holds knots l*KPL ... l*KPL+KPL-1),
           // then stage it in shared memory at r * 32 + l with its difference coefficients
-          float uu[kKpl];
-          int pl[kKpl];
+          float uu[KPL];
+          int pl[KPL];
 #pragma unroll
-          for (int r = 0; r < kKpl; ++r) {
-            const int i = lane * kKpl + r;
+          for (int r = 0; r < KPL; ++r) {
+            const int i = lane * KPL + r;
             uu[r] = i < nc ? GK[i] : 0.f;
             pl[r] = i < nc ? GV[i] : -1;
           }
           __syncwarp();
-          float* su = T.wdl + kW * D;
-          int* sv = (int*)(su + kW);
+          float* su = T.wdl + WCAP * D;
+          int* sv = (int*)(su + WCAP);
 #pragma unroll 2
-          for (int r = 0; r < kKpl; ++r) {
+          for (int r = 0; r < KPL; ++r) {
             if (pl[r] >= 0) {
               const int e = pl[r] & 0xffff, k = pl[r] >> 16;
               const float4 E = T.ent[e];
@@ -1166,7 +1169,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             su[r * 32 + lane] = uu[r];
             sv[r * 32 + lane] = pl[r];
           }
-          const int cnt_l = min(max(nc - lane * kKpl, 0), kKpl);  // this lane's knots (a prefix)
+          const int cnt_l = min(max(nc - lane * KPL, 0), KPL);  // this lane's knots (a prefix)
           int nf = 0, nl = 0;
           float umax = 0.f;
 #pragma unroll 1
@@ -1190,14 +1193,14 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           }
           Uend = fmaxf(Uend, 0.f);
 #pragma unroll 1
-          for (int r = 0; r < kKpl; ++r)
+          for (int r = 0; r < KPL; ++r)
             su[r * 32 + lane] = r < cnt_l ? fminf(fmaxf(su[r * 32 + lane], 0.f), Uend) : Uend;
           PT_END(5)
 
           PT_BEGIN
           // mark the window's knots processed; active list and bin counts
 #pragma unroll 1
-          for (int r = 0; r < kKpl; ++r) {
+          for (int r = 0; r < KPL; ++r) {
             const bool valid = r < cnt_l;
             const int vv = sv[r * 32 + lane];
             const int e = vv & 0xffff, k = vv >> 16;
@@ -1280,7 +1283,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           // next lane's first knot (piece end for this lane's last knot)
           float unext = __shfl_down_sync(kFull, ufirst, 1);
           if (lane == 31) unext = Uend;
-          const float ulane_end = cnt_l == kKpl ? unext : Uend;
+          const float ulane_end = cnt_l == KPL ? unext : Uend;
           // ---- composite this lane's pieces: lane 0 first takes the leading
           // piece [0, u_0] (the whole window if it has no knot) with the
           // window's incoming polynomial, then every lane one piece per knot
