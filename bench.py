@@ -43,6 +43,11 @@ WORKLOADS = {
 
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
+# DRAM bytes (read + write) of one render launch of the default workload, from
+# the ncu capture recorded in profiles/launches_halo16m_2048.md (the render
+# kernel as it is in this tree); None for other workloads or image sizes.
+PROFILED_DRAM_BYTES = {("halo16m", 2048): 239.85e9 + 819.21e9}
+
 
 def flops_per_segment(K, D):
     """Algorithmic FP32 operations per particle-ray segment (FMA = 2):
@@ -265,12 +270,12 @@ def main():
             o_ = torch.empty((r_, r_, 4), dtype=torch.float32, device=dev)
             outs.append(o_)
             tickets.append(srv.submit(ds, lut, c_, tf, opts, o_.data_ptr()))
-            time.sleep(float(rng.exponential(0.25)))
+            time.sleep(float(rng.exponential(1.5)))
         for t_ in tickets:
             srv.wait(t_, -1)
         sv = srv.stats()
         srv.destroy()
-        serving = dict(requests=args.serve_requests, sizes=sizes, arrivals="Poisson, mean gap 250 ms", workers=2,
+        serving = dict(requests=args.serve_requests, sizes=sizes, arrivals="Poisson, mean gap 1.5 s", workers=2,
                        p50_ms=sv["p50_ms"], p99_ms=sv["p99_ms"], mrays_per_s=sv["rays_per_s"] / 1e6,
                        failed=int(sv["failed"]))
         del outs
@@ -295,7 +300,8 @@ def main():
                              max_table=st0["max_table"], overflow=st0["overflow"], ert_rays=st0["ert_rays"],
                              render_kernel_ms=kern_s * 1e3),
             roofline=dict(bound="alu", achieved=achieved, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
-                          frac=achieved / FP32_PEAK_TFLOPS, traffic=None,
+                          frac=achieved / FP32_PEAK_TFLOPS,
+                          traffic=PROFILED_DRAM_BYTES.get((args.workload, w["res"])),
                           note="FP32 peak = 148 SMs x 128 lanes x 2 x 2032 MHz; algorithmic %d FLOP/segment" % fps),
             e2e=dict(value=e2e_val, unit="Mrays/s", h2d_bytes_per_step=int(tf["rgba"].nbytes),
                      d2h_bytes_per_step=int(W * H * 16)),
