@@ -148,6 +148,18 @@ sphdvr_status sphdvr_last_error(const sphdvr_ctx* ctx, char* buf, size_t len);
  *   (err = ||S_L - B_L||_2, may be NULL).  EINVAL on bad arguments. */
 sphdvr_status sphdvr_lut_build(int kernel, int K, int D, int n_lambda, double* theta, double* pieces, double* err);
 
+/* Per-particle relative approximation error E of a table, from its per-entry
+ * errors err[j] = ||S_{L_j} - B_{L_j}||_2 (host array, n_lambda >= 3 entries on
+ * the uniform grid above, e.g. from sphdvr_lut_build): the error along the rays
+ * of one direction integrated over all of them and divided by the L2 norm of a
+ * normalised particle's contribution -- the approximation part of the paper's
+ * combined accuracy measure (Sec. "Combined Accuracy Measure"; its
+ * quantisation part is zero on this library's floating-point path).  A
+ * readout for users choosing (kernel, K, D), e.g. M4 with K = 4, D = 3 gives
+ * about 9.3e-4.  EINVAL on a bad kernel, n_lambda < 3, NULL pointers or
+ * negative / non-finite errors. */
+sphdvr_status sphdvr_lut_error_measure(int kernel, int n_lambda, const double* err, double* E);
+
 /* Upload a table (host arrays in the layout above, e.g. from
  * sphdvr_lut_build) to the context's device as FP32 knots, difference
  * coefficients (Sec. 2) and pieces.  The library keeps no reference to the

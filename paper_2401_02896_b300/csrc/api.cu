@@ -225,6 +225,10 @@ sphdvr_status sphdvr_last_error(const sphdvr_ctx* c, char* buf, size_t len) {
   return SPHDVR_OK;
 }
 
+sphdvr_status sphdvr_lut_error_measure(int kernel, int n_lambda, const double* err, double* E) {
+  return lut_error_measure_host(kernel, n_lambda, err, E) == 0 ? SPHDVR_OK : SPHDVR_EINVAL;
+}
+
 sphdvr_status sphdvr_lut_build(int kernel, int K, int D, int n_lambda, double* theta, double* pieces, double* err) {
   if (kernel < 0 || kernel > 3 || K < 1 || K > 4 || D < 1 || D > 6 || n_lambda < 2 || n_lambda > 65536 || !theta ||
       !pieces)

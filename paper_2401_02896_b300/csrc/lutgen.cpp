@@ -422,6 +422,44 @@ ld search(const Problem& P, ld* best) {
 
 }  // namespace
 
+// Per-particle relative error of a table of optimal approximations: the error
+// along every ray of one direction, integrated over the rays and divided by
+// the L2 norm of a normalised particle's contribution (the paper's combined
+// accuracy measure, approximation part):
+//   E = (1 / kappa) (2 pi int_0^q L err(L)^2 dL)^(1/2),
+//   kappa^2 = int w(|x|)^2 dV = 4 pi int_0^q r^2 w(r)^2 dr.
+// kappa by 16-point Gauss-Legendre on [0, 1] and [1, q] (exact for these
+// piecewise polynomial kernels); the L integral by composite Simpson over the
+// table's uniform entries (the last interval by the trapezoid rule when the
+// entry count is even).
+int lut_error_measure_host(int kernel, int n_lambda, const double* err, double* E) {
+  if (kernel < 0 || kernel > 3 || n_lambda < 3 || !err || !E) return 1;
+  for (int j = 0; j < n_lambda; ++j)
+    if (!(err[j] >= 0) || !std::isfinite(err[j])) return 1;
+  const ld q = kernel == 3 ? 1 : 2;
+  const GL16& g = gl16();
+  ld k2 = 0;
+  const ld ends[3] = {0, 1, q};
+  for (int seg = 0; seg < 2; ++seg) {
+    const ld a = ends[seg], b = ends[seg + 1];
+    if (!(b > a)) continue;
+    for (int i = 0; i < 16; ++i) {
+      const ld r = 0.5L * (a + b) + 0.5L * (b - a) * g.x[i];
+      const ld w = kernel_value(kernel, r);
+      k2 += 0.5L * (b - a) * g.w[i] * r * r * w * w;
+    }
+  }
+  k2 *= 4 * kPi;
+  const ld hstep = q / (n_lambda - 1);
+  auto f = [&](int j) { return (ld)j * hstep * (ld)err[j] * (ld)err[j]; };
+  const int nodd = (n_lambda % 2 == 1) ? n_lambda : n_lambda - 1;
+  ld I = 0;
+  for (int j = 0; j + 2 < nodd; j += 2) I += hstep / 3 * (f(j) + 4 * f(j + 1) + f(j + 2));
+  if (nodd < n_lambda) I += 0.5L * hstep * (f(n_lambda - 2) + f(n_lambda - 1));
+  *E = (double)(std::sqrt(2 * kPi * I) / std::sqrt(k2));
+  return 0;
+}
+
 int build_lut_host(int kernel, int K, int D, int n_lambda, double* theta, double* pieces, double* err) {
   if (kernel < 0 || kernel > 3 || K < 1 || K > 2 * kMaxM || D < 1 || D > kMaxD || n_lambda < 2 ||
       n_lambda > 65536 || !theta || !pieces)

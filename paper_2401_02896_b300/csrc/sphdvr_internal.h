@@ -13,6 +13,8 @@ namespace sphdvr {
 
 // Host look-up-table builder (lutgen.cpp).  Returns 0 on success.
 int build_lut_host(int kernel, int K, int D, int n_lambda, double* theta, double* pieces, double* err);
+// Per-particle relative approximation error of a table from its per-entry errors.  Returns 0 on success.
+int lut_error_measure_host(int kernel, int n_lambda, const double* err, double* E);
 
 constexpr int kChunk = 32;       // particles per chunk of the acceleration structure
 constexpr int kTile = 16;        // binning tile edge in pixels

@@ -87,6 +87,8 @@ def _load():
                                               ctypes.POINTER(RenderOpts), vp, vp]),
         "sphdvr_render_static_scratch": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                                        ctypes.POINTER(RenderOpts), vp, vp]),
+        "sphdvr_lut_error_measure": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                    ctypes.POINTER(ctypes.c_double)]),
         "sphdvr_frame_stats": (ctypes.c_int, [vp, i64p]),
         "sphdvr_server_create": (ctypes.c_int, [vp, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]),
         "sphdvr_server_submit": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
@@ -194,6 +196,15 @@ def sphdvr_create(device=0):
 
 def sphdvr_destroy(ctx):
     return _check(_lib.sphdvr_destroy(ctx))
+
+
+def sphdvr_lut_error_measure(kernel, err):
+    """Per-particle relative approximation error of a table from its per-entry errors (host)."""
+    e = np.ascontiguousarray(err, dtype=np.float64)
+    out = ctypes.c_double()
+    _check(_lib.sphdvr_lut_error_measure(_kid(kernel), int(e.shape[0]),
+                                         e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(out)))
+    return out.value
 
 
 def sphdvr_lut_build(kernel, K, D, n_lambda):

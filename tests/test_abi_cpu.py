@@ -103,3 +103,28 @@ def test_library_table_poly6_exact():
         nb = math.sqrt(oracle.ray_norm2("poly6", lam[j]))
         assert err[j] <= 1e-10 * nb
         assert abs(th[j][0] - math.sqrt(1 - lam[j] ** 2)) < 1e-5
+
+
+@pytest.mark.parametrize("key", ["2,1", "4,3", "3,2", "4,4", "1,6", "2,5"])
+def test_lut_error_measure_reproduces_printed_errors(key):
+    """sphdvr_lut_error_measure on the library's own table gives the paper's printed E_{K,D} (Sec. 5.2 figure)."""
+    table = json.load(open(os.path.join(HERE, "golden", "paper_error_table.json")))
+    K, D = map(int, key.split(","))
+    _, _, err = S.sphdvr_lut_build("m4", K, D, 257)
+    E = S.sphdvr_lut_error_measure("m4", err)
+    assert abs(E / table["E"][key] - 1) < 1.5e-4
+
+
+def test_lut_error_measure_special_cases():
+    # poly6 is a polynomial in r^2: its ray restriction is represented exactly for D = 6
+    _, _, err = S.sphdvr_lut_build("poly6", 1, 6, 33)
+    assert S.sphdvr_lut_error_measure("poly6", err) < 1e-9
+    # a constant per-entry error e gives e * sqrt(pi q^2) / kappa (closed form of the Lambda integral)
+    kap = math.sqrt(4 * math.pi * quad(lambda r: (r * oracle.kernel_w("wendland_c2", r)) ** 2, 0, 2, epsabs=1e-16)[0])
+    for n in (65, 64):
+        E = S.sphdvr_lut_error_measure("wendland_c2", np.full(n, 1e-3))
+        assert abs(E / (1e-3 * math.sqrt(math.pi * 4.0) / kap) - 1) < 1e-9
+    for bad in (np.zeros(2), np.array([0.0, -1.0, 0.0]), np.array([0.0, np.nan, 0.0])):
+        with pytest.raises(S.SphdvrError) as e:
+            S.sphdvr_lut_error_measure("m4", bad)
+        assert e.value.status == S.EINVAL
