@@ -293,3 +293,25 @@ def test_invalid_inputs_are_rejected(S, ctx):
     finally:
         S.sphdvr_dataset_free(ds)
         S.sphdvr_lut_free(lt)
+
+
+def test_static_and_dynamic_schedules_agree(S, ctx):
+    """The static ray stride and the atomic work queue render the same image (same per-ray arithmetic)."""
+    import torch
+
+    P = SY.halo_mixture(100_000, seed=SY.BASE_SEED + 17)
+    lut = oracle_lut("wendland_c2", 4, 3, 4096)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.orbit_camera(120, 88)
+    tf = SY.tf_density(P["value"])
+    try:
+        a = torch.zeros((88, 120, 4), dtype=torch.float32, device="cuda")
+        b = torch.zeros_like(a)
+        S.sphdvr_render(ctx, ds, lt, cam, tf, dict(persistent=0), a.data_ptr())
+        S.sphdvr_render(ctx, ds, lt, cam, tf, dict(persistent=1), b.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        assert a[..., 3].max().item() > 0.05
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
