@@ -198,7 +198,10 @@ def main():
     lut = S.sphdvr_lut_create(ctx, w["kernel"], w["K"], w["D"], w["n_lambda"], th, pc)
     dev = torch.device("cuda", local)
     tens = {k: torch.from_numpy(np.ascontiguousarray(P[k])).to(dev) for k in ("pos", "h", "mass", "density", "value")}
+    torch.cuda.synchronize()
+    t_build = time.perf_counter()
     ds = S.sphdvr_dataset_create(ctx, tens["pos"], tens["h"], tens["mass"], tens["density"], tens["value"])
+    t_build = time.perf_counter() - t_build  # the call returns after the build has completed
     del tens
     cam = camera_for(w, rank)
     opts = dict(precision=args.precision, ert_eps=1e-5)
@@ -310,6 +313,10 @@ def main():
         )
         if serving:
             line["serving"] = serving
+        info = S.sphdvr_dataset_info(ds)
+        line["dataset_build"] = dict(ms=t_build * 1e3, particles_per_s=w["n"] / t_build,
+                                     input_bytes=int(w["n"] * 28), resident_bytes=int(info["bytes"]),
+                                     note="inputs already on the device; levels, Morton keys, radix sort, chunks")
         if not args.no_cpu_baseline:
             cb = cpu_oracle_rate(P, w, tf, args.cpu_pixels, seed=77)
             line["cpu_baseline"] = dict(value=cb["rays_per_s"] / 1e6, unit="Mrays/s", cores=cb["cores"], kind="oracle",
