@@ -64,7 +64,12 @@ typedef enum {
    * the paper's plain scheme, which exhibits the drift of Sec. 4.1. */
   SPHDVR_PREC_FP32_NAIVE = 1,
   /* as NAIVE, but the recurrence's running coefficients are FP64. */
-  SPHDVR_PREC_FP64_NAIVE = 2
+  SPHDVR_PREC_FP64_NAIVE = 2,
+  /* FP32 recurrence run front to back with reinitialisation knots at
+   * t = j * reinit_dt (j integer) on every ray: there the running
+   * coefficients are replaced by the exact sum of the active particles' own
+   * pieces -- the paper's first mitigation of the drift (Sec. 4.1). */
+  SPHDVR_PREC_FP32_REINIT = 3
 } sphdvr_precision;
 
 /* Viewing rays.  Basis: f = normalize(target - eye), r = normalize(f x up),
@@ -111,7 +116,8 @@ typedef struct {
   float window_h;    /* a window of knots spans at most window_h times the smallest
                         smoothing length among the ray's pending particles (> 0);
                         0 selects the default 1.0 */
-  int reserved[3];   /* must be 0 */
+  float reinit_dt;   /* FP32_REINIT: spacing of the reinitialisation knots along t (> 0); else 0 */
+  int reserved[2];   /* must be 0 */
 } sphdvr_render_opts;
 
 typedef struct sphdvr_ctx sphdvr_ctx;

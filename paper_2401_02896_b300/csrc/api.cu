@@ -125,11 +125,15 @@ sphdvr_status pack_tf(sphdvr_ctx* ctx, const sphdvr_tf* tf, std::vector<float4>&
 
 sphdvr_status check_opts(sphdvr_ctx* ctx, const sphdvr_render_opts* o) {
   if (!o) return SPHDVR_OK;
-  if (o->precision < 0 || o->precision > 2) return set_err(ctx, SPHDVR_EINVAL, "opts: precision out of range");
+  if (o->precision < 0 || o->precision > 3) return set_err(ctx, SPHDVR_EINVAL, "opts: precision out of range");
+  if (!(o->reinit_dt >= 0.f) || !std::isfinite(o->reinit_dt))
+    return set_err(ctx, SPHDVR_EINVAL, "opts: reinit_dt must be finite and >= 0");
+  if (o->precision == 3 && !(o->reinit_dt > 0.f))
+    return set_err(ctx, SPHDVR_EINVAL, "opts: FP32_REINIT needs reinit_dt > 0");
   if (o->precision == 0 && o->anchor_every < 1) return set_err(ctx, SPHDVR_EINVAL, "opts: anchor_every must be >= 1");
   if (!(o->ert_eps >= 0.f && o->ert_eps < 1.f)) return set_err(ctx, SPHDVR_EINVAL, "opts: ert_eps must be in [0, 1)");
   if (!(o->window_h >= 0.f) || !std::isfinite(o->window_h)) return set_err(ctx, SPHDVR_EINVAL, "opts: window_h must be >= 0");
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (o->reserved[i]) return set_err(ctx, SPHDVR_EINVAL, "opts: reserved fields must be 0");
   return SPHDVR_OK;
 }

@@ -353,6 +353,7 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
   int prec = o ? o->precision : SPHDVR_PREC_FP32_ANCHORED;
   p.anchor_every = (prec == SPHDVR_PREC_FP32_ANCHORED) ? std::max(1, o ? o->anchor_every : 2) : 0;
   p.window_h = (o && o->window_h > 0.f) ? o->window_h : 1.0f;
+  p.reinit_dt = (prec == SPHDVR_PREC_FP32_REINIT) ? o->reinit_dt : 0.f;
   float eps = o ? o->ert_eps : 1e-5f;
   p.tau_ert = eps > 0.f ? -std::log(eps) : 0.f;
   p.out = a.out;

@@ -92,6 +92,7 @@ struct RenderParams {
   const float4* tf;
   // options
   int anchor_every;  // 0: never (naive recurrence)
+  float reinit_dt;   // > 0: re-anchor at the reinitialisation knots t = j reinit_dt (naive in between)
   float window_h;    // window length limit in units of the smallest h it touches
   float tau_ert;     // stop when accumulated optical depth exceeds this
   float* out;
@@ -861,6 +862,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
 #pragma unroll
     for (int d = 0; d <= D; ++d) carry[d] = (S)0;
     int hwm = 0, nfree = 0, nal = 0, n_act = 0, whead = 0, nwait = 0, wb = 0, nnk = 0, win_count = 0;
+    bool at_reinit = false;  // the next window starts at a reinitialisation knot
     long long dbg_np = 0, dbg_nc = 0;
     unsigned long long my_knots = 0;
     for (int b = lane; b < kLevels; b += 32) T.lvl[b] = 0;
@@ -1007,6 +1009,17 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             U = gam * h_fresh;
             capped = true;
           }
+          // reinitialisation knots: the window ends at the next one
+          float ureinit = -1.f;
+          if (p.reinit_dt > 0.f) {
+            const double ta = (double)Ta.hi + (double)Ta.lo, dt = (double)p.reinit_dt;
+            const float ur = (float)((floor(ta / dt + 1e-6) + 1.0) * dt - ta);
+            if (ur < U) {
+              U = ur;
+              capped = true;
+              ureinit = ur;
+            }
+          }
           if (n_act > 0) {
             // smallest occupied bin (4 per lane)
             const int4 c4 = *(const int4*)(T.lvl + 4 * lane);
@@ -1028,7 +1041,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           // anchor (exact field coefficients at Ta, every 2nd window) and the
           // removal of finished particles from the active list
           S A[D + 1];
-          const bool do_anchor = p.anchor_every > 0 && !fresh && (win_count % p.anchor_every) == 0;
+          const bool do_anchor =
+              !fresh && ((p.anchor_every > 0 && (win_count % p.anchor_every) == 0) || (p.reinit_dt > 0.f && at_reinit));
           float acc[D + 1];
 #pragma unroll
           for (int d = 0; d <= D; ++d) acc[d] = 0.f;
@@ -1192,6 +1206,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             Uend = umax;
           }
           Uend = fmaxf(Uend, 0.f);
+          at_reinit = ureinit >= 0.f && !final_w && Uend == ureinit;  // the next window starts on one
 #pragma unroll 1
           for (int r = 0; r < KPL; ++r)
             su[r * 32 + lane] = r < cnt_l ? fminf(fmaxf(su[r * 32 + lane], 0.f), Uend) : Uend;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libsphdvr.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, EOVERFLOW, EDEVICE, ENOTFOUND = range(9)
 KERNELS = {"m4": 0, "wendland_c2": 1, "wendland_c4": 2, "poly6": 3}
-PRECISIONS = {"fp32_anchored": 0, "fp32_naive": 1, "fp64_naive": 2}
+PRECISIONS = {"fp32_anchored": 0, "fp32_naive": 1, "fp64_naive": 2, "fp32_reinit": 3}
 
 
 class SphdvrError(RuntimeError):
@@ -59,7 +59,8 @@ class RenderOpts(ctypes.Structure):
         ("ert_eps", ctypes.c_float),
         ("persistent", ctypes.c_int),
         ("window_h", ctypes.c_float),
-        ("reserved", ctypes.c_int * 3),
+        ("reinit_dt", ctypes.c_float),
+        ("reserved", ctypes.c_int * 2),
     ]
 
 
@@ -180,6 +181,7 @@ def opts_struct(opts=None):
     o.ert_eps = float(opts.get("ert_eps", 1e-5))
     o.persistent = int(opts.get("persistent", 1))
     o.window_h = float(opts.get("window_h", 0.0))
+    o.reinit_dt = float(opts.get("reinit_dt", 0.0))
     return o
 
 

@@ -315,3 +315,34 @@ def test_static_and_dynamic_schedules_agree(S, ctx):
     finally:
         S.sphdvr_dataset_free(ds)
         S.sphdvr_lut_free(lt)
+
+
+def test_reinitialisation_knots(S, ctx):
+    """FP32 recurrence with reinitialisation knots every reinit_dt along t (Sec. 4.1): dense knots bound the
+    drift like re-anchored windows, knots farther apart than the rays let it grow as in the plain recurrence."""
+    P = SY.uniform_cube()
+    lut = oracle_lut("m4", 4, 3, 4096)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.ortho_camera_z(32, 32)
+    tf = SY.tf_bumps()
+    pix = np.arange(32 * 32)
+    R = oracle.render(_orc_particles(P), lut, cam, tf, pix, field_cap=4096)
+
+    def worst(opts):
+        g = S.sphdvr_debug_rays(ctx, ds, lt, cam, tf, dict(opts, ert_eps=0.0), pix, field_cap=4096, D=3)
+        return max(field_rel_l2(g["field"][r, :g["counts"][r, 2]], R["field"][r, :R["stats"][r, 5]], 3)
+                   for r in range(len(pix)) if R["stats"][r, 0])
+
+    try:
+        dense = worst(dict(precision="fp32_reinit", reinit_dt=0.02))
+        sparse = worst(dict(precision="fp32_reinit", reinit_dt=100.0))
+        naive = worst(dict(precision="fp32_naive"))
+        print(dense, sparse, naive)
+        assert dense <= FIELD_REL_L2
+        assert sparse > 10 * dense
+        assert sparse == pytest.approx(naive, rel=0.5)
+        with pytest.raises(S.SphdvrError):
+            S.sphdvr_debug_rays(ctx, ds, lt, cam, tf, dict(precision="fp32_reinit"), pix[:4], D=3)
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
