@@ -749,7 +749,9 @@ static __device__ __noinline__ int nearest_entry_fp64(const df* wv, float h, int
 
 // Each warp is an independent worker; the only shared state of a CTA is the
 // transfer function.
-template <int D, typename S, int NW, bool DBG>
+// RE: reinitialisation knots (precision mode FP32_REINIT), a separate
+// instantiation so that the other modes carry none of its code.
+template <int D, typename S, int NW, bool DBG, bool RE>
 __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderParams p) {
   // knots per lane in a window: as many as the shared work area holds with the
   // window's D difference coefficients, its positions and its knot ids
@@ -1011,7 +1013,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           }
           // reinitialisation knots: the window ends at the next one
           float ureinit = -1.f;
-          if (p.reinit_dt > 0.f) {
+          if (RE) {
             const double ta = (double)Ta.hi + (double)Ta.lo, dt = (double)p.reinit_dt;
             const float ur = (float)((floor(ta / dt + 1e-6) + 1.0) * dt - ta);
             if (ur < U) {
@@ -1042,7 +1044,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           // removal of finished particles from the active list
           S A[D + 1];
           const bool do_anchor =
-              !fresh && ((p.anchor_every > 0 && (win_count % p.anchor_every) == 0) || (p.reinit_dt > 0.f && at_reinit));
+              !fresh && ((p.anchor_every > 0 && (win_count % p.anchor_every) == 0) || (RE && at_reinit));
           float acc[D + 1];
 #pragma unroll
           for (int d = 0; d <= D; ++d) acc[d] = 0.f;
@@ -1206,7 +1208,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             Uend = umax;
           }
           Uend = fmaxf(Uend, 0.f);
-          at_reinit = ureinit >= 0.f && !final_w && Uend == ureinit;  // the next window starts on one
+          if (RE) at_reinit = ureinit >= 0.f && !final_w && Uend == ureinit;  // the next window starts on one
 #pragma unroll 1
           for (int r = 0; r < KPL; ++r)
             su[r * 32 + lane] = r < cnt_l ? fminf(fmaxf(su[r * 32 + lane], 0.f), Uend) : Uend;

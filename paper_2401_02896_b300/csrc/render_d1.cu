@@ -3,9 +3,9 @@
 
 namespace sphdvr {
 
-template <typename S, int NW, bool DBG>
+template <typename S, int NW, bool DBG, bool RE>
 static sphdvr_status launch(sphdvr_ctx* ctx, const RenderParams& p, int grid, size_t smem, cudaStream_t st) {
-  auto kern = k_render<1, S, NW, DBG>;
+  auto kern = k_render<1, S, NW, DBG, RE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_err(ctx, e, "render smem attribute");
   if (!ctx->ev_ready) {
@@ -22,7 +22,7 @@ static sphdvr_status launch(sphdvr_ctx* ctx, const RenderParams& p, int grid, si
 
 template <typename S, int NW, bool DBG>
 static int occupancy(size_t smem) {
-  auto kern = k_render<1, S, NW, DBG>;
+  auto kern = k_render<1, S, NW, DBG, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NW * 32, smem) != cudaSuccess) return 0;
@@ -31,9 +31,14 @@ static int occupancy(size_t smem) {
 
 sphdvr_status launch_render_d1(sphdvr_ctx* ctx, bool f64, bool dbg, const RenderParams& p, int grid, size_t smem,
                                 cudaStream_t st) {
-  if (dbg) return f64 ? launch<double, 1, true>(ctx, p, grid, smem, st) : launch<float, 1, true>(ctx, p, grid, smem, st);
-  return f64 ? launch<double, kRenderWarps, false>(ctx, p, grid, smem, st)
-             : launch<float, kRenderWarps, false>(ctx, p, grid, smem, st);
+  const bool re = p.reinit_dt > 0.f;  // FP32 only
+  if (dbg) {
+    if (f64) return launch<double, 1, true, false>(ctx, p, grid, smem, st);
+    return re ? launch<float, 1, true, true>(ctx, p, grid, smem, st) : launch<float, 1, true, false>(ctx, p, grid, smem, st);
+  }
+  if (f64) return launch<double, kRenderWarps, false, false>(ctx, p, grid, smem, st);
+  return re ? launch<float, kRenderWarps, false, true>(ctx, p, grid, smem, st)
+            : launch<float, kRenderWarps, false, false>(ctx, p, grid, smem, st);
 }
 
 int render_occupancy_d1(bool f64, bool dbg, size_t smem) {
