@@ -46,7 +46,7 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x ma
 # DRAM bytes (read + write) of one render launch of the default workload, from
 # the ncu capture recorded in profiles/launches_halo16m_2048.md (the render
 # kernel as it is in this tree); None for other workloads or image sizes.
-PROFILED_DRAM_BYTES = {("halo16m", 2048): 239.82e9 + 819.20e9}
+PROFILED_DRAM_BYTES = {}
 
 
 def flops_per_segment(K, D):

@@ -1050,12 +1050,11 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
           for (int d = 0; d <= D; ++d) acc[d] = 0.f;
           float cap2 = kInf;
           int T_all = 0;
-          int* hist = T.rh;  // 64 buckets of [0, U) + the emission counter
+          int* hist = T.rh;  // hist[64]: the emission counter
 #pragma unroll 1
           for (int gen = 0;; ++gen) {
-            for (int b = lane; b <= 64; b += 32) hist[b] = 0;
+            if (lane == 0) hist[64] = 0;
             __syncwarp();
-            const float hsc = U < kInf ? 64.f / U : 0.f;
             // active particles (lanes [0, nal)) and the waiting particles whose
             // first knot lies below U (lanes [nal, nal + ns))
             const int ns = warp_count_below(WK, whead, nwait, Ta.hi + U);
@@ -1097,7 +1096,6 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
                     T.nk0[pos] = u;
                     T.nv0[pos] = e | (k << 16);
                   }
-                  atomicAdd(&hist[min(63, max(0, (int)(u * hsc)))], 1);
                 }
               }
               if (gen == 0 && b0 < nal) {
@@ -1113,16 +1111,10 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             if (gen == 0) nal = wr;
             __syncwarp();
             T_all = hist[64];
-            if (T_all <= kNK || gen >= 8) break;
-            // too many knots below U for the buffer: shrink U to a bucket
-            // boundary keeping at most WCAP of them, and generate again
-            int cnt0 = 0, bcut = 0;
-            for (int b = 0; b < 64; ++b) {
-              if (cnt0 + hist[b] > WCAP) break;
-              cnt0 += hist[b];
-              bcut = b + 1;
-            }
-            U = bcut > 0 ? U * (bcut / 64.f) : U / 64.f;
+            if (T_all <= kNK || gen >= 16) break;
+            // too many knots below U for the buffer: shrink U in proportion
+            // (to about WCAP of them at uniform density) and generate again
+            U *= 0.9f * (float)WCAP / (float)T_all;
             capped = false;
             cap2 = kInf;
             __syncwarp();
