@@ -32,6 +32,9 @@
 #include <stddef.h>
 #include <stdint.h>
 
+/* Most frames one sphdvr_render_batch call (or one server launch) renders. */
+#define SPHDVR_MAX_BATCH 8
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -220,6 +223,22 @@ sphdvr_status sphdvr_render_host(sphdvr_ctx* ctx, const sphdvr_dataset* ds, cons
                                  const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
                                  float* rgba_host, void* stream);
 
+/* Render `n_frames` (1..SPHDVR_MAX_BATCH) frames of the same data set with
+ * the same table, transfer function and options in ONE launch of the render
+ * kernel (no counterpart in the paper: a serving service).  cams[f] is frame
+ * f's camera (sizes may differ); rgba_out[f] its DEVICE image (width*height*4
+ * floats, caller-owned).  Each frame is binned as in sphdvr_render; the
+ * kernel's warps then take rays from one work queue that runs through all
+ * frames in order, so the long rays at the end of one frame overlap with
+ * the next frame's rays instead of leaving SMs idle.  Images equal those of
+ * n separate sphdvr_render calls.  Enqueued on `stream`; the call
+ * synchronises the stream once per frame to size its pair buffers.  Frame
+ * statistics (sphdvr_frame_stats) are summed over the batch.  EINVAL for
+ * n_frames out of range or a NULL pointer, before any work is enqueued. */
+sphdvr_status sphdvr_render_batch(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut, int n_frames,
+                                  const sphdvr_camera* cams, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
+                                  float* const* rgba_out, void* stream);
+
 /* Allocation-free form of sphdvr_render (no counterpart in the paper: a
  * library service for callers that must not allocate device memory while
  * they render, e.g. a server whose device memory is all handed to its own
@@ -265,7 +284,11 @@ sphdvr_status sphdvr_frame_stats(sphdvr_ctx* ctx, int64_t out[16]);
  *
  * A server owns `max_inflight` (1..8) worker threads, each with its own CUDA
  * stream and frame buffers; submitted requests are rendered in submission
- * order by whichever worker is free, so frames overlap on the GPU.  The
+ * order by whichever worker is free, so frames overlap on the GPU.  A free
+ * worker takes the oldest queued request together with up to max_batch - 1
+ * (default 4, see sphdvr_server_set_batch) later queued requests of the
+ * same data set, table, transfer function and options, and renders them
+ * with one launch (sphdvr_render_batch); a batch completes as a whole.  The
  * device memory all workers hold for frame buffers stays within `hbm_budget`
  * bytes (datasets and tables are not counted: they belong to the caller's
  * context): a worker whose frame does not fit beside the others' holdings
@@ -298,6 +321,15 @@ sphdvr_status sphdvr_server_wait(sphdvr_server* srv, uint64_t ticket, int timeou
  * failed, out[5] device bytes the workers hold, out[6] largest latency (ms),
  * out[7] frames queued and not yet started. */
 sphdvr_status sphdvr_server_stats(sphdvr_server* srv, double out[8]);
+
+/* Frames a worker may render with one launch: 1..SPHDVR_MAX_BATCH (1 turns
+ * batching off).  Applies to batches formed after the call. */
+sphdvr_status sphdvr_server_set_batch(sphdvr_server* srv, int max_batch);
+
+/* out[0] render launches the workers made, out[1] frames those launches
+ * rendered (out[1] / out[0] is the mean batch size), out[2] largest batch,
+ * out[3] 0. */
+sphdvr_status sphdvr_server_batch_stats(sphdvr_server* srv, int64_t out[4]);
 
 /* Finish every queued frame, then stop the workers and free their buffers.
  * Tickets not waited for are retired. */

@@ -154,7 +154,7 @@ size_t ctx_held_bytes(const sphdvr_ctx* c) {
   const DevBuf* bufs[] = {&c->chunk_rect, &c->chunk_front, &c->chunk_ntile, &c->chunk_off, &c->pair_key,
                           &c->pair_val, &c->pair_key2, &c->pair_val2, &c->tile_range, &c->scan_tmp, &c->sort_tmp,
                           &c->stats, &c->tf, &c->img, &c->dbg_pix, &c->dbg_rgba, &c->dbg_counts, &c->dbg_cands,
-                          &c->dbg_field, &c->table, &c->work};
+                          &c->dbg_field, &c->table, &c->work, &c->frames};
   size_t t = 0;
   for (const DevBuf* b : bufs) t += b->bytes;
   return t;
@@ -164,7 +164,7 @@ void ctx_release_buffers(sphdvr_ctx* c) {
   DevBuf* bufs[] = {&c->chunk_rect, &c->chunk_front, &c->chunk_ntile, &c->chunk_off, &c->pair_key, &c->pair_val,
                     &c->pair_key2, &c->pair_val2, &c->tile_range, &c->scan_tmp, &c->sort_tmp, &c->stats,
                     &c->tf, &c->img, &c->dbg_pix, &c->dbg_rgba, &c->dbg_counts, &c->dbg_cands, &c->dbg_field,
-                    &c->table, &c->work};
+                    &c->table, &c->work, &c->frames};
   for (DevBuf* b : bufs) free_buf(*b);
   c->stats_pending = false;
 }
@@ -427,6 +427,40 @@ sphdvr_status sphdvr_render(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sph
   if (!ctx) return SPHDVR_EINVAL;
   if (!rgba_out) return set_err(ctx, SPHDVR_EINVAL, "render: rgba_out is NULL");
   return do_render(ctx, ds, lut, cam, tf, opts, rgba_out, (cudaStream_t)stream, nullptr);
+}
+
+sphdvr_status sphdvr_render_batch(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut, int n_frames,
+                                  const sphdvr_camera* cams, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
+                                  float* const* rgba_out, void* stream) {
+  if (!ctx) return SPHDVR_EINVAL;
+  if (n_frames < 1 || n_frames > SPHDVR_MAX_BATCH)
+    return set_err(ctx, SPHDVR_EINVAL, "render_batch: n_frames out of [1, SPHDVR_MAX_BATCH]");
+  if (!cams || !rgba_out) return set_err(ctx, SPHDVR_EINVAL, "render_batch: NULL argument");
+  sphdvr_status s = check_common(ctx, ds, lut);
+  if (s != SPHDVR_OK) return s;
+  if ((s = check_opts(ctx, opts)) != SPHDVR_OK) return s;
+  std::vector<float4> tfh;
+  if ((s = pack_tf(ctx, tf, tfh)) != SPHDVR_OK) return s;
+  RenderArgs a[SPHDVR_MAX_BATCH];
+  for (int f = 0; f < n_frames; ++f) {
+    if (!rgba_out[f]) return set_err(ctx, SPHDVR_EINVAL, "render_batch: rgba_out[f] is NULL");
+    a[f].ds = ds;
+    a[f].lut = &lut->d;
+    if ((s = check_camera(ctx, &cams[f], &a[f].cam)) != SPHDVR_OK) return s;
+    a[f].tf_n = tf->n;
+    a[f].tf_lo = (float)tf->lo;
+    a[f].tf_hi = (float)tf->hi;
+    a[f].tf_host = tfh.data();
+    a[f].opts = opts;
+    a[f].out = rgba_out[f];
+  }
+  ctx->frame_launch0 = ctx->launches;
+  const cudaStream_t st = (cudaStream_t)stream;
+  s = render_batch_sized(ctx, a, n_frames, st, ctx_pair_sizer, nullptr);
+  if (s != SPHDVR_OK) return s;
+  ctx->last_stream = st;
+  ctx->stats_pending = true;
+  return SPHDVR_OK;
 }
 
 sphdvr_status sphdvr_render_host(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,

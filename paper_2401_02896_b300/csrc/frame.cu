@@ -124,20 +124,22 @@ __global__ void k_emit_pairs(int n_chunks, const float4* rect, const unsigned* f
   }
 }
 
-__global__ void k_tile_ranges(int64_t n, const uint64_t* keys, int2* range) {
+// [first, end) of each tile's pairs, as indices into the pair arrays that
+// start `base` entries before `keys`
+__global__ void k_tile_ranges(int64_t n, const uint64_t* keys, int2* range, int base) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int t = (int)(keys[i] >> 32);
-  if (i == 0 || (int)(keys[i - 1] >> 32) != t) range[t].x = (int)i;
-  if (i == n - 1 || (int)(keys[i + 1] >> 32) != t) range[t].y = (int)(i + 1);
+  if (i == 0 || (int)(keys[i - 1] >> 32) != t) range[t].x = base + (int)i;
+  if (i == n - 1 || (int)(keys[i + 1] >> 32) != t) range[t].y = base + (int)(i + 1);
 }
 
 }  // namespace
 
 // per-degree launchers (render_d<D>.cu)
 #define SPHDVR_DECL(D)                                                                                         \
-  sphdvr_status launch_render_d##D(sphdvr_ctx* ctx, bool f64, bool dbg, const RenderParams& p, int grid,    \
-                                   size_t smem, cudaStream_t st);                                            \
+  sphdvr_status launch_render_d##D(sphdvr_ctx* ctx, bool f64, bool dbg, bool batch, const RenderParams& p,  \
+                                   int grid, size_t smem, cudaStream_t st);                                  \
   int render_occupancy_d##D(bool f64, bool dbg, size_t smem);
 SPHDVR_DECL(1)
 SPHDVR_DECL(2)
@@ -147,15 +149,15 @@ SPHDVR_DECL(5)
 SPHDVR_DECL(6)
 #undef SPHDVR_DECL
 
-static sphdvr_status dispatch_render(sphdvr_ctx* ctx, int D, bool f64, bool dbg, const RenderParams& p, int grid,
-                                     size_t smem, cudaStream_t st) {
+static sphdvr_status dispatch_render(sphdvr_ctx* ctx, int D, bool f64, bool dbg, bool batch, const RenderParams& p,
+                                     int grid, size_t smem, cudaStream_t st) {
   switch (D) {
-    case 1: return launch_render_d1(ctx, f64, dbg, p, grid, smem, st);
-    case 2: return launch_render_d2(ctx, f64, dbg, p, grid, smem, st);
-    case 3: return launch_render_d3(ctx, f64, dbg, p, grid, smem, st);
-    case 4: return launch_render_d4(ctx, f64, dbg, p, grid, smem, st);
-    case 5: return launch_render_d5(ctx, f64, dbg, p, grid, smem, st);
-    case 6: return launch_render_d6(ctx, f64, dbg, p, grid, smem, st);
+    case 1: return launch_render_d1(ctx, f64, dbg, batch, p, grid, smem, st);
+    case 2: return launch_render_d2(ctx, f64, dbg, batch, p, grid, smem, st);
+    case 3: return launch_render_d3(ctx, f64, dbg, batch, p, grid, smem, st);
+    case 4: return launch_render_d4(ctx, f64, dbg, batch, p, grid, smem, st);
+    case 5: return launch_render_d5(ctx, f64, dbg, batch, p, grid, smem, st);
+    case 6: return launch_render_d6(ctx, f64, dbg, batch, p, grid, smem, st);
   }
   return set_err(ctx, SPHDVR_EINVAL, "D out of range");
 }
@@ -172,7 +174,10 @@ static int render_occupancy(int D, bool f64, bool dbg, size_t smem) {
   return 0;
 }
 
-int render_grid(sphdvr_ctx* ctx, const RenderArgs& a) {
+static int frame_tiles(const DevCamera& c) { return ((c.width + kTile - 1) / kTile) * ((c.height + kTile - 1) / kTile); }
+
+// Persistent grid: resident CTAs on every SM, no more CTAs than work items.
+static int grid_for_items(sphdvr_ctx* ctx, const RenderArgs& a, int64_t items) {
   const bool dbg = a.n_dbg > 0;
   const int prec = a.opts ? a.opts->precision : SPHDVR_PREC_FP32_ANCHORED;
   const bool f64 = prec == SPHDVR_PREC_FP64_NAIVE;
@@ -183,20 +188,23 @@ int render_grid(sphdvr_ctx* ctx, const RenderArgs& a) {
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, ctx->device);
     ctx->num_sms = n > 0 ? n : 1;
   }
-  int items;
-  if (dbg) {
-    items = a.n_dbg;
-  } else {
-    const int tiles = ((a.cam.width + kTile - 1) / kTile) * ((a.cam.height + kTile - 1) / kTile);
-    items = (tiles * kTile * kTile + kRenderWarps - 1) / kRenderWarps;
-  }
-  int grid = std::max(1, nb) * ctx->num_sms;
-  return std::max(1, std::min(grid, items));
+  const int64_t grid = (int64_t)std::max(1, nb) * ctx->num_sms;
+  return (int)std::max<int64_t>(1, std::min(grid, items));
+}
+
+int render_grid(sphdvr_ctx* ctx, const RenderArgs& a) {
+  const int64_t items = a.n_dbg > 0 ? a.n_dbg
+                                    : ((int64_t)frame_tiles(a.cam) * kTile * kTile + kRenderWarps - 1) / kRenderWarps;
+  return grid_for_items(ctx, a, items);
+}
+
+int render_grid_batch(sphdvr_ctx* ctx, const RenderArgs* a, int n) {
+  int64_t rays = 0;
+  for (int f = 0; f < n; ++f) rays += (int64_t)frame_tiles(a[f].cam) * kTile * kTile;
+  return grid_for_items(ctx, a[0], (rays + kRenderWarps - 1) / kRenderWarps);
 }
 
 size_t render_table_floats(int grid, bool dbg) { return (size_t)grid * (dbg ? 1 : kRenderWarps) * kTableWords; }
-
-
 
 // grow the context's pair buffers once the pair count is known
 sphdvr_status ctx_pair_sizer(sphdvr_ctx* ctx, FrameWork& w, size_t pairs, void*) {
@@ -216,126 +224,162 @@ sphdvr_status ctx_pair_sizer(sphdvr_ctx* ctx, FrameWork& w, size_t pairs, void*)
   return SPHDVR_OK;
 }
 
+// size of a grow-only buffer after ensure(b, bytes)
+static size_t grown(const DevBuf& b, size_t bytes) {
+  return (b.bytes >= bytes && b.p) ? b.bytes : bytes + bytes / 4 + 256;
+}
+
+size_t held_after_pair_sizer(const sphdvr_ctx* ctx, size_t pairs) {
+  const size_t np = std::max<size_t>(pairs, 1);
+  const DevBuf* b[] = {&ctx->pair_key, &ctx->pair_val, &ctx->pair_key2, &ctx->pair_val2, &ctx->sort_tmp};
+  const size_t want[] = {np * 8, np * 4, np * 8, np * 4, sort_tmp_words((int64_t)np) * sizeof(uint32_t)};
+  size_t t = ctx_held_bytes(ctx);
+  for (int i = 0; i < 5; ++i) t = t - b[i]->bytes + grown(*b[i], want[i]);
+  return t;
+}
+
 size_t pair_bytes(size_t pairs) {
   const size_t np = std::max<size_t>(pairs, 1);
   return np * 24 + sort_tmp_words((int64_t)np) * sizeof(uint32_t);
 }
 
-size_t frame_fixed_bytes(sphdvr_ctx* ctx, const RenderArgs& a) {
-  const size_t tiles = (size_t)((a.cam.width + kTile - 1) / kTile) * ((a.cam.height + kTile - 1) / kTile);
+// Bytes shared by the frames of a batch (chunk scratch, statistics, table
+// scratch of the grid, transfer function, work counter, frame records).
+static size_t shared_fixed_bytes(const RenderArgs& a, int grid, int n) {
   const size_t nc = a.ds->n_chunks;
-  const int grid = render_grid(ctx, a);
-  return nc * (sizeof(float4) + sizeof(unsigned) + 2 * sizeof(uint32_t)) + 32 + tiles * sizeof(int2) +
-         32 * sizeof(unsigned long long) + scan_tmp_words(nc) * sizeof(uint32_t) + (size_t)a.tf_n * sizeof(float4) +
-         render_table_floats(grid, a.n_dbg > 0) * sizeof(float) + 4 * sizeof(unsigned);
+  return nc * (sizeof(unsigned) + 2 * sizeof(uint32_t)) + 32 + 32 * sizeof(unsigned long long) +
+         scan_tmp_words(nc) * sizeof(uint32_t) + (size_t)a.tf_n * sizeof(float4) +
+         render_table_floats(grid, a.n_dbg > 0) * sizeof(float) + 4 * sizeof(unsigned) +
+         (n > 1 ? (size_t)n * sizeof(RenderFrame) : 0);
+}
+
+size_t frame_fixed_bytes(sphdvr_ctx* ctx, const RenderArgs& a) {
+  return (size_t)a.ds->n_chunks * sizeof(float4) + (size_t)frame_tiles(a.cam) * sizeof(int2) +
+         shared_fixed_bytes(a, render_grid(ctx, a), 1);
+}
+
+size_t batch_fixed_bytes(sphdvr_ctx* ctx, const RenderArgs* a, int n) {
+  size_t t = shared_fixed_bytes(a[0], render_grid_batch(ctx, a, n), n) + (size_t)n * a[0].ds->n_chunks * sizeof(float4);
+  for (int f = 0; f < n; ++f) t += (size_t)frame_tiles(a[f].cam) * sizeof(int2);
+  return t;
 }
 
 sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st) {
   return render_frame_sized(ctx, a, st, ctx_pair_sizer, nullptr);
 }
 
-sphdvr_status render_frame_sized(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st, PairSizer sizer, void* user) {
-  const int tiles = ((a.cam.width + kTile - 1) / kTile) * ((a.cam.height + kTile - 1) / kTile);
+// Grow the buffers the frames of a batch share and point `w` at them.
+static sphdvr_status shared_work(sphdvr_ctx* ctx, const RenderArgs& a, int grid, FrameWork& w) {
   const int nc = a.ds->n_chunks;
   sphdvr_status s;
-  if ((s = ensure(ctx, ctx->chunk_rect, (size_t)nc * sizeof(float4))) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->chunk_front, (size_t)nc * sizeof(unsigned))) != SPHDVR_OK ||
+  if ((s = ensure(ctx, ctx->chunk_front, (size_t)nc * sizeof(unsigned))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->chunk_ntile, (size_t)nc * sizeof(uint32_t) + 16)) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->chunk_off, (size_t)nc * sizeof(uint32_t) + 16)) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->tile_range, (size_t)tiles * sizeof(int2))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->stats, 32 * sizeof(unsigned long long))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->scan_tmp, scan_tmp_words(nc) * sizeof(uint32_t))) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->tf, (size_t)a.tf_n * sizeof(float4))) != SPHDVR_OK)
-    return s;
-  const int grid = render_grid(ctx, a);
-  if ((s = ensure(ctx, ctx->table, render_table_floats(grid, a.n_dbg > 0) * sizeof(float))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->tf, (size_t)a.tf_n * sizeof(float4))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->table, render_table_floats(grid, a.n_dbg > 0) * sizeof(float))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->work, 4 * sizeof(unsigned))) != SPHDVR_OK)
     return s;
-  FrameWork w;
   w.table = (float*)ctx->table.p;
   w.table_ctas = grid;
   w.work = (unsigned*)ctx->work.p;
-  w.chunk_rect = (float4*)ctx->chunk_rect.p;
   w.chunk_front = (unsigned*)ctx->chunk_front.p;
   w.chunk_ntile = (uint32_t*)ctx->chunk_ntile.p;
   w.chunk_off = (uint32_t*)ctx->chunk_off.p;
-  w.tile_range = (int2*)ctx->tile_range.p;
   w.stats = (unsigned long long*)ctx->stats.p;
   w.tf = (float4*)ctx->tf.p;
   w.tmp = (uint32_t*)ctx->scan_tmp.p;
   w.tmp_words = ctx->scan_tmp.bytes / sizeof(uint32_t);
+  return SPHDVR_OK;
+}
+
+// Grow the chunk rectangles (n_rect frames) and tile ranges (tiles) and point `w` at them.
+static sphdvr_status rect_range_work(sphdvr_ctx* ctx, const RenderArgs& a, int n_rect, int64_t tiles, FrameWork& w) {
+  sphdvr_status s;
+  if ((s = ensure(ctx, ctx->chunk_rect, (size_t)n_rect * a.ds->n_chunks * sizeof(float4))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->tile_range, (size_t)tiles * sizeof(int2))) != SPHDVR_OK)
+    return s;
+  w.chunk_rect = (float4*)ctx->chunk_rect.p;
+  w.tile_range = (int2*)ctx->tile_range.p;
+  return SPHDVR_OK;
+}
+
+sphdvr_status render_frame_sized(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st, PairSizer sizer, void* user) {
+  FrameWork w;
+  sphdvr_status s;
+  if ((s = shared_work(ctx, a, render_grid(ctx, a), w)) != SPHDVR_OK ||
+      (s = rect_range_work(ctx, a, 1, frame_tiles(a.cam), w)) != SPHDVR_OK)
+    return s;
   return render_frame_ws(ctx, a, w, sizer, user, st);
 }
 
-sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w, PairSizer sizer, void* user,
-                              cudaStream_t st) {
+// Binning, first half: project the chunks into the frame (rectangles into
+// `rect`, fronts and tile counts into w's chunk scratch) and scan the counts
+// into offsets; with `total` non-null, read the frame's pair count back.
+static sphdvr_status project_frame(sphdvr_ctx* ctx, const RenderArgs& a, float4* rect, const FrameWork& w,
+                                   cudaStream_t st, uint32_t* total) {
   const sphdvr_dataset* ds = a.ds;
-  const DevLut* L = a.lut;
-  const DevCamera& cam = a.cam;
-  const int tiles_x = (cam.width + kTile - 1) / kTile, tiles_y = (cam.height + kTile - 1) / kTile;
-  const int n_tiles = tiles_x * tiles_y;
+  const int tiles_x = (a.cam.width + kTile - 1) / kTile, tiles_y = (a.cam.height + kTile - 1) / kTile;
   const int nc = ds->n_chunks;
-  sphdvr_status s;
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(w.tf, a.tf_host, (size_t)a.tf_n * sizeof(float4), cudaMemcpyHostToDevice, st)) !=
-      cudaSuccess)
-    return cuda_err(ctx, e, "transfer function upload");
-  float4* rect = w.chunk_rect;
-  unsigned* front = w.chunk_front;
-  uint32_t* ntile = w.chunk_ntile;
-  uint32_t* off = w.chunk_off;
-  int2* trange = w.tile_range;
-  unsigned long long* stats = w.stats;
-  k_chunk_project<<<(nc + 255) / 256, 256, 0, st>>>(nc, ds->chunk_lo, ds->chunk_hi, cam, L->q, L->reach, tiles_x,
-                                                    tiles_y, rect, front, ntile);
+  k_chunk_project<<<(nc + 255) / 256, 256, 0, st>>>(nc, ds->chunk_lo, ds->chunk_hi, a.cam, a.lut->q, a.lut->reach,
+                                                    tiles_x, tiles_y, rect, w.chunk_front, w.chunk_ntile);
   ++ctx->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(ctx, e, "k_chunk_project");
-  uint32_t* d_total = off + nc;
+  uint32_t* d_total = w.chunk_off + nc;
   if (w.tmp_words < scan_tmp_words(nc)) return set_err(ctx, SPHDVR_EOVERFLOW, "frame scratch too small for the scan");
-  if ((s = scan_exclusive_u32(ctx, ntile, off, nc, d_total, w.tmp, st)) != SPHDVR_OK) return s;
-  uint32_t total = 0;
-  if ((e = cudaMemcpyAsync(&total, d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+  sphdvr_status s = scan_exclusive_u32(ctx, w.chunk_ntile, w.chunk_off, nc, d_total, w.tmp, st);
+  if (s != SPHDVR_OK || !total) return s;
+  if ((e = cudaMemcpyAsync(total, d_total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return cuda_err(ctx, e, "pair count");
-  ctx->last_pairs = total;
-  if (sizer && (s = sizer(ctx, w, total, user)) != SPHDVR_OK) return s;
-  if (w.pair_cap < total || w.tmp_words < sort_tmp_words(total))
+  return SPHDVR_OK;
+}
+
+// Binning, second half: emit the frame's `total` chunk-tile pairs at entry
+// `base` of w's pair arrays, sort them by (tile, front) and write each tile's
+// range (indices into the pair arrays) to `trange`.
+static sphdvr_status sort_frame(sphdvr_ctx* ctx, const RenderArgs& a, const float4* rect, const FrameWork& w,
+                                uint32_t total, int64_t base, int2* trange, cudaStream_t st) {
+  const int tiles_x = (a.cam.width + kTile - 1) / kTile, tiles_y = (a.cam.height + kTile - 1) / kTile;
+  const int n_tiles = tiles_x * tiles_y;
+  const int nc = a.ds->n_chunks;
+  cudaError_t e;
+  if ((int64_t)w.pair_cap < base + total || w.tmp_words < sort_tmp_words(total))
     return set_err(ctx, SPHDVR_EOVERFLOW, "frame scratch too small for " + std::to_string(total) + " chunk-tile pairs");
-  uint64_t* keys = w.pair_key;
-  uint32_t* vals = w.pair_val;
-  k_emit_pairs<<<(nc + 255) / 256, 256, 0, st>>>(nc, rect, front, ntile, off, tiles_x, tiles_y, keys, vals);
+  uint64_t* keys = w.pair_key + base;
+  uint32_t* vals = w.pair_val + base;
+  k_emit_pairs<<<(nc + 255) / 256, 256, 0, st>>>(nc, rect, w.chunk_front, w.chunk_ntile, w.chunk_off, tiles_x,
+                                                 tiles_y, keys, vals);
   ++ctx->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(ctx, e, "k_emit_pairs");
   int tbits = 0;
   while ((1 << tbits) < n_tiles) ++tbits;
-  if ((s = radix_sort_u64(ctx, keys, vals, w.pair_key2, w.pair_val2, total, 32 + tbits, w.tmp, st)) != SPHDVR_OK)
-    return s;
+  sphdvr_status s = radix_sort_u64(ctx, keys, vals, w.pair_key2, w.pair_val2, total, 32 + tbits, w.tmp, st);
+  if (s != SPHDVR_OK) return s;
   if ((e = cudaMemsetAsync(trange, 0, (size_t)n_tiles * sizeof(int2), st)) != cudaSuccess)
     return cuda_err(ctx, e, "tile range memset");
   if (total) {
-    k_tile_ranges<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(total, keys, trange);
+    k_tile_ranges<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(total, keys, trange, (int)base);
     ++ctx->launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(ctx, e, "k_tile_ranges");
   }
-  if ((e = cudaMemsetAsync(stats, 0, 32 * sizeof(unsigned long long), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(w.work, 0, sizeof(unsigned), st)) != cudaSuccess)
-    return cuda_err(ctx, e, "stats memset");
+  return SPHDVR_OK;
+}
 
-  RenderParams p;
+// Kernel parameters common to every frame of a launch (data, table, transfer
+// function, options, scratch).
+static void common_params(const RenderArgs& a, const FrameWork& w, RenderParams& p) {
+  const sphdvr_dataset* ds = a.ds;
+  const DevLut* L = a.lut;
   std::memset(&p, 0, sizeof(p));
-  p.cam = cam;
   p.pos = ds->pos;
   p.amp = ds->amp;
   p.orig = ds->orig;
   p.chunk = ds->chunk;
   p.chunk_lo = ds->chunk_lo;
   p.chunk_hi = ds->chunk_hi;
-  p.chunk_rect = rect;
-  p.pair_key = keys;
-  p.pair_val = vals;
-  p.tile_range = trange;
-  p.tiles_x = tiles_x;
-  p.tiles_y = tiles_y;
   p.K = L->K;
   p.m = L->m;
   p.n_lambda = L->n_lambda;
@@ -356,8 +400,47 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
   p.reinit_dt = (prec == SPHDVR_PREC_FP32_REINIT) ? o->reinit_dt : 0.f;
   float eps = o ? o->ert_eps : 1e-5f;
   p.tau_ert = eps > 0.f ? -std::log(eps) : 0.f;
+  p.stats = w.stats;
+  p.scratch = w.table;
+  p.work = w.work;
+  p.dynamic = o ? (o->persistent ? 1 : 0) : 1;
+}
+
+static sphdvr_status upload_tf(sphdvr_ctx* ctx, const RenderArgs& a, const FrameWork& w, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(w.tf, a.tf_host, (size_t)a.tf_n * sizeof(float4), cudaMemcpyHostToDevice, st);
+  return e == cudaSuccess ? SPHDVR_OK : cuda_err(ctx, e, "transfer function upload");
+}
+
+static sphdvr_status clear_counters(sphdvr_ctx* ctx, const FrameWork& w, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(w.stats, 0, 32 * sizeof(unsigned long long), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(w.work, 0, sizeof(unsigned), st)) != cudaSuccess)
+    return cuda_err(ctx, e, "stats memset");
+  return SPHDVR_OK;
+}
+
+sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w, PairSizer sizer, void* user,
+                              cudaStream_t st) {
+  sphdvr_status s;
+  uint32_t pairs = 0;
+  if ((s = upload_tf(ctx, a, w, st)) != SPHDVR_OK || (s = project_frame(ctx, a, w.chunk_rect, w, st, &pairs)) != SPHDVR_OK)
+    return s;
+  ctx->last_pairs = pairs;
+  if (sizer && (s = sizer(ctx, w, pairs, user)) != SPHDVR_OK) return s;
+  if ((s = sort_frame(ctx, a, w.chunk_rect, w, pairs, 0, w.tile_range, st)) != SPHDVR_OK ||
+      (s = clear_counters(ctx, w, st)) != SPHDVR_OK)
+    return s;
+  RenderParams p;
+  common_params(a, w, p);
+  p.cam = a.cam;
+  p.chunk_rect = w.chunk_rect;
+  p.pair_key = w.pair_key;
+  p.pair_val = w.pair_val;
+  p.tile_range = w.tile_range;
+  p.tiles_x = (a.cam.width + kTile - 1) / kTile;
+  p.tiles_y = (a.cam.height + kTile - 1) / kTile;
   p.out = a.out;
-  p.stats = stats;
+  p.n_items = frame_tiles(a.cam) * kTile * kTile;
   p.n_dbg = a.n_dbg;
   p.dbg_pix = a.dbg_pix;
   p.dbg_rgba = a.dbg_rgba;
@@ -366,15 +449,77 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
   p.cand_cap = a.cand_cap;
   p.dbg_field = a.dbg_field;
   p.field_cap = a.field_cap;
-  const bool f64 = prec == SPHDVR_PREC_FP64_NAIVE;
+  const int prec = a.opts ? a.opts->precision : SPHDVR_PREC_FP32_ANCHORED;
   const bool dbg = a.n_dbg > 0;
   const int grid = std::min(render_grid(ctx, a), w.table_ctas);
-  p.scratch = w.table;
-  p.work = w.work;
-  p.n_items = n_tiles * kTile * kTile;
-  p.dynamic = o ? (o->persistent ? 1 : 0) : 1;
-  size_t smem = render_smem_bytes(a.tf_n, dbg ? 1 : kRenderWarps);
-  return dispatch_render(ctx, L->D, f64, dbg, p, grid, smem, st);
+  const size_t smem = render_smem_bytes(a.tf_n, dbg ? 1 : kRenderWarps);
+  return dispatch_render(ctx, a.lut->D, prec == SPHDVR_PREC_FP64_NAIVE, dbg, false, p, grid, smem, st);
+}
+
+sphdvr_status render_batch_sized(sphdvr_ctx* ctx, const RenderArgs* a, int n, cudaStream_t st, PairSizer sizer,
+                                 void* user) {
+  if (n < 1 || n > SPHDVR_MAX_BATCH) return set_err(ctx, SPHDVR_EINVAL, "batch: frame count out of range");
+  if (n == 1) return render_frame_sized(ctx, a[0], st, sizer, user);
+  const int grid = render_grid_batch(ctx, a, n);
+  const int nc = a[0].ds->n_chunks;
+  int64_t tiles = 0, rays = 0;
+  for (int f = 0; f < n; ++f) {
+    tiles += frame_tiles(a[f].cam);
+    rays += (int64_t)frame_tiles(a[f].cam) * kTile * kTile;
+  }
+  if (rays > INT32_MAX) return set_err(ctx, SPHDVR_EINVAL, "batch: more than 2^31 rays");
+  FrameWork w;
+  sphdvr_status s;
+  if ((s = shared_work(ctx, a[0], grid, w)) != SPHDVR_OK || (s = rect_range_work(ctx, a[0], n, tiles, w)) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->frames, (size_t)n * sizeof(RenderFrame))) != SPHDVR_OK ||
+      (s = upload_tf(ctx, a[0], w, st)) != SPHDVR_OK)
+    return s;
+  // pass 1: each frame's pair count (the chunk scratch is reused frame after frame)
+  uint32_t cnt[SPHDVR_MAX_BATCH];
+  int64_t pairs = 0;
+  for (int f = 0; f < n; ++f) {
+    if ((s = project_frame(ctx, a[f], w.chunk_rect + (size_t)f * nc, w, st, &cnt[f])) != SPHDVR_OK) return s;
+    pairs += cnt[f];
+  }
+  if (pairs > INT32_MAX) return set_err(ctx, SPHDVR_EOVERFLOW, "batch: more than 2^31 chunk-tile pairs");
+  ctx->last_pairs = pairs;
+  if (sizer && (s = sizer(ctx, w, (size_t)pairs, user)) != SPHDVR_OK) return s;
+  // pass 2: project again and sort each frame's pairs into its part of the common arrays
+  RenderFrame fr[SPHDVR_MAX_BATCH];
+  int64_t base = 0, tile_base = 0, items = 0;
+  for (int f = 0; f < n; ++f) {
+    const float4* rect = w.chunk_rect + (size_t)f * nc;
+    if ((s = project_frame(ctx, a[f], w.chunk_rect + (size_t)f * nc, w, st, nullptr)) != SPHDVR_OK ||
+        (s = sort_frame(ctx, a[f], rect, w, cnt[f], base, w.tile_range + tile_base, st)) != SPHDVR_OK)
+      return s;
+    std::memset(&fr[f], 0, sizeof(RenderFrame));
+    fr[f].cam = a[f].cam;
+    fr[f].tiles_x = (a[f].cam.width + kTile - 1) / kTile;
+    fr[f].tiles_y = (a[f].cam.height + kTile - 1) / kTile;
+    fr[f].tile_base = (int)tile_base;
+    items += (int64_t)frame_tiles(a[f].cam) * kTile * kTile;
+    fr[f].item_end = (int)items;
+    fr[f].out = a[f].out;
+    base += cnt[f];
+    tile_base += frame_tiles(a[f].cam);
+  }
+  cudaError_t e = cudaMemcpyAsync(ctx->frames.p, fr, (size_t)n * sizeof(RenderFrame), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "frame records upload");
+  if ((s = clear_counters(ctx, w, st)) != SPHDVR_OK) return s;
+  RenderParams p;
+  common_params(a[0], w, p);
+  p.chunk_rect = w.chunk_rect;
+  p.pair_key = w.pair_key;
+  p.pair_val = w.pair_val;
+  p.tile_range = w.tile_range;
+  p.frames = (const RenderFrame*)ctx->frames.p;
+  p.n_frames = n;
+  p.rect_stride = nc;
+  p.n_items = (int)items;
+  const int prec = a[0].opts ? a[0].opts->precision : SPHDVR_PREC_FP32_ANCHORED;
+  const size_t smem = render_smem_bytes(a[0].tf_n, kRenderWarps);
+  return dispatch_render(ctx, a[0].lut->D, prec == SPHDVR_PREC_FP64_NAIVE, false, true, p, std::min(grid, w.table_ctas),
+                         smem, st);
 }
 
 }  // namespace sphdvr

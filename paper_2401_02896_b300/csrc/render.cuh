@@ -65,6 +65,16 @@ constexpr int kTableWords = 11 * kCap;
 constexpr int kWorkBytes = 4 * kNK * 4;
 constexpr int kWarpSmem = 256 * 4 + kLevels * 4 + kCap / 2 + kWorkBytes;
 
+// One frame of a batch rendered by a single launch.  The frames' binning
+// outputs are concatenated: frame f's tile ranges start at tile_base (and
+// index the common pair arrays), its chunk rectangles at f * rect_stride.
+struct RenderFrame {
+  DevCamera cam;
+  int tiles_x, tiles_y, tile_base;
+  int item_end;  // work items of this and the preceding frames
+  float* out;
+};
+
 struct RenderParams {
   DevCamera cam;
   // data set
@@ -99,7 +109,10 @@ struct RenderParams {
   unsigned long long* stats;
   float* scratch;       // per-ray scratch: (grid * NW) * kTableWords words
   unsigned* work;       // work-queue counter (dynamic scheduling), zeroed per frame
-  int n_items;          // rays (tile-major, 256 per tile)
+  int n_items;          // rays (tile-major, 256 per tile); of all frames in a batch
+  const RenderFrame* frames;  // batch (BT instantiation): per-frame fields, device memory
+  int n_frames;
+  int rect_stride;            // batch: chunk rectangles per frame
   int dynamic;          // 1: atomic work queue, 0: static stride
   // debug
   int n_dbg;
@@ -751,7 +764,9 @@ static __device__ __noinline__ int nearest_entry_fp64(const df* wv, float h, int
 // transfer function.
 // RE: reinitialisation knots (precision mode FP32_REINIT), a separate
 // instantiation so that the other modes carry none of its code.
-template <int D, typename S, int NW, bool DBG, bool RE>
+// BT: a batch of frames sharing data, table, transfer function and options;
+// the work queue spans the rays of all of them.
+template <int D, typename S, int NW, bool DBG, bool RE, bool BT = false>
 __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderParams p) {
   // knots per lane in a window: as many as the shared work area holds with the
   // window's D difference coefficients, its positions and its knot ids
@@ -792,8 +807,6 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
   PT_DECL
   const int K = p.K, m = p.m;
   const float q = p.q, gam = p.window_h;
-  const float t_near = (float)p.cam.t_near;
-  const df t_near_df = df_from_double(p.cam.t_near);
   const float kInf = __int_as_float(0x7f800000);
 
   for (int it = 0;; ++it) {
@@ -809,27 +822,36 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
       item = (blockIdx.x * NW + wid) + it * gridDim.x * NW;
     }
     if (item >= (DBG ? p.n_dbg : p.n_items)) break;
+    int fb = 0;  // frame of the ray (batch)
+    if (BT) {
+      while (fb + 1 < p.n_frames && item >= p.frames[fb].item_end) ++fb;
+      if (fb > 0) item -= p.frames[fb - 1].item_end;
+    }
+    const DevCamera& cam = BT ? p.frames[fb].cam : p.cam;
+    const int tiles_x = BT ? p.frames[fb].tiles_x : p.tiles_x;
+    const float t_near = (float)cam.t_near;
+    const df t_near_df = df_from_double(cam.t_near);
     int tile, px, py;
     long long dbg_row = -1;
     if (DBG) {
       dbg_row = item;
       const int pix = p.dbg_pix[item];
-      px = pix % p.cam.width;
-      py = pix / p.cam.width;
-      tile = (py / kTile) * p.tiles_x + px / kTile;
+      px = pix % cam.width;
+      py = pix / cam.width;
+      tile = (py / kTile) * tiles_x + px / kTile;
     } else {
       tile = item >> 8;
       const int sub = item & 255;
-      px = (tile % p.tiles_x) * kTile + (sub & 15);
-      py = (tile / p.tiles_x) * kTile + (sub >> 4);
+      px = (tile % tiles_x) * kTile + (sub & 15);
+      py = (tile / tiles_x) * kTile + (sub >> 4);
     }
-    if (px >= p.cam.width || py >= p.cam.height) continue;
+    if (px >= cam.width || py >= cam.height) continue;
     const float pxf = (float)px, pyf = (float)py;
 
     // ---- the ray, FP64 -> double-float
     df o[3], v[3];
     {
-      const DevCamera& c = p.cam;
+      const DevCamera& c = cam;
       double sx = 2.0 * (px + 0.5) / c.width - 1.0, sy = 1.0 - 2.0 * (py + 0.5) / c.height;
       double oo[3], vv[3];
       if (c.proj == 0) {
@@ -870,7 +892,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     for (int b = lane; b < kLevels; b += 32) T.lvl[b] = 0;
     __syncwarp();
 
-    const int2 tr = p.tile_range[tile];
+    const int2 tr = p.tile_range[(BT ? p.frames[fb].tile_base : 0) + tile];
     const int ce = tr.y;
     // the tile list is read 32 entries at a time; each lane keeps its
     // entry's chunk, particle range and bound F for when the chunk is processed
@@ -890,7 +912,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             g_cid = (int)__ldg(p.pair_val + idx);
             const unsigned ob = (unsigned)(__ldg(p.pair_key + idx) & 0xffffffffu);
             g_F = __uint_as_float((ob & 0x80000000u) ? (ob & 0x7fffffffu) : ~ob);
-            const float4 r = __ldg(p.chunk_rect + g_cid);
+            const float4 r = __ldg(p.chunk_rect + (BT ? fb * p.rect_stride : 0) + g_cid);
             if (r.x <= pxf + 0.5f && r.z >= pxf - 0.5f && r.y <= pyf + 0.5f && r.w >= pyf - 0.5f) {
               const float4 lo = __ldg(p.chunk_lo + g_cid), hi = __ldg(p.chunk_hi + g_cid);
               const int2 chk = __ldg(p.chunk + g_cid);
@@ -993,7 +1015,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
               if (DBG && df_to_double(kp) > df_to_double(Ta)) ++dbg_np;
             } else {
               started = true;
-              t_start = (df_to_double(kp) > (double)p.cam.t_near) ? kp : t_near_df;
+              t_start = (df_to_double(kp) > (double)cam.t_near) ? kp : t_near_df;
             }
             Ta = kp;
             fresh = true;
@@ -1512,8 +1534,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
         p.dbg_counts[4 * dbg_row + 2] = dbg_np;
         p.dbg_counts[4 * dbg_row + 3] = st_flags;
       } else {
-        float4* o4 = (float4*)p.out;
-        o4[(size_t)py * p.cam.width + px] = make_float4(col[0], col[1], col[2], alpha);
+        float4* o4 = (float4*)(BT ? p.frames[fb].out : p.out);
+        o4[(size_t)py * cam.width + px] = make_float4(col[0], col[1], col[2], alpha);
       }
     }
   }

@@ -3,9 +3,9 @@
 
 namespace sphdvr {
 
-template <typename S, int NW, bool DBG, bool RE>
+template <typename S, int NW, bool DBG, bool RE, bool BT = false>
 static sphdvr_status launch(sphdvr_ctx* ctx, const RenderParams& p, int grid, size_t smem, cudaStream_t st) {
-  auto kern = k_render<1, S, NW, DBG, RE>;
+  auto kern = k_render<1, S, NW, DBG, RE, BT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_err(ctx, e, "render smem attribute");
   if (!ctx->ev_ready) {
@@ -29,9 +29,14 @@ static int occupancy(size_t smem) {
   return nb;
 }
 
-sphdvr_status launch_render_d1(sphdvr_ctx* ctx, bool f64, bool dbg, const RenderParams& p, int grid, size_t smem,
-                                cudaStream_t st) {
+sphdvr_status launch_render_d1(sphdvr_ctx* ctx, bool f64, bool dbg, bool batch, const RenderParams& p, int grid,
+                                size_t smem, cudaStream_t st) {
   const bool re = p.reinit_dt > 0.f;  // FP32 only
+  if (batch) {  // several frames, one work queue
+    if (f64) return launch<double, kRenderWarps, false, false, true>(ctx, p, grid, smem, st);
+    return re ? launch<float, kRenderWarps, false, true, true>(ctx, p, grid, smem, st)
+              : launch<float, kRenderWarps, false, false, true>(ctx, p, grid, smem, st);
+  }
   if (dbg) {
     if (f64) return launch<double, 1, true, false>(ctx, p, grid, smem, st);
     return re ? launch<float, 1, true, true>(ctx, p, grid, smem, st) : launch<float, 1, true, false>(ctx, p, grid, smem, st);

@@ -3,10 +3,13 @@
 //
 // Each worker thread owns a CUDA stream and an internal context (its own
 // grow-only frame buffers, events and counters), takes the oldest queued
-// request, renders it with the same binning and render kernels as
-// sphdvr_render, and marks it done once its stream has drained.  Frames of
-// different workers overlap on the GPU: the persistent render kernel of one
-// frame fills the SMs that another frame's kernel leaves idle at its tail.
+// request together with later queued requests of the same data set, table,
+// transfer function and options (up to max_batch frames), renders them with
+// one launch of the render kernel whose work queue spans all their rays (the
+// kernels of sphdvr_render_batch), and marks them done once its stream has
+// drained.  Frames of different workers overlap on the GPU as well: the
+// persistent render kernel of one batch fills the SMs that another's leaves
+// idle at its tail.
 //
 // Memory: the bytes all workers hold stay within the budget.  Before a frame
 // grows a worker's buffers the worker checks the budget; when the frame does
@@ -14,11 +17,12 @@
 // and waits (holding nothing, so waits cannot form a cycle) until the others
 // have released enough; workers release their buffers after a request while
 // another worker is waiting.  A frame that alone exceeds the budget fails with
-// SPHDVR_EBUSY.
+// SPHDVR_EBUSY; a batch that does not fit is split into single frames.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <new>
@@ -61,6 +65,8 @@ struct sphdvr_server {
   uint64_t next_ticket = 1;
   bool stop = false;
   std::vector<sphdvr::Worker*> workers;
+  int max_batch = 4;      // frames one render launch may take
+  int64_t launches = 0, batch_frames = 0, largest_batch = 0;
   size_t held_total = 0;  // device bytes all workers hold
   int waiting_mem = 0;
   // statistics of completed requests
@@ -80,8 +86,11 @@ struct Worker {
   cudaStream_t st = nullptr;
   std::thread th;
   size_t held = 0;          // bytes this worker holds (counted in S->held_total)
-  size_t need_now = 0;      // bytes the current frame needs in total (set by the sizer)
+  size_t need_now = 0;      // bytes the current frames need in total (set by the sizer)
   bool retry = false;       // the sizer found no room beside the other workers
+  bool split = false;       // the batch alone exceeds the budget
+  bool fresh = false;       // the worker held no buffers when the current attempt began
+  int batch_n = 1;          // frames of the current launch
 };
 
 // Update this worker's share of held_total (caller holds S->mu).
@@ -121,16 +130,21 @@ size_t with_headroom(size_t b) { return b + b / 4 + 4096; }
 sphdvr_status server_sizer(sphdvr_ctx* ctx, FrameWork& fw, size_t pairs, void* user) {
   Worker* w = (Worker*)user;
   sphdvr_server* S = w->S;
-  const size_t np = std::max<size_t>(pairs, 1);
-  const bool grows = ctx->pair_key.bytes < np * 8 || ctx->pair_val.bytes < np * 4 ||
-                     ctx->sort_tmp.bytes < pair_bytes(pairs) - np * 24;
   std::unique_lock<std::mutex> lk(S->mu);
-  const size_t mine = ctx_held_bytes(ctx);
-  const size_t old_pairs =
-      ctx->pair_key.bytes + ctx->pair_val.bytes + ctx->pair_key2.bytes + ctx->pair_val2.bytes + ctx->sort_tmp.bytes;
-  const size_t after = grows ? mine - old_pairs + with_headroom(pair_bytes(pairs)) : mine;
-  w->need_now = after;
-  if (after > S->budget) return set_err(ctx, SPHDVR_EBUSY, "frame needs more device memory than the budget");
+  const size_t after = held_after_pair_sizer(ctx, pairs);
+  w->need_now = std::max(w->need_now, after);
+  if (after > S->budget) {
+    if (!w->fresh) {  // buffers of earlier frames count: drop them all and redo the frames
+      w->retry = true;
+      w->need_now = 0;
+      return SPHDVR_EBUSY;
+    }
+    if (w->batch_n > 1) {
+      w->split = true;
+      return SPHDVR_EBUSY;
+    }
+    return set_err(ctx, SPHDVR_EBUSY, "frame needs more device memory than the budget");
+  }
   if (S->held_total - w->held + after > S->budget) {
     w->retry = true;
     return SPHDVR_EBUSY;
@@ -143,55 +157,106 @@ sphdvr_status server_sizer(sphdvr_ctx* ctx, FrameWork& fw, size_t pairs, void* u
   return s;
 }
 
-void run_request(Worker* w, Request* r) {
-  sphdvr_server* S = w->S;
+RenderArgs args_of(Request* r) {
   RenderArgs a = r->a;
   a.tf_host = r->tf.data();
   a.opts = r->has_opts ? &r->opts : nullptr;
+  return a;
+}
+
+// Requests that one launch can render together.
+bool same_launch(const Request* x, const Request* y) {
+  if (x->a.ds != y->a.ds || x->a.lut != y->a.lut || x->a.tf_n != y->a.tf_n || x->a.tf_lo != y->a.tf_lo ||
+      x->a.tf_hi != y->a.tf_hi || x->has_opts != y->has_opts)
+    return false;
+  if (std::memcmp(x->tf.data(), y->tf.data(), x->tf.size() * sizeof(float4)) != 0) return false;
+  if (!x->has_opts) return true;
+  const sphdvr_render_opts &a = x->opts, &b = y->opts;
+  return a.precision == b.precision && a.anchor_every == b.anchor_every && a.window_h == b.window_h &&
+         a.ert_eps == b.ert_eps && a.persistent == b.persistent && a.reinit_dt == b.reinit_dt;
+}
+
+// Render the requests `rs` with one launch and complete them.
+void run_batch(Worker* w, std::vector<Request*>& rs) {
+  sphdvr_server* S = w->S;
   sphdvr_status s = SPHDVR_OK;
+  std::string msg;
+  RenderArgs a[SPHDVR_MAX_BATCH];
   w->need_now = 0;
   for (int attempt = 0;; ++attempt) {
-    const size_t fixed = with_headroom(frame_fixed_bytes(w->wctx, a));
+    const int n = (int)rs.size();
+    for (int f = 0; f < n; ++f) a[f] = args_of(rs[f]);
+    w->batch_n = n;
+    const size_t fixed = with_headroom(batch_fixed_bytes(w->wctx, a, n));
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      if (fixed > S->budget) {
-        r->msg = "frame needs more device memory than the budget";
+      w->fresh = ctx_held_bytes(w->wctx) == 0;
+      if (fixed > S->budget && n == 1) {
+        msg = "frame needs more device memory than the budget";
         s = SPHDVR_EBUSY;
         break;
       }
-      const size_t want = std::max(w->held, std::max(fixed, w->need_now));
-      if (S->held_total - w->held + want > S->budget) wait_for_room(w, lk, std::max(fixed, w->need_now));
-      reserve(w, std::max(w->held, std::max(fixed, w->need_now)));
+      if (fixed > S->budget) {
+        w->split = true;
+      } else {
+        const size_t want = std::max(w->held, std::max(fixed, w->need_now));
+        if (S->held_total - w->held + want > S->budget) wait_for_room(w, lk, std::max(fixed, w->need_now));
+        reserve(w, std::max(w->held, std::max(fixed, w->need_now)));
+      }
     }
-    w->retry = false;
-    w->wctx->last_error.clear();
-    s = render_frame_sized(w->wctx, a, w->st, server_sizer, w);
-    if (s == SPHDVR_OK) {
-      cudaError_t e = cudaStreamSynchronize(w->st);
-      if (e != cudaSuccess) s = cuda_err(w->wctx, e, "server frame");
+    if (!w->split) {
+      w->retry = false;
+      w->wctx->last_error.clear();
+      s = render_batch_sized(w->wctx, a, n, w->st, server_sizer, w);
+      if (s == SPHDVR_OK) {
+        cudaError_t e = cudaStreamSynchronize(w->st);
+        if (e != cudaSuccess) s = cuda_err(w->wctx, e, "server frame");
+      }
+    }
+    if (w->split) {
+      // the batch does not fit the budget as a whole: put all but the oldest
+      // request back at the head of the queue and render that one alone
+      cudaStreamSynchronize(w->st);
+      std::unique_lock<std::mutex> lk(S->mu);
+      for (int f = n - 1; f >= 1; --f) S->queue.push_front(rs[f]);
+      rs.resize(1);
+      w->split = false;
+      w->need_now = 0;
+      release(w);
+      S->cv_work.notify_all();
+      continue;
     }
     if (s == SPHDVR_EBUSY && w->retry && attempt < 64 && !S->stop) {
-      // no room beside the other workers: free everything, wait for room, redo the frame
+      // no room beside the other workers: free everything, wait for room, redo the frames
       cudaStreamSynchronize(w->st);
       std::unique_lock<std::mutex> lk(S->mu);
       wait_for_room(w, lk, w->need_now);
       continue;
     }
-    if (s != SPHDVR_OK) r->msg = w->wctx->last_error;
+    if (s != SPHDVR_OK) msg = w->wctx->last_error;
     break;
   }
   std::unique_lock<std::mutex> lk(S->mu);
   account(w);
-  r->status = s;
-  r->t_done = Clock::now();
-  r->done = true;
+  const auto t_done = Clock::now();
   if (s == SPHDVR_OK) {
-    ++S->completed;
-    S->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
-    S->rays_done += (double)a.cam.width * a.cam.height;
-    S->t_last = r->t_done;
-  } else {
-    ++S->failed;
+    ++S->launches;
+    S->batch_frames += (int64_t)rs.size();
+    S->largest_batch = std::max<int64_t>(S->largest_batch, (int64_t)rs.size());
+  }
+  for (Request* r : rs) {
+    r->status = s;
+    r->msg = msg;
+    r->t_done = t_done;
+    r->done = true;
+    if (s == SPHDVR_OK) {
+      ++S->completed;
+      S->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+      S->rays_done += (double)r->a.cam.width * r->a.cam.height;
+      S->t_last = r->t_done;
+    } else {
+      ++S->failed;
+    }
   }
   if (S->waiting_mem > 0) release(w);
   S->cv_done.notify_all();
@@ -201,7 +266,7 @@ void worker_main(Worker* w) {
   sphdvr_server* S = w->S;
   cudaSetDevice(S->ctx->device);
   for (;;) {
-    Request* r = nullptr;
+    std::vector<Request*> rs;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || (S->waiting_mem > 0 && w->held > 0); });
@@ -210,10 +275,19 @@ void worker_main(Worker* w) {
         continue;
       }
       if (S->queue.empty()) break;  // stop requested and nothing left
-      r = S->queue.front();
+      rs.push_back(S->queue.front());
       S->queue.pop_front();
+      // later requests that can share the launch join it, in queue order
+      for (auto it = S->queue.begin(); it != S->queue.end() && (int)rs.size() < S->max_batch;) {
+        if (same_launch(rs[0], *it)) {
+          rs.push_back(*it);
+          it = S->queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
     }
-    run_request(w, r);
+    run_batch(w, rs);
   }
 }
 
@@ -371,6 +445,25 @@ sphdvr_status sphdvr_server_stats(sphdvr_server* S, double out[8]) {
   out[4] = (double)S->failed;
   out[5] = (double)S->held_total;
   out[7] = (double)S->queue.size();
+  return SPHDVR_OK;
+}
+
+sphdvr_status sphdvr_server_set_batch(sphdvr_server* S, int max_batch) {
+  if (!S) return SPHDVR_EINVAL;
+  if (max_batch < 1 || max_batch > SPHDVR_MAX_BATCH)
+    return set_err(S->ctx, SPHDVR_EINVAL, "server_set_batch: max_batch out of [1, SPHDVR_MAX_BATCH]");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->max_batch = max_batch;
+  return SPHDVR_OK;
+}
+
+sphdvr_status sphdvr_server_batch_stats(sphdvr_server* S, int64_t out[4]) {
+  if (!S || !out) return SPHDVR_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  out[0] = S->launches;
+  out[1] = S->batch_frames;
+  out[2] = S->largest_batch;
+  out[3] = 0;
   return SPHDVR_OK;
 }
 

@@ -65,6 +65,7 @@ struct sphdvr_ctx {
   sphdvr::DevBuf chunk_rect, chunk_front, chunk_ntile, chunk_off, pair_key, pair_val, pair_key2, pair_val2,
       tile_range, scan_tmp, sort_tmp, stats, tf, img, dbg_pix, dbg_rgba, dbg_counts, dbg_cands, dbg_field, table,
       work;
+  sphdvr::DevBuf frames;  // frame records of a batch
   int num_sms = 0;
   std::vector<int64_t> last_stats = std::vector<int64_t>(16, 0);
   cudaStream_t last_stream = nullptr;
@@ -170,6 +171,8 @@ struct FrameWork {
 };
 // Persistent render grid for this frame and the table scratch it needs (floats).
 int render_grid(sphdvr_ctx* ctx, const RenderArgs& a);
+// The same for a batch of frames sharing data set, table and options.
+int render_grid_batch(sphdvr_ctx* ctx, const RenderArgs* a, int n);
 size_t render_table_floats(int grid, bool dbg);
 // Render with scratch from the context's grow-only buffers.
 sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st);
@@ -180,12 +183,23 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
                               cudaStream_t st);
 // As render_frame, with the pair buffers sized by `sizer`.
 sphdvr_status render_frame_sized(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st, PairSizer sizer, void* user);
+// Render n (1..SPHDVR_MAX_BATCH) frames that share data set, table, transfer
+// function and options with one launch of the render kernel, whose work
+// queue spans the rays of all of them; scratch from the context's buffers.
+// The frames' chunk rectangles, pairs and tile ranges are concatenated; the
+// pair buffers are sized by `sizer` for the pairs of all frames.
+sphdvr_status render_batch_sized(sphdvr_ctx* ctx, const RenderArgs* a, int n, cudaStream_t st, PairSizer sizer,
+                                 void* user);
 // The sizer of render_frame: grows the context's pair buffers.
 sphdvr_status ctx_pair_sizer(sphdvr_ctx* ctx, FrameWork& w, size_t pairs, void* user);
 // Device bytes a frame needs besides its pair buffers, and the pair buffers'
 // bytes for a given pair count (both without the grow-only headroom).
 size_t frame_fixed_bytes(sphdvr_ctx* ctx, const RenderArgs& a);
+size_t batch_fixed_bytes(sphdvr_ctx* ctx, const RenderArgs* a, int n);
 size_t pair_bytes(size_t pairs);
+// Device bytes the context holds after ctx_pair_sizer grew its pair buffers
+// for `pairs` pairs.
+size_t held_after_pair_sizer(const sphdvr_ctx* ctx, size_t pairs);
 // api.cu: frame buffers a context holds; release them all.
 size_t ctx_held_bytes(const sphdvr_ctx* ctx);
 void ctx_release_buffers(sphdvr_ctx* ctx);

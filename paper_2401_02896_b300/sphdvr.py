@@ -84,6 +84,8 @@ def _load():
         "sphdvr_dataset_info": (ctypes.c_int, [vp, i64p]),
         "sphdvr_render": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                          ctypes.POINTER(RenderOpts), vp, vp]),
+        "sphdvr_render_batch": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
+                                               ctypes.POINTER(RenderOpts), ctypes.POINTER(vp), vp]),
         "sphdvr_render_host": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                               ctypes.POINTER(RenderOpts), vp, vp]),
         "sphdvr_render_static_scratch": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
@@ -97,6 +99,8 @@ def _load():
         "sphdvr_server_wait": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_int]),
         "sphdvr_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
         "sphdvr_server_destroy": (ctypes.c_int, [vp]),
+        "sphdvr_server_set_batch": (ctypes.c_int, [vp, ctypes.c_int]),
+        "sphdvr_server_batch_stats": (ctypes.c_int, [vp, i64p]),
         "sphdvr_debug_rays": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                              ctypes.POINTER(RenderOpts), ctypes.c_int, vp, vp, vp, vp, ctypes.c_int,
                                              vp, ctypes.c_int]),
@@ -268,6 +272,20 @@ def sphdvr_render(ctx, ds, lut, camera, tf, opts, out_ptr, stream=None, allow_ov
     return _check(st, ctx, (EOVERFLOW,) if allow_overflow else ())
 
 
+MAX_BATCH = 8
+
+
+def sphdvr_render_batch(ctx, ds, lut, cameras, tf, opts, out_ptrs, stream=None, allow_overflow=False):
+    """Render several frames (same data, table, transfer function, options) with one kernel launch."""
+    n = len(cameras)
+    cams = (Camera * max(n, 1))(*[camera_struct(c) for c in cameras])
+    outs = (ctypes.c_void_p * max(len(out_ptrs), 1))(*[ctypes.c_void_p(p) for p in out_ptrs])
+    t, o = tf_struct(tf), opts_struct(opts)
+    st = _lib.sphdvr_render_batch(ctx, ds, lut, n, cams, ctypes.byref(t), ctypes.byref(o), outs,
+                                  ctypes.c_void_p(stream) if stream else None)
+    return _check(st, ctx, (EOVERFLOW,) if allow_overflow else ())
+
+
 def sphdvr_render_static_scratch(ctx, ds, lut, camera, tf, opts, out_ptr, stream=None):
     """As sphdvr_render, with all frame scratch in the library's fixed device array (no allocation)."""
     c, t, o = camera_struct(camera), tf_struct(tf), opts_struct(opts)
@@ -342,6 +360,15 @@ class Server:
         _check(_lib.sphdvr_server_stats(self.h, o), self.ctx)
         keys = ["p50_ms", "p99_ms", "rays_per_s", "completed", "failed", "held_bytes", "max_ms", "queued"]
         return dict(zip(keys, list(o)))
+
+    def set_batch(self, max_batch):
+        """Frames one render launch may take (1 turns batching off)."""
+        _check(_lib.sphdvr_server_set_batch(self.h, int(max_batch)), self.ctx)
+
+    def batch_stats(self):
+        o = (ctypes.c_int64 * 4)()
+        _check(_lib.sphdvr_server_batch_stats(self.h, o), self.ctx)
+        return dict(launches=o[0], frames=o[1], largest=o[2])
 
     def destroy(self):
         if self.h is not None:
