@@ -46,7 +46,7 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x ma
 # DRAM bytes (read + write) of one render launch of the default workload, from
 # the ncu capture recorded in profiles/launches_halo16m_2048.md (the render
 # kernel as it is in this tree); None for other workloads or image sizes.
-PROFILED_DRAM_BYTES = {}
+PROFILED_DRAM_BYTES = {("halo16m", 2048): 249.19e9 + 833.20e9}
 
 
 def flops_per_segment(K, D):
@@ -170,6 +170,9 @@ def main():
     ap.add_argument("--res", type=int, default=0, help="override the workload's image size (square)")
     ap.add_argument("--serve-requests", type=int, default=12,
                     help="frames pushed through the frame server after the timed region (0: skip)")
+    ap.add_argument("--batch-frames", type=int, default=8,
+                    help="small frames timed separately and as one batched launch after the timed region (<2: skip)")
+    ap.add_argument("--batch-res", type=int, default=128)
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.res > 0:
@@ -277,11 +280,44 @@ def main():
         for t_ in tickets:
             srv.wait(t_, -1)
         sv = srv.stats()
+        bs = srv.batch_stats()
         srv.destroy()
         serving = dict(requests=args.serve_requests, sizes=sizes, arrivals="Poisson, mean gap 1.5 s", workers=2,
                        p50_ms=sv["p50_ms"], p99_ms=sv["p99_ms"], mrays_per_s=sv["rays_per_s"] / 1e6,
-                       failed=int(sv["failed"]))
+                       failed=int(sv["failed"]), render_launches=bs["launches"], largest_batch=bs["largest"])
         del outs
+
+    # ---- batching: the same small frames rendered one launch each and as one batched launch
+    batching = None
+    if args.batch_frames > 1:
+        nb, rb = args.batch_frames, args.batch_res
+        cams_b = [SY.orbit_camera(rb, rb, azimuth_deg=360.0 * i / nb, elevation_deg=-30 + 60.0 * i / nb)
+                  for i in range(nb)]
+        outs_b = [torch.empty((rb, rb, 4), dtype=torch.float32, device=dev) for _ in cams_b]
+
+        def separate():
+            for c_, o_ in zip(cams_b, outs_b):
+                S.sphdvr_render(ctx, ds, lut, c_, tf, opts, o_.data_ptr(), stream=stream, allow_overflow=True)
+
+        def batched():
+            S.sphdvr_render_batch(ctx, ds, lut, cams_b, tf, opts, [o_.data_ptr() for o_ in outs_b], stream=stream,
+                                  allow_overflow=True)
+
+        tb = {}
+        for name, fn in (("separate", separate), ("batched", batched)):
+            fn()
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(3):
+                t0 = time.perf_counter()
+                fn()
+                torch.cuda.synchronize()
+                best = min(best, time.perf_counter() - t0)
+            tb[name] = best
+        batching = dict(frames=nb, size=rb, separate_ms=tb["separate"] * 1e3, batched_ms=tb["batched"] * 1e3,
+                        speedup=tb["separate"] / tb["batched"],
+                        note="wall time incl. binning, best of 3; batched = one render launch for all frames")
+        del outs_b
 
     if rank == 0:
         seg_per_frame = segs / args.steps
@@ -313,6 +349,8 @@ def main():
         )
         if serving:
             line["serving"] = serving
+        if batching:
+            line["batching"] = batching
         info = S.sphdvr_dataset_info(ds)
         line["dataset_build"] = dict(ms=t_build * 1e3, particles_per_s=w["n"] / t_build,
                                      input_bytes=int(w["n"] * 28), resident_bytes=int(info["bytes"]),

@@ -285,10 +285,12 @@ sphdvr_status sphdvr_frame_stats(sphdvr_ctx* ctx, int64_t out[16]);
  * A server owns `max_inflight` (1..8) worker threads, each with its own CUDA
  * stream and frame buffers; submitted requests are rendered in submission
  * order by whichever worker is free, so frames overlap on the GPU.  A free
- * worker takes the oldest queued request together with up to max_batch - 1
- * (default 4, see sphdvr_server_set_batch) later queued requests of the
- * same data set, table, transfer function and options, and renders them
- * with one launch (sphdvr_render_batch); a batch completes as a whole.  The
+ * worker takes the oldest queued request together with later queued requests
+ * of the same data set, table, transfer function and options, up to
+ * max_batch frames and max_batch_rays rays in all (sphdvr_server_set_batch;
+ * defaults SPHDVR_MAX_BATCH and 512*512), and renders them with one launch
+ * (sphdvr_render_batch); a batch completes as a whole.  Small frames gain
+ * most: their rays are too few to keep every SM busy until the frame ends.  The
  * device memory all workers hold for frame buffers stays within `hbm_budget`
  * bytes (datasets and tables are not counted: they belong to the caller's
  * context): a worker whose frame does not fit beside the others' holdings
@@ -322,9 +324,11 @@ sphdvr_status sphdvr_server_wait(sphdvr_server* srv, uint64_t ticket, int timeou
  * out[7] frames queued and not yet started. */
 sphdvr_status sphdvr_server_stats(sphdvr_server* srv, double out[8]);
 
-/* Frames a worker may render with one launch: 1..SPHDVR_MAX_BATCH (1 turns
- * batching off).  Applies to batches formed after the call. */
-sphdvr_status sphdvr_server_set_batch(sphdvr_server* srv, int max_batch);
+/* Batch limits: at most `max_batch` frames (1..SPHDVR_MAX_BATCH; 1 turns
+ * batching off) with at most `max_batch_rays` rays (width*height summed over
+ * the frames; >= 0) per launch; the oldest queued request is always taken,
+ * whatever its size.  Apply to batches formed after the call. */
+sphdvr_status sphdvr_server_set_batch(sphdvr_server* srv, int max_batch, int64_t max_batch_rays);
 
 /* out[0] render launches the workers made, out[1] frames those launches
  * rendered (out[1] / out[0] is the mean batch size), out[2] largest batch,

@@ -65,7 +65,8 @@ struct sphdvr_server {
   uint64_t next_ticket = 1;
   bool stop = false;
   std::vector<sphdvr::Worker*> workers;
-  int max_batch = 4;      // frames one render launch may take
+  int max_batch = SPHDVR_MAX_BATCH;  // frames one render launch may take
+  int64_t max_batch_rays = 512 * 512;  // rays of a batch beyond its first frame's
   int64_t launches = 0, batch_frames = 0, largest_batch = 0;
   size_t held_total = 0;  // device bytes all workers hold
   int waiting_mem = 0;
@@ -277,9 +278,13 @@ void worker_main(Worker* w) {
       if (S->queue.empty()) break;  // stop requested and nothing left
       rs.push_back(S->queue.front());
       S->queue.pop_front();
-      // later requests that can share the launch join it, in queue order
+      // later requests that can share the launch join it, in queue order,
+      // while the batch stays within the frame and ray limits
+      int64_t rays = (int64_t)rs[0]->a.cam.width * rs[0]->a.cam.height;
       for (auto it = S->queue.begin(); it != S->queue.end() && (int)rs.size() < S->max_batch;) {
-        if (same_launch(rs[0], *it)) {
+        const int64_t r_ = (int64_t)(*it)->a.cam.width * (*it)->a.cam.height;
+        if (rays + r_ <= S->max_batch_rays && same_launch(rs[0], *it)) {
+          rays += r_;
           rs.push_back(*it);
           it = S->queue.erase(it);
         } else {
@@ -448,12 +453,14 @@ sphdvr_status sphdvr_server_stats(sphdvr_server* S, double out[8]) {
   return SPHDVR_OK;
 }
 
-sphdvr_status sphdvr_server_set_batch(sphdvr_server* S, int max_batch) {
+sphdvr_status sphdvr_server_set_batch(sphdvr_server* S, int max_batch, int64_t max_batch_rays) {
   if (!S) return SPHDVR_EINVAL;
   if (max_batch < 1 || max_batch > SPHDVR_MAX_BATCH)
     return set_err(S->ctx, SPHDVR_EINVAL, "server_set_batch: max_batch out of [1, SPHDVR_MAX_BATCH]");
+  if (max_batch_rays < 0) return set_err(S->ctx, SPHDVR_EINVAL, "server_set_batch: max_batch_rays < 0");
   std::lock_guard<std::mutex> lk(S->mu);
   S->max_batch = max_batch;
+  S->max_batch_rays = max_batch_rays;
   return SPHDVR_OK;
 }
 

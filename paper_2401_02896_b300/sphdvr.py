@@ -99,7 +99,7 @@ def _load():
         "sphdvr_server_wait": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_int]),
         "sphdvr_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
         "sphdvr_server_destroy": (ctypes.c_int, [vp]),
-        "sphdvr_server_set_batch": (ctypes.c_int, [vp, ctypes.c_int]),
+        "sphdvr_server_set_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64]),
         "sphdvr_server_batch_stats": (ctypes.c_int, [vp, i64p]),
         "sphdvr_debug_rays": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                              ctypes.POINTER(RenderOpts), ctypes.c_int, vp, vp, vp, vp, ctypes.c_int,
@@ -361,9 +361,9 @@ class Server:
         keys = ["p50_ms", "p99_ms", "rays_per_s", "completed", "failed", "held_bytes", "max_ms", "queued"]
         return dict(zip(keys, list(o)))
 
-    def set_batch(self, max_batch):
-        """Frames one render launch may take (1 turns batching off)."""
-        _check(_lib.sphdvr_server_set_batch(self.h, int(max_batch)), self.ctx)
+    def set_batch(self, max_batch, max_batch_rays=512 * 512):
+        """Frames and rays one render launch may take (max_batch 1 turns batching off)."""
+        _check(_lib.sphdvr_server_set_batch(self.h, int(max_batch), int(max_batch_rays)), self.ctx)
 
     def batch_stats(self):
         o = (ctypes.c_int64 * 4)()

@@ -128,8 +128,9 @@ def test_server_groups_compatible_requests(env):
             assert srv.wait(tk, 120_000)
         bs = srv.batch_stats()
         st = srv.stats()
-        with pytest.raises(S.SphdvrError):
-            srv.set_batch(0)
+        for bad in ((0, 1000), (S.MAX_BATCH + 1, 1000), (2, -1)):
+            with pytest.raises(S.SphdvrError):
+                srv.set_batch(*bad)
     finally:
         srv.destroy()
     for o, ref in zip(outs, refs):
@@ -139,13 +140,15 @@ def test_server_groups_compatible_requests(env):
     assert bs["launches"] < len(reqs) and 2 <= bs["largest"] <= S.MAX_BATCH
 
 
-def test_server_without_batching(env):
+@pytest.mark.parametrize("limits", [(1, 1 << 20), (8, 0)], ids=["one_frame", "no_rays_beyond_the_first"])
+def test_server_without_batching(env, limits):
+    """Batching off, by the frame limit or by the ray limit: one launch per request."""
     S, torch, ctx, lut, lt, P, ds, _, tf, _ = env
     cams = [SY.orbit_camera(64, 64, azimuth_deg=30.0 * i) for i in range(5)]
     refs = _single(S, torch, ctx, ds, lt, cams, tf, None)
     srv = S.Server(ctx, 8 << 30, max_inflight=1)
     try:
-        srv.set_batch(1)
+        srv.set_batch(*limits)
         outs = [torch.zeros((64, 64, 4), dtype=torch.float32, device="cuda") for _ in cams]
         tickets = [srv.submit(ds, lt, c, tf, None, o.data_ptr()) for c, o in zip(cams, outs)]
         for tk in tickets:
