@@ -15,6 +15,9 @@ Higher-Order SPH Field Approximation for DVR") computes on the per-ray path:
   alternative) -- no recurrence, so no drift;
 * classification and emission-absorption compositing (Sec. 1), evaluated
   exactly per piece.
+* the quantised fixed-point path (Sec. 4.2-4.4, module ``oracle.quant``): the
+  quantisation error estimate and optimal quanta, quantised knots in exact
+  integers, and the per-ray field of exact integer coefficients.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
 may import this package.  It shares no code with ``paper_2401_02896_b300``.
