@@ -169,6 +169,28 @@ sphdvr_status sphdvr_lut_build(int kernel, int K, int D, int n_lambda, double* t
  * negative / non-finite errors. */
 sphdvr_status sphdvr_lut_error_measure(int kernel, int n_lambda, const double* err, double* E);
 
+/* Quantisation error estimate Q_E(tau, sigma) of Sec. 4.4 (derivation App. A.4)
+ * for a normalised particle (unit mass, density, smoothing length and
+ * attribute): the expected relative L2 error from rounding knot positions to
+ * multiples of the length quantum `tau` (> 0) and difference coefficients of
+ * order d to multiples of sigma / tau^d (`sigma` >= 0), for degree D (0..16).
+ * For a particle with smoothing length h and m v / (rho h^3) = pc, pass
+ * tau / h and sigma / pc.  EINVAL on a bad kernel, D or quantum. */
+sphdvr_status sphdvr_quant_error(int kernel, int D, double tau, double sigma, double* qe);
+
+/* Quantum values of Sec. 4.4 for an integer bit length `int_bits` (8..1024;
+ * int_max = 2^(int_bits-1)) and a data variance ratio A_max / (w(0) pc_rep)
+ * (> 0; A_max bounds the field, w(0) pc_rep is the representative particle's
+ * peak value): sigma_rel = ratio * w(0) / int_max and the length quantum
+ * tau_rel minimising Q_E(tau_rel, sigma_rel) (Q_E is convex in tau), both
+ * relative to the representative particle (multiply by pc_rep and h_rep), and
+ * that Q_E.  The combined per-particle error of Sec. 5.2 is sqrt(E^2 + qe^2)
+ * with E from sphdvr_lut_error_measure; e.g. M4, 64 bits, ratio 1e5, D = 3
+ * gives qe = 8.56e-5, and with K = 4 a combined 9.29e-4.  EINVAL on bad
+ * arguments. */
+sphdvr_status sphdvr_quant_params(int kernel, int D, int int_bits, double variance_ratio, double* tau_rel,
+                                  double* sigma_rel, double* qe);
+
 /* Upload a table (host arrays in the layout above, e.g. from
  * sphdvr_lut_build) to the context's device as FP32 knots, difference
  * coefficients (Sec. 2) and pieces.  The library keeps no reference to the

@@ -229,6 +229,16 @@ sphdvr_status sphdvr_last_error(const sphdvr_ctx* c, char* buf, size_t len) {
   return SPHDVR_OK;
 }
 
+sphdvr_status sphdvr_quant_error(int kernel, int D, double tau, double sigma, double* qe) {
+  return quant_error_host(kernel, D, tau, sigma, qe) == 0 ? SPHDVR_OK : SPHDVR_EINVAL;
+}
+
+sphdvr_status sphdvr_quant_params(int kernel, int D, int int_bits, double variance_ratio, double* tau_rel,
+                                  double* sigma_rel, double* qe) {
+  return quant_params_host(kernel, D, int_bits, variance_ratio, tau_rel, sigma_rel, qe) == 0 ? SPHDVR_OK
+                                                                                              : SPHDVR_EINVAL;
+}
+
 sphdvr_status sphdvr_lut_error_measure(int kernel, int n_lambda, const double* err, double* E) {
   return lut_error_measure_host(kernel, n_lambda, err, E) == 0 ? SPHDVR_OK : SPHDVR_EINVAL;
 }

@@ -460,6 +460,106 @@ int lut_error_measure_host(int kernel, int n_lambda, const double* err, double* 
   return 0;
 }
 
+// dw/dr of the kernels of kernel_value
+static ld kernel_slope(int kernel, ld r) {
+  r = std::fabs(r);
+  switch (kernel) {
+    case 0: {
+      if (r >= 2) return 0;
+      ld a = 2 - r, v = -3 * a * a;
+      if (r < 1) { ld b = 1 - r; v += 12 * b * b; }
+      return v / (4 * kPi);
+    }
+    case 1: {  // d/dr [a^4 (1 + 2r)] = -5 r a^3, a = 1 - r/2
+      if (r >= 2) return 0;
+      ld a = 1 - r / 2;
+      return (21.0L / 16.0L) / kPi * (-5 * r) * a * a * a;
+    }
+    case 2: {  // d/dr [a^6 (1 + 3r + 35/12 r^2)] = -(7/3) r (5r + 2) a^5
+      if (r >= 2) return 0;
+      ld a = 1 - r / 2, a2 = a * a;
+      return (495.0L / 256.0L) / kPi * (-7.0L / 3.0L) * r * (5 * r + 2) * a2 * a2 * a;
+    }
+    default: {
+      if (r >= 1) return 0;
+      ld a = 1 - r * r;
+      return (315.0L / 64.0L) / kPi * (-6 * r) * a * a;
+    }
+  }
+}
+
+// kappa (L2 norm of w over R^3) and kappa' (App. A.4) by GL16 on the kernel's
+// polynomial pieces (exact up to rounding).  kappa'^2 is the paper's integral
+// over s of s * int_R [d/dt w(sqrt(s^2 + t^2))]^2 dt; in polar coordinates of
+// the (s, t) half-plane it is (2/3) int_0^q r^2 w'(r)^2 dr.
+static void quant_constants(int kernel, ld* kappa, ld* kappa_p) {
+  const ld q = kernel == 3 ? 1 : 2;
+  const GL16& g = gl16();
+  const ld ends[3] = {0, 1, q};
+  ld k2 = 0, kp2 = 0;
+  for (int seg = 0; seg < 2; ++seg) {
+    const ld a = ends[seg], b = ends[seg + 1];
+    if (!(b > a)) continue;
+    for (int i = 0; i < 16; ++i) {
+      const ld r = 0.5L * (a + b) + 0.5L * (b - a) * g.x[i], wt = 0.5L * (b - a) * g.w[i];
+      const ld w = kernel_value(kernel, r), dw = kernel_slope(kernel, r);
+      k2 += wt * r * r * w * w;
+      kp2 += wt * r * r * dw * dw;
+    }
+  }
+  *kappa = std::sqrt(4 * kPi * k2);
+  *kappa_p = std::sqrt(2 * kp2 / 3);
+}
+
+// squared Q_E(tau, sigma) times (4 kappa)^2 (Sec. 4.4)
+static ld quant_radicand(ld kp, ld q, int D, ld tau, ld sigma) {
+  ld s = kp * kp * tau * tau;
+  for (int d = 0; d <= D; ++d)
+    s += 2 * std::pow(q, (ld)(2 * d + 3)) / ((2 * d + 1) * (2 * d + 3)) * sigma * sigma / std::pow(tau, (ld)(2 * d));
+  return s;
+}
+
+int quant_error_host(int kernel, int D, double tau, double sigma, double* qe) {
+  if (kernel < 0 || kernel > 3 || D < 0 || D > 16 || !(tau > 0) || !(sigma >= 0) || !std::isfinite(tau) ||
+      !std::isfinite(sigma) || !qe)
+    return 1;
+  ld kap, kp;
+  quant_constants(kernel, &kap, &kp);
+  *qe = (double)(std::sqrt(quant_radicand(kp, kernel == 3 ? 1 : 2, D, tau, sigma)) / (4 * kap));
+  return 0;
+}
+
+int quant_params_host(int kernel, int D, int int_bits, double ratio, double* tau, double* sigma, double* qe) {
+  if (kernel < 0 || kernel > 3 || D < 0 || D > 16 || int_bits < 8 || int_bits > 1024 || !(ratio > 0) ||
+      !std::isfinite(ratio) || !tau || !sigma || !qe)
+    return 1;
+  ld kap, kp;
+  quant_constants(kernel, &kap, &kp);
+  const ld q = kernel == 3 ? 1 : 2;
+  const ld sg = (ld)ratio * kernel_value(kernel, 0) / std::ldexp(1.0L, int_bits - 1);
+  // the radicand is convex in tau; tau times its derivative, as a function of
+  // x = log(tau), increases: bisect it for its root
+  auto slope = [&](ld x) {
+    const ld t = std::exp(x);
+    ld v = 2 * kp * kp * t * t;
+    for (int d = 1; d <= D; ++d)
+      v -= 2 * d * 2 * std::pow(q, (ld)(2 * d + 3)) / ((2 * d + 1) * (2 * d + 3)) * sg * sg / std::pow(t, (ld)(2 * d));
+    return v;
+  };
+  ld lo = -1, hi = 1;
+  while (slope(lo) > 0 && lo > -4000) lo -= 4;
+  while (slope(hi) < 0 && hi < 4000) hi += 4;
+  for (int it = 0; it < 200; ++it) {
+    const ld mid = 0.5L * (lo + hi);
+    (slope(mid) < 0 ? lo : hi) = mid;
+  }
+  const ld t = std::exp(0.5L * (lo + hi));
+  *tau = (double)t;
+  *sigma = (double)sg;
+  *qe = (double)(std::sqrt(quant_radicand(kp, q, D, t, sg)) / (4 * kap));
+  return 0;
+}
+
 int build_lut_host(int kernel, int K, int D, int n_lambda, double* theta, double* pieces, double* err) {
   if (kernel < 0 || kernel > 3 || K < 1 || K > 2 * kMaxM || D < 1 || D > kMaxD || n_lambda < 2 ||
       n_lambda > 65536 || !theta || !pieces)

@@ -15,6 +15,10 @@ namespace sphdvr {
 int build_lut_host(int kernel, int K, int D, int n_lambda, double* theta, double* pieces, double* err);
 // Per-particle relative approximation error of a table from its per-entry errors.  Returns 0 on success.
 int lut_error_measure_host(int kernel, int n_lambda, const double* err, double* E);
+// Quantisation error estimate Q_E(tau, sigma) (Sec. 4.4) and the quantum values
+// for a bit length and data variance ratio.  Return 0 on success.
+int quant_error_host(int kernel, int D, double tau, double sigma, double* qe);
+int quant_params_host(int kernel, int D, int int_bits, double ratio, double* tau, double* sigma, double* qe);
 
 constexpr int kChunk = 32;       // particles per chunk of the acceleration structure
 constexpr int kTile = 16;        // binning tile edge in pixels

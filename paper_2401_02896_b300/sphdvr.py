@@ -92,6 +92,10 @@ def _load():
                                                        ctypes.POINTER(RenderOpts), vp, vp]),
         "sphdvr_lut_error_measure": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                                     ctypes.POINTER(ctypes.c_double)]),
+        "sphdvr_quant_error": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                              ctypes.POINTER(ctypes.c_double)]),
+        "sphdvr_quant_params": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+                                + [ctypes.POINTER(ctypes.c_double)] * 3),
         "sphdvr_frame_stats": (ctypes.c_int, [vp, i64p]),
         "sphdvr_server_create": (ctypes.c_int, [vp, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]),
         "sphdvr_server_submit": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
@@ -211,6 +215,21 @@ def sphdvr_lut_error_measure(kernel, err):
     _check(_lib.sphdvr_lut_error_measure(_kid(kernel), int(e.shape[0]),
                                          e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(out)))
     return out.value
+
+
+def sphdvr_quant_error(kernel, D, tau, sigma):
+    """Q_E(tau, sigma) of a normalised particle (Sec. 4.4)."""
+    q = ctypes.c_double()
+    _check(_lib.sphdvr_quant_error(_kid(kernel), int(D), float(tau), float(sigma), ctypes.byref(q)))
+    return q.value
+
+
+def sphdvr_quant_params(kernel, D, int_bits, variance_ratio):
+    """(tau_rel, sigma_rel, Q_E): quantum values for a bit length and data variance ratio (Sec. 4.4)."""
+    t, s_, q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.sphdvr_quant_params(_kid(kernel), int(D), int(int_bits), float(variance_ratio), ctypes.byref(t),
+                                    ctypes.byref(s_), ctypes.byref(q)))
+    return t.value, s_.value, q.value
 
 
 def sphdvr_lut_build(kernel, K, D, n_lambda):

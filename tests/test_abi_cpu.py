@@ -128,3 +128,45 @@ def test_lut_error_measure_special_cases():
         with pytest.raises(S.SphdvrError) as e:
             S.sphdvr_lut_error_measure("m4", bad)
         assert e.value.status == S.EINVAL
+
+
+@pytest.mark.parametrize("D", [2, 3, 4, 5, 6])
+def test_quant_params_reproduce_the_printed_quantisation_errors(D):
+    """sphdvr_quant_params gives the paper's printed Q_E bars (Sec. 5.2 figure: M4, 64 bits, ratio 1e5)."""
+    g = json.load(open(os.path.join(HERE, "golden", "paper_quant_error.json")))
+    tau, sigma, qe = S.sphdvr_quant_params(g["kernel"], D, g["int_bits"], g["variance_ratio"])
+    assert abs(qe / g["QE"][str(D)] - 1) < 1e-12
+    assert abs(S.sphdvr_quant_error(g["kernel"], D, tau, sigma) / qe - 1) < 1e-15
+
+
+def test_combined_error_from_the_library_matches_the_printed_marks():
+    g = json.load(open(os.path.join(HERE, "golden", "paper_quant_error.json")))
+    for key in ("4,3", "3,2", "2,5", "4,4"):
+        K, D = map(int, key.split(","))
+        _, _, err = S.sphdvr_lut_build("m4", K, D, 257)
+        E = S.sphdvr_lut_error_measure("m4", err)
+        qe = S.sphdvr_quant_params("m4", D, 64, 1e5)[2]
+        assert abs(math.sqrt(E * E + qe * qe) / g["combined"][key] - 1) < 1.5e-4
+
+
+@pytest.mark.parametrize("kernel", ["wendland_c2", "wendland_c4", "poly6"])
+def test_quant_error_agrees_with_the_oracle(kernel):
+    from oracle import quant as OQ
+
+    for D, bits, ratio in ((1, 32, 10.0), (3, 64, 1e5), (5, 96, 1e3)):
+        t_l, s_l, q_l = S.sphdvr_quant_params(kernel, D, bits, ratio)
+        t_o, s_o, q_o = OQ.quant_params(kernel, D, bits, ratio)
+        assert abs(t_l / t_o - 1) < 1e-12 and abs(s_l / s_o - 1) < 1e-14 and abs(q_l / q_o - 1) < 1e-12
+        assert abs(S.sphdvr_quant_error(kernel, D, 3 * t_o, s_o) / OQ.quant_error(kernel, D, 3 * t_o, s_o) - 1) < 1e-12
+
+
+def test_quant_functions_reject_bad_arguments():
+    for args in (("m4", 3, 0.0, 1e-9), ("m4", 3, -1.0, 1e-9), ("m4", -1, 1e-3, 1e-9), ("m4", 3, 1e-3, -1.0),
+                 (7, 3, 1e-3, 1e-9), ("m4", 3, float("nan"), 1e-9)):
+        with pytest.raises(S.SphdvrError) as e:
+            S.sphdvr_quant_error(*args)
+        assert e.value.status == S.EINVAL
+    for args in (("m4", 3, 4, 1e5), ("m4", 3, 64, 0.0), ("m4", 3, 64, -1.0), (9, 3, 64, 1e5)):
+        with pytest.raises(S.SphdvrError) as e:
+            S.sphdvr_quant_params(*args)
+        assert e.value.status == S.EINVAL
