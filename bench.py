@@ -173,6 +173,8 @@ def main():
     ap.add_argument("--batch-frames", type=int, default=8,
                     help="small frames timed separately and as one batched launch after the timed region (<2: skip)")
     ap.add_argument("--batch-res", type=int, default=128)
+    ap.add_argument("--quant-frame", type=int, default=1,
+                    help="time the quantised integer path against FP32 anchored on a 1M-particle frame (0: skip)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.res > 0:
@@ -319,6 +321,42 @@ def main():
                         note="wall time incl. binning, best of 3; batched = one render launch for all frames")
         del outs_b
 
+    # ---- quantised fixed-point path (Sec. 4.2-4.4) beside FP32 anchored: uniform 1M particles, one
+    # smoothing length (one length quantum serves every particle), 512x512
+    quant = None
+    if args.quant_frame:
+        nq, hq, rq = 1_000_000, 0.012, 512
+        PQ = SY.uniform_cube(nq, h=hq, seed=SY.BASE_SEED + 90)
+        dsq = S.sphdvr_dataset_create(ctx, PQ["pos"], PQ["h"], PQ["mass"], PQ["density"], PQ["value"])
+        ampq = SY.particles_to_amp(PQ["mass"], PQ["value"], PQ["density"])
+        pc_rep = float(np.median(ampq / PQ["h"].astype(np.float64) ** 3))
+        # A_max: 8 times the particles overlapping a point at the mean density, each at its peak value
+        ratio = 8 * nq * 4.0 / 3.0 * math.pi * (2 * hq) ** 3
+        tau_rel, sig_rel, qe = S.sphdvr_quant_params(w["kernel"], w["D"], 64, ratio)
+        camq = SY.orbit_camera(rq, rq)
+        oq = torch.empty((rq, rq, 4), dtype=torch.float32, device=dev)
+        ref_q = torch.empty_like(oq)
+        qopts = dict(precision="int64_quant", quant_tau=tau_rel * hq, quant_sigma=sig_rel * pc_rep, ert_eps=1e-5)
+        tq = {}
+        for name, op_, img in (("fp32_anchored", None, ref_q), ("int64_quant", qopts, oq)):
+            S.sphdvr_render(ctx, dsq, lut, camq, tf, op_, img.data_ptr(), stream=stream, allow_overflow=True)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(2):
+                t0 = time.perf_counter()
+                S.sphdvr_render(ctx, dsq, lut, camq, tf, op_, img.data_ptr(), stream=stream, allow_overflow=True)
+                torch.cuda.synchronize()
+                best = min(best, time.perf_counter() - t0)
+            tq[name] = (best, S.sphdvr_frame_stats(ctx)["segments"])
+        quant = dict(workload="uniform cube 1,000,000 particles, h 0.012, perspective 512x512", int_bits=64,
+                     tau=tau_rel * hq, sigma=sig_rel * pc_rep, quant_error_estimate=qe,
+                     anchored_ms=tq["fp32_anchored"][0] * 1e3, quant_ms=tq["int64_quant"][0] * 1e3,
+                     quant_segments_per_s=tq["int64_quant"][1] / tq["int64_quant"][0],
+                     max_pixel_diff_vs_anchored=float((oq - ref_q).abs().max()),
+                     note="wall time incl. binning, best of 2")
+        S.sphdvr_dataset_free(dsq)
+        del oq, ref_q
+
     if rank == 0:
         seg_per_frame = segs / args.steps
         fps = flops_per_segment(w["K"], w["D"])
@@ -351,6 +389,8 @@ def main():
             line["serving"] = serving
         if batching:
             line["batching"] = batching
+        if quant:
+            line["quantised"] = quant
         info = S.sphdvr_dataset_info(ds)
         line["dataset_build"] = dict(ms=t_build * 1e3, particles_per_s=w["n"] / t_build,
                                      input_bytes=int(w["n"] * 28), resident_bytes=int(info["bytes"]),

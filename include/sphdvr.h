@@ -72,7 +72,18 @@ typedef enum {
    * t = j * reinit_dt (j integer) on every ray: there the running
    * coefficients are replaced by the exact sum of the active particles' own
    * pieces -- the paper's first mitigation of the drift (Sec. 4.1). */
-  SPHDVR_PREC_FP32_REINIT = 3
+  SPHDVR_PREC_FP32_REINIT = 3,
+  /* the quantised fixed-point path (Sec. 4.2-4.4): knot positions are
+   * integer multiples of quant_tau, difference coefficients of order d
+   * integer multiples of quant_sigma / quant_tau^d (rounded as Sec. 4.3
+   * prescribes, with each particle's approximation exactly compactly
+   * supported and shifted-even), and the coefficient update is exact
+   * 64-bit integer arithmetic -- no drift, no re-anchoring; the error is the
+   * quantisation error of Sec. 4.4 (sphdvr_quant_params gives quanta and
+   * estimate).  quant_sigma must bound the field as Sec. 4.4 prescribes
+   * (A_max / 2^63) so that every coefficient fits 64 bits; compositing is
+   * FP32 as in the other modes.  Not available in batched launches. */
+  SPHDVR_PREC_INT64_QUANT = 4
 } sphdvr_precision;
 
 /* Viewing rays.  Basis: f = normalize(target - eye), r = normalize(f x up),
@@ -121,6 +132,8 @@ typedef struct {
                         0 selects the default 1.0 */
   float reinit_dt;   /* FP32_REINIT: spacing of the reinitialisation knots along t (> 0); else 0 */
   int reserved[2];   /* must be 0 */
+  double quant_tau;   /* INT64_QUANT: length quantum (ray-parameter units, > 0) */
+  double quant_sigma; /* INT64_QUANT: field value quantum (> 0) */
 } sphdvr_render_opts;
 
 typedef struct sphdvr_ctx sphdvr_ctx;

@@ -125,7 +125,10 @@ sphdvr_status pack_tf(sphdvr_ctx* ctx, const sphdvr_tf* tf, std::vector<float4>&
 
 sphdvr_status check_opts(sphdvr_ctx* ctx, const sphdvr_render_opts* o) {
   if (!o) return SPHDVR_OK;
-  if (o->precision < 0 || o->precision > 3) return set_err(ctx, SPHDVR_EINVAL, "opts: precision out of range");
+  if (o->precision < 0 || o->precision > 4) return set_err(ctx, SPHDVR_EINVAL, "opts: precision out of range");
+  if (o->precision == SPHDVR_PREC_INT64_QUANT &&
+      !(o->quant_tau > 0 && std::isfinite(o->quant_tau) && o->quant_sigma > 0 && std::isfinite(o->quant_sigma)))
+    return set_err(ctx, SPHDVR_EINVAL, "opts: INT64_QUANT needs finite quant_tau > 0 and quant_sigma > 0");
   if (!(o->reinit_dt >= 0.f) || !std::isfinite(o->reinit_dt))
     return set_err(ctx, SPHDVR_EINVAL, "opts: reinit_dt must be finite and >= 0");
   if (o->precision == 3 && !(o->reinit_dt > 0.f))

@@ -138,8 +138,8 @@ __global__ void k_tile_ranges(int64_t n, const uint64_t* keys, int2* range, int 
 
 // per-degree launchers (render_d<D>.cu)
 #define SPHDVR_DECL(D)                                                                                         \
-  sphdvr_status launch_render_d##D(sphdvr_ctx* ctx, bool f64, bool dbg, bool batch, const RenderParams& p,  \
-                                   int grid, size_t smem, cudaStream_t st);                                  \
+  sphdvr_status launch_render_d##D(sphdvr_ctx* ctx, bool f64, bool dbg, bool batch, bool qt,               \
+                                   const RenderParams& p, int grid, size_t smem, cudaStream_t st);           \
   int render_occupancy_d##D(bool f64, bool dbg, size_t smem);
 SPHDVR_DECL(1)
 SPHDVR_DECL(2)
@@ -149,15 +149,15 @@ SPHDVR_DECL(5)
 SPHDVR_DECL(6)
 #undef SPHDVR_DECL
 
-static sphdvr_status dispatch_render(sphdvr_ctx* ctx, int D, bool f64, bool dbg, bool batch, const RenderParams& p,
-                                     int grid, size_t smem, cudaStream_t st) {
+static sphdvr_status dispatch_render(sphdvr_ctx* ctx, int D, bool f64, bool dbg, bool batch, bool qt,
+                                     const RenderParams& p, int grid, size_t smem, cudaStream_t st) {
   switch (D) {
-    case 1: return launch_render_d1(ctx, f64, dbg, batch, p, grid, smem, st);
-    case 2: return launch_render_d2(ctx, f64, dbg, batch, p, grid, smem, st);
-    case 3: return launch_render_d3(ctx, f64, dbg, batch, p, grid, smem, st);
-    case 4: return launch_render_d4(ctx, f64, dbg, batch, p, grid, smem, st);
-    case 5: return launch_render_d5(ctx, f64, dbg, batch, p, grid, smem, st);
-    case 6: return launch_render_d6(ctx, f64, dbg, batch, p, grid, smem, st);
+    case 1: return launch_render_d1(ctx, f64, dbg, batch, qt, p, grid, smem, st);
+    case 2: return launch_render_d2(ctx, f64, dbg, batch, qt, p, grid, smem, st);
+    case 3: return launch_render_d3(ctx, f64, dbg, batch, qt, p, grid, smem, st);
+    case 4: return launch_render_d4(ctx, f64, dbg, batch, qt, p, grid, smem, st);
+    case 5: return launch_render_d5(ctx, f64, dbg, batch, qt, p, grid, smem, st);
+    case 6: return launch_render_d6(ctx, f64, dbg, batch, qt, p, grid, smem, st);
   }
   return set_err(ctx, SPHDVR_EINVAL, "D out of range");
 }
@@ -398,6 +398,10 @@ static void common_params(const RenderArgs& a, const FrameWork& w, RenderParams&
   p.anchor_every = (prec == SPHDVR_PREC_FP32_ANCHORED) ? std::max(1, o ? o->anchor_every : 2) : 0;
   p.window_h = (o && o->window_h > 0.f) ? o->window_h : 1.0f;
   p.reinit_dt = (prec == SPHDVR_PREC_FP32_REINIT) ? o->reinit_dt : 0.f;
+  const bool qt = prec == SPHDVR_PREC_INT64_QUANT;
+  p.q_tau = qt ? o->quant_tau : 1.0;
+  p.q_inv_tau = 1.0 / p.q_tau;
+  p.q_sigma = qt ? o->quant_sigma : 1.0;
   float eps = o ? o->ert_eps : 1e-5f;
   p.tau_ert = eps > 0.f ? -std::log(eps) : 0.f;
   p.stats = w.stats;
@@ -453,13 +457,16 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
   const bool dbg = a.n_dbg > 0;
   const int grid = std::min(render_grid(ctx, a), w.table_ctas);
   const size_t smem = render_smem_bytes(a.tf_n, dbg ? 1 : kRenderWarps);
-  return dispatch_render(ctx, a.lut->D, prec == SPHDVR_PREC_FP64_NAIVE, dbg, false, p, grid, smem, st);
+  return dispatch_render(ctx, a.lut->D, prec == SPHDVR_PREC_FP64_NAIVE, dbg, false, prec == SPHDVR_PREC_INT64_QUANT, p,
+                         grid, smem, st);
 }
 
 sphdvr_status render_batch_sized(sphdvr_ctx* ctx, const RenderArgs* a, int n, cudaStream_t st, PairSizer sizer,
                                  void* user) {
   if (n < 1 || n > SPHDVR_MAX_BATCH) return set_err(ctx, SPHDVR_EINVAL, "batch: frame count out of range");
   if (n == 1) return render_frame_sized(ctx, a[0], st, sizer, user);
+  if (a[0].opts && a[0].opts->precision == SPHDVR_PREC_INT64_QUANT)
+    return set_err(ctx, SPHDVR_EINVAL, "batch: the quantised path renders one frame per launch");
   const int grid = render_grid_batch(ctx, a, n);
   const int nc = a[0].ds->n_chunks;
   int64_t tiles = 0, rays = 0;
@@ -518,8 +525,8 @@ sphdvr_status render_batch_sized(sphdvr_ctx* ctx, const RenderArgs* a, int n, cu
   p.n_items = (int)items;
   const int prec = a[0].opts ? a[0].opts->precision : SPHDVR_PREC_FP32_ANCHORED;
   const size_t smem = render_smem_bytes(a[0].tf_n, kRenderWarps);
-  return dispatch_render(ctx, a[0].lut->D, prec == SPHDVR_PREC_FP64_NAIVE, false, true, p, std::min(grid, w.table_ctas),
-                         smem, st);
+  return dispatch_render(ctx, a[0].lut->D, prec == SPHDVR_PREC_FP64_NAIVE, false, true, false, p,
+                         std::min(grid, w.table_ctas), smem, st);
 }
 
 }  // namespace sphdvr

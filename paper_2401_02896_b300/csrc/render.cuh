@@ -103,6 +103,8 @@ struct RenderParams {
   // options
   int anchor_every;  // 0: never (naive recurrence)
   float reinit_dt;   // > 0: re-anchor at the reinitialisation knots t = j reinit_dt (naive in between)
+  // quantised path (QT instantiation): length quantum tau and value quantum sigma
+  double q_tau, q_inv_tau, q_sigma;
   float window_h;    // window length limit in units of the smallest h it touches
   float tau_ert;     // stop when accumulated optical depth exceeds this
   float* out;
@@ -137,6 +139,12 @@ __device__ __forceinline__ void taylor_shift(T* c, T s) {
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = D - 1; j >= i; --j) c[j] = c[j] + s * c[j + 1];
+}
+
+__host__ __device__ constexpr int binom_i(int n, int k) {
+  int r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
 }
 
 template <int D>
@@ -390,6 +398,93 @@ __device__ __forceinline__ void knot_delta(const RenderParams& p, int j, float h
     float v = __ldg(jr + d - 1) * s;
     dl[d - 1] = (mir && !(d & 1)) ? -v : v;
   }
+}
+
+// ---- quantised fixed-point knots (Sec. 4.2-4.4): positions are integer
+// multiples of the length quantum tau, difference coefficients of order d
+// integer multiples of sigma / tau^d, and the coefficient update is exact
+// integer arithmetic.  The int64 operations wrap modulo 2^64; every value the
+// rendering reads back (a knot's localized coefficients) is a true integer of
+// magnitude below 2^63 when sigma bounds the field as Sec. 4.4 prescribes, and
+// wrapping sums and products are exact modulo 2^64, so intermediate overflow
+// cannot change it.
+
+// Integers of the quantised path are kept as uint64 (two's complement bit
+// patterns): wrapping arithmetic is defined for unsigned types.
+typedef unsigned long long u64;
+
+// integer position of sorted knot k (0..K) of a particle: tbar_0 = [t_chi / tau],
+// tbar_{+-s} = tbar_0 +- [h theta_s / tau]
+__device__ __forceinline__ u64 qknot_pos(const RenderParams& p, float4 E, float2 th, int k) {
+  const u64 t0 = (u64)__double2ll_rn(((double)E.x + (double)E.y) * p.q_inv_tau);
+  bool mir;
+  const int s = knot_slot(p.K, p.m, k, mir);
+  if (s == 0) return t0;  // the middle knot (even K)
+  const u64 off = (u64)__double2ll_rn((double)E.z * (double)(s == 1 ? th.x : th.y) * p.q_inv_tau);
+  return mir ? t0 - off : t0 + off;
+}
+
+// Quantised localized difference coefficients, orders 1..D, of sorted knot k of
+// a particle (order 0 is zero: the approximations are continuous).  Knots
+// +-theta_s take [tau^d c s^_sd / (sigma h^d)], mirrored with (-1)^(d+1); the
+// odd orders of the middle knot (even K), resp. of the knots +-theta_1 (odd K,
+// in decreasing order), follow from exact shifted evenness about tbar_0.
+template <int D>
+__device__ __noinline__ void qknot_coef(const RenderParams& p, float4 E, float2 th, int j, int k, u64* out) {
+  const int K = p.K, m = p.m;
+  u64 fr[2][D + 1], off[2];
+  const double r = p.q_tau / (double)E.z, f = (double)E.w / p.q_sigma;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    off[s] = (u64)__double2ll_rn((double)E.z * (double)(s == 0 ? th.x : th.y) * p.q_inv_tau);
+    const float* jr = p.jump + (size_t)j * 3 * D + (s + 1) * D;
+    double g = f;
+#pragma unroll
+    for (int d = 1; d <= D; ++d) {
+      g *= r;
+      fr[s][d] = s < m ? (u64)__double2ll_rn(g * (double)__ldg(jr + d - 1)) : 0ull;
+    }
+    fr[s][0] = 0;
+  }
+  // coefficients of the mirrored knot -theta_s: (-1)^(d+1) times those of +theta_s
+  auto neg = [&](int s, int d) -> u64 { return (d & 1) ? fr[s][d] : 0ull - fr[s][d]; };
+  u64 mid[D + 1];
+#pragma unroll
+  for (int d = 0; d <= D; ++d) mid[d] = 0;
+  if (!(K & 1)) {
+#pragma unroll
+    for (int d = 1; d <= D; d += 2) {
+      u64 acc = 0;
+      for (int s = 0; s < m; ++s) {
+        u64 pw = 1;
+#pragma unroll
+        for (int jx = d; jx <= D; ++jx) {
+          acc += (u64)binom_i(jx, d) * neg(s, jx) * pw;
+          pw *= off[s];
+        }
+      }
+      mid[d] = 0ull - 2ull * acc;
+    }
+  } else {
+#pragma unroll
+    for (int d = (D & 1) ? D : D - 1; d >= 1; d -= 2) {
+      u64 v = 0;
+      for (int s = 1; s < m; ++s) v -= neg(s, d);
+      for (int s = 0; s < m; ++s) {
+        u64 pw = off[s];
+#pragma unroll
+        for (int jx = d + 1; jx <= D; ++jx) {
+          v -= (u64)binom_i(jx, d) * neg(s, jx) * pw;
+          pw *= off[s];
+        }
+      }
+      fr[0][d] = v;  // odd d: the same for +theta_1 and -theta_1
+    }
+  }
+  bool mir;
+  const int s = knot_slot(K, m, k, mir);
+#pragma unroll
+  for (int d = 1; d <= D; ++d) out[d] = s == 0 ? mid[d] : (mir ? neg(s - 1, d) : fr[s - 1][d]);
 }
 
 __device__ __forceinline__ int knots_done(const RayScratch& T, int e) { return (T.knc[e >> 3] >> (4 * (e & 7))) & 15; }
@@ -766,12 +861,18 @@ static __device__ __noinline__ int nearest_entry_fp64(const df* wv, float h, int
 // instantiation so that the other modes carry none of its code.
 // BT: a batch of frames sharing data, table, transfer function and options;
 // the work queue spans the rays of all of them.
-template <int D, typename S, int NW, bool DBG, bool RE, bool BT = false>
+// QT: the quantised fixed-point path (Sec. 4.2-4.4): knots at integer multiples
+// of tau, exact integer coefficient update, no anchoring (nothing drifts).
+template <int D, typename S, int NW, bool DBG, bool RE, bool BT = false, bool QT = false>
 __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderParams p) {
   // knots per lane in a window: as many as the shared work area holds with the
   // window's D difference coefficients, its positions and its knot ids
-  constexpr int KPL = D <= 2 ? 16 : (D == 3 ? 12 : 8);
+  // (quantised path: D int64 coefficients, an int64 position, the FP32 position
+  // and the id per knot)
+  constexpr int KPLQ = kWorkBytes / (32 * (2 * D + 4) * 4) < 16 ? kWorkBytes / (32 * (2 * D + 4) * 4) : 16;
+  constexpr int KPL = QT ? KPLQ : (D <= 2 ? 16 : (D == 3 ? 12 : 8));
   constexpr int WCAP = 32 * KPL;
+  static_assert(!QT || WCAP * (2 * D + 4) * 4 <= kWorkBytes, "quantised window does not fit the work area");
   static_assert(WCAP * (D + 2) * 4 <= kWorkBytes && WCAP <= kNK, "window does not fit the work area");
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -885,6 +986,11 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     S carry[D + 1];
 #pragma unroll
     for (int d = 0; d <= D; ++d) carry[d] = (S)0;
+    // quantised path: exact coefficients qc at the integer position qct of the
+    // last knot processed
+    u64 qc[D + 1], qct = 0;
+#pragma unroll
+    for (int d = 0; d <= D; ++d) qc[d] = 0;
     int hwm = 0, nfree = 0, nal = 0, n_act = 0, whead = 0, nwait = 0, wb = 0, nnk = 0, win_count = 0;
     bool at_reinit = false;  // the next window starts at a reinitialisation knot
     long long dbg_np = 0, dbg_nc = 0;
@@ -1022,12 +1128,19 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             h_fresh = E0.z;
 #pragma unroll
             for (int d = 0; d <= D; ++d) carry[d] = (S)0;
+            if (QT) {
+#pragma unroll
+              for (int d = 0; d <= D; ++d) qc[d] = 0;
+              qct = 0;
+            }
           }
           // window end (relative to Ta): the bound F, and gamma times the
           // lower edge of the smallest bin of h among the active particles
           // (at a restart: gamma h of the particle restarted at)
           float U = kInf;
           if (F < kInf) U = (F - Ta.hi) - Ta.lo;
+          // a quantised knot lies within tau of the FP32 knot F bounds
+          if (QT && F < kInf) U -= 2.f * (float)p.q_tau;
           bool capped = false;
           if (gam * h_fresh < U) {
             U = gam * h_fresh;
@@ -1106,9 +1219,11 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
                 }
                 const float2 th = __ldg(p.theta + j);
                 const float base = (E.x - Ta.hi) + (E.y - Ta.lo);
+                const double ta_d = (double)Ta.hi + (double)Ta.lo;
 #pragma unroll 1
                 for (int k = kstart; k <= K; ++k) {
-                  const float u = fmaf(knot_sigma(K, m, th, k), E.z, base);
+                  const float u = QT ? (float)((double)(long long)qknot_pos(p, E, th, k) * p.q_tau - ta_d)
+                                     : fmaf(knot_sigma(K, m, th, k), E.z, base);
                   if (!(u < U)) break;
                   // a particle starting inside the window bounds it by its own
                   // gamma h, or by its first knot when that lies farther
@@ -1153,6 +1268,18 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
 #pragma unroll
             for (int d = 0; d <= D; ++d) A[d] = fresh ? (S)0 : carry[d];
           }
+          if (QT) {
+            // the exact polynomial at the last knot, expanded at the window start
+            double ca[D + 1], sc = p.q_sigma;
+#pragma unroll
+            for (int d = 0; d <= D; ++d) {
+              ca[d] = (double)(long long)qc[d] * sc;
+              sc *= p.q_inv_tau;
+            }
+            taylor_shift<D, double>(ca, ((double)Ta.hi + (double)Ta.lo) - (double)(long long)qct * p.q_tau);
+#pragma unroll
+            for (int d = 0; d <= D; ++d) A[d] = (S)ca[d];
+          }
           // sort by position (ties: slot, then knot index)
           const int rb = warp_bucket_sort(T.nk0, T.nv0, T.nk1, T.nv1, T_all, T.rh);
           const float* GK = rb ? T.nk1 : T.nk0;
@@ -1184,17 +1311,29 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             pl[r] = i < nc ? GV[i] : -1;
           }
           __syncwarp();
-          float* su = T.wdl + WCAP * D;
+          // quantised path: [WCAP * D] int64 coefficients, [WCAP] int64 positions
+          u64* const qd = (u64*)T.wdl;
+          u64* const qt = qd + WCAP * D;
+          float* su = QT ? (float*)(qt + WCAP) : T.wdl + WCAP * D;
           int* sv = (int*)(su + WCAP);
 #pragma unroll 2
           for (int r = 0; r < KPL; ++r) {
             if (pl[r] >= 0) {
               const int e = pl[r] & 0xffff, k = pl[r] >> 16;
               const float4 E = T.ent[e];
-              float dl[D];
-              knot_delta<D>(p, T.jj[e], E.z, E.w, k, dl);
+              if (QT) {
+                const float2 th = __ldg(p.theta + T.jj[e]);
+                u64 qa[D + 1];
+                qknot_coef<D>(p, E, th, T.jj[e], k, qa);
 #pragma unroll
-              for (int d = 0; d < D; ++d) T.wdl[(r * D + d) * 32 + lane] = dl[d];
+                for (int d = 0; d < D; ++d) qd[(r * D + d) * 32 + lane] = qa[d + 1];
+                qt[r * 32 + lane] = qknot_pos(p, E, th, k);
+              } else {
+                float dl[D];
+                knot_delta<D>(p, T.jj[e], E.z, E.w, k, dl);
+#pragma unroll
+                for (int d = 0; d < D; ++d) T.wdl[(r * D + d) * 32 + lane] = dl[d];
+              }
             }
             su[r * 32 + lane] = uu[r];
             sv[r * 32 + lane] = pl[r];
@@ -1253,63 +1392,122 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
 
           PT_BEGIN
           const float ufirst = su[lane];
-          // ---- segmented scan of the difference coefficients (Sec. 2)
-          S agg[D + 1];
-#pragma unroll
-          for (int d = 0; d <= D; ++d) agg[d] = (S)0;
-          float ulast = ufirst;
-#pragma unroll 1
-          for (int r = 0; r < cnt_l; ++r) {
-            const float ur = su[r * 32 + lane];
-            if (r > 0) taylor_shift<D, S>(agg, (S)(ur - ulast));
-#pragma unroll
-            for (int d = 1; d <= D; ++d) agg[d] += (S)T.wdl[(r * D + d - 1) * 32 + lane];
-            ulast = ur;
-          }
           const bool has = cnt_l > 0;
-          // inclusive warp scan of (agg, ulast, has)
-          S sa[D + 1];
+          // incoming polynomial at this lane's first knot: P (FP32/FP64 paths),
+          // qP at integer position qtp (quantised path)
+          S P[D + 1];
+          u64 qP[D + 1], qtp = 0;
+          if (!QT) {
+            // ---- segmented scan of the difference coefficients (Sec. 2)
+            S agg[D + 1];
 #pragma unroll
-          for (int d = 0; d <= D; ++d) sa[d] = agg[d];
-          float se = ulast;
-          int sh = has ? 1 : 0;
+            for (int d = 0; d <= D; ++d) agg[d] = (S)0;
+            float ulast = ufirst;
 #pragma unroll 1
-          for (int o2 = 1; o2 < 32; o2 <<= 1) {
-            S oa[D + 1];
+            for (int r = 0; r < cnt_l; ++r) {
+              const float ur = su[r * 32 + lane];
+              if (r > 0) taylor_shift<D, S>(agg, (S)(ur - ulast));
 #pragma unroll
-            for (int d = 0; d <= D; ++d) oa[d] = __shfl_up_sync(kFull, sa[d], o2);
-            float oe = __shfl_up_sync(kFull, se, o2);
-            int oh = __shfl_up_sync(kFull, sh, o2);
-            if (lane >= o2 && oh) {
-              if (sh) {
-                // (other, oe) (+) (mine, se) = (Shift(other, se - oe) + mine, se)
-                taylor_shift<D, S>(oa, (S)(se - oe));
+              for (int d = 1; d <= D; ++d) agg[d] += (S)T.wdl[(r * D + d - 1) * 32 + lane];
+              ulast = ur;
+            }
+            // inclusive warp scan of (agg, ulast, has)
+            S sa[D + 1];
 #pragma unroll
-                for (int d = 0; d <= D; ++d) sa[d] += oa[d];
-              } else {
+            for (int d = 0; d <= D; ++d) sa[d] = agg[d];
+            float se = ulast;
+            int sh = has ? 1 : 0;
+#pragma unroll 1
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+              S oa[D + 1];
 #pragma unroll
-                for (int d = 0; d <= D; ++d) sa[d] = oa[d];
-                se = oe;
-                sh = 1;
+              for (int d = 0; d <= D; ++d) oa[d] = __shfl_up_sync(kFull, sa[d], o2);
+              float oe = __shfl_up_sync(kFull, se, o2);
+              int oh = __shfl_up_sync(kFull, sh, o2);
+              if (lane >= o2 && oh) {
+                if (sh) {
+                  // (other, oe) (+) (mine, se) = (Shift(other, se - oe) + mine, se)
+                  taylor_shift<D, S>(oa, (S)(se - oe));
+#pragma unroll
+                  for (int d = 0; d <= D; ++d) sa[d] += oa[d];
+                } else {
+#pragma unroll
+                  for (int d = 0; d <= D; ++d) sa[d] = oa[d];
+                  se = oe;
+                  sh = 1;
+                }
               }
             }
-          }
-          // exclusive prefix
-          S pa[D + 1];
+            // exclusive prefix
+            S pa[D + 1];
 #pragma unroll
-          for (int d = 0; d <= D; ++d) pa[d] = __shfl_up_sync(kFull, sa[d], 1);
-          float pe = __shfl_up_sync(kFull, se, 1);
-          int ph = __shfl_up_sync(kFull, sh, 1);
-          if (lane == 0) ph = 0;
-          // incoming polynomial at this lane's first knot
-          S P[D + 1];
+            for (int d = 0; d <= D; ++d) pa[d] = __shfl_up_sync(kFull, sa[d], 1);
+            float pe = __shfl_up_sync(kFull, se, 1);
+            int ph = __shfl_up_sync(kFull, sh, 1);
+            if (lane == 0) ph = 0;
 #pragma unroll
-          for (int d = 0; d <= D; ++d) P[d] = A[d];
-          taylor_shift<D, S>(P, (S)ufirst);
-          if (ph) {
-            taylor_shift<D, S>(pa, (S)(ufirst - pe));
+            for (int d = 0; d <= D; ++d) P[d] = A[d];
+            taylor_shift<D, S>(P, (S)ufirst);
+            if (ph) {
+              taylor_shift<D, S>(pa, (S)(ufirst - pe));
 #pragma unroll
-            for (int d = 0; d <= D; ++d) P[d] += pa[d];
+              for (int d = 0; d <= D; ++d) P[d] += pa[d];
+            }
+          } else {
+            // ---- the same scan in exact integers (Sec. 4.2): knot positions
+            // and coefficient sums are uint64 bit patterns of int64 values
+            u64 agg[D + 1];
+#pragma unroll
+            for (int d = 0; d <= D; ++d) agg[d] = 0;
+            const u64 qfirst = has ? qt[lane] : 0ull;
+            u64 qlast = qfirst;
+#pragma unroll 1
+            for (int r = 0; r < cnt_l; ++r) {
+              const u64 tr = qt[r * 32 + lane];
+              if (r > 0) taylor_shift<D, u64>(agg, tr - qlast);
+#pragma unroll
+              for (int d = 1; d <= D; ++d) agg[d] += qd[(r * D + d - 1) * 32 + lane];
+              qlast = tr;
+            }
+            u64 sa[D + 1], se = qlast;
+#pragma unroll
+            for (int d = 0; d <= D; ++d) sa[d] = agg[d];
+            int sh = has ? 1 : 0;
+#pragma unroll 1
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+              u64 oa[D + 1];
+#pragma unroll
+              for (int d = 0; d <= D; ++d) oa[d] = __shfl_up_sync(kFull, sa[d], o2);
+              const u64 oe = __shfl_up_sync(kFull, se, o2);
+              const int oh = __shfl_up_sync(kFull, sh, o2);
+              if (lane >= o2 && oh) {
+                if (sh) {
+                  taylor_shift<D, u64>(oa, se - oe);
+#pragma unroll
+                  for (int d = 0; d <= D; ++d) sa[d] += oa[d];
+                } else {
+#pragma unroll
+                  for (int d = 0; d <= D; ++d) sa[d] = oa[d];
+                  se = oe;
+                  sh = 1;
+                }
+              }
+            }
+            u64 pa[D + 1];
+#pragma unroll
+            for (int d = 0; d <= D; ++d) pa[d] = __shfl_up_sync(kFull, sa[d], 1);
+            const u64 pe = __shfl_up_sync(kFull, se, 1);
+            int ph = __shfl_up_sync(kFull, sh, 1);
+            if (lane == 0) ph = 0;
+#pragma unroll
+            for (int d = 0; d <= D; ++d) qP[d] = qc[d];
+            taylor_shift<D, u64>(qP, qfirst - qct);
+            if (ph) {
+              taylor_shift<D, u64>(pa, qfirst - pe);
+#pragma unroll
+              for (int d = 0; d <= D; ++d) qP[d] += pa[d];
+            }
+            qtp = qfirst;
           }
           // next lane's first knot (piece end for this lane's last knot)
           float unext = __shfl_down_sync(kFull, ufirst, 1);
@@ -1351,13 +1549,29 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
               ub = ufirst;
             } else {
               ua = su[sp * 32 + lane];
-              if (sp > 0) taylor_shift<D, S>(P, (S)(ua - lastu));
+              if (QT) {
+                // exact update at the knot's integer position, then the piece's
+                // polynomial in ray units: coefficient d is qP_d sigma / tau^d
+                const u64 tcur = qt[sp * 32 + lane];
+                if (sp > 0) taylor_shift<D, u64>(qP, tcur - qtp);
 #pragma unroll
-              for (int d = 1; d <= D; ++d) P[d] += (S)T.wdl[(sp * D + d - 1) * 32 + lane];
+                for (int d = 1; d <= D; ++d) qP[d] += qd[(sp * D + d - 1) * 32 + lane];
+                qtp = tcur;
+                double sc = p.q_sigma;
+#pragma unroll
+                for (int d = 0; d <= D; ++d) {
+                  Pf.c[d] = (float)((double)(long long)qP[d] * sc);
+                  sc *= p.q_inv_tau;
+                }
+              } else {
+                if (sp > 0) taylor_shift<D, S>(P, (S)(ua - lastu));
+#pragma unroll
+                for (int d = 1; d <= D; ++d) P[d] += (S)T.wdl[(sp * D + d - 1) * 32 + lane];
+#pragma unroll
+                for (int d = 0; d <= D; ++d) Pf.c[d] = (float)P[d];
+              }
               lastu = ua;
               ub = sp + 1 < cnt_l ? su[(sp + 1) * 32 + lane] : ulane_end;
-#pragma unroll
-              for (int d = 0; d <= D; ++d) Pf.c[d] = (float)P[d];
             }
             const float a0 = fmaxf(ua, ystart);
             if (ub > a0) {
@@ -1370,13 +1584,26 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
                 double* fo = p.dbg_field + ((size_t)dbg_row * p.field_cap + row) * (D + 3);
                 fo[0] = df_to_double(Ta) + (double)ua;
                 fo[1] = df_to_double(Ta) + (double)ub;
-                for (int d = 0; d <= D; ++d) fo[2 + d] = sp < 0 ? (double)A[d] : (double)P[d];
+                double sc = p.q_sigma;
+                for (int d = 0; d <= D; ++d) {
+                  fo[2 + d] = sp < 0 ? (double)A[d] : (QT ? (double)(long long)qP[d] * sc : (double)P[d]);
+                  sc *= p.q_inv_tau;
+                }
               }
             }
           }
           if (DBG) dbg_np += npieces;
           // carry the polynomial to the window end (plain recurrence / next window)
-          {
+          if (QT) {
+            // exact: the last lane's coefficients at its last knot
+            const unsigned anym = __ballot_sync(kFull, has);
+            if (anym) {
+              const int lastlane = 31 - __clz(anym);
+#pragma unroll
+              for (int d = 0; d <= D; ++d) qc[d] = __shfl_sync(kFull, qP[d], lastlane);
+              qct = __shfl_sync(kFull, qtp, lastlane);
+            }
+          } else {
             S cpy[D + 1];
 #pragma unroll
             for (int d = 0; d <= D; ++d) cpy[d] = P[d];

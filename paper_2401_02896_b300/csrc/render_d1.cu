@@ -3,9 +3,9 @@
 
 namespace sphdvr {
 
-template <typename S, int NW, bool DBG, bool RE, bool BT = false>
+template <typename S, int NW, bool DBG, bool RE, bool BT = false, bool QT = false>
 static sphdvr_status launch(sphdvr_ctx* ctx, const RenderParams& p, int grid, size_t smem, cudaStream_t st) {
-  auto kern = k_render<1, S, NW, DBG, RE, BT>;
+  auto kern = k_render<1, S, NW, DBG, RE, BT, QT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_err(ctx, e, "render smem attribute");
   if (!ctx->ev_ready) {
@@ -29,9 +29,13 @@ static int occupancy(size_t smem) {
   return nb;
 }
 
-sphdvr_status launch_render_d1(sphdvr_ctx* ctx, bool f64, bool dbg, bool batch, const RenderParams& p, int grid,
-                                size_t smem, cudaStream_t st) {
+sphdvr_status launch_render_d1(sphdvr_ctx* ctx, bool f64, bool dbg, bool batch, bool qt, const RenderParams& p,
+                                int grid, size_t smem, cudaStream_t st) {
   const bool re = p.reinit_dt > 0.f;  // FP32 only
+  if (qt) {  // quantised path: integer knots and coefficients, FP32 compositing
+    if (dbg) return launch<float, 1, true, false, false, true>(ctx, p, grid, smem, st);
+    return launch<float, kRenderWarps, false, false, false, true>(ctx, p, grid, smem, st);
+  }
   if (batch) {  // several frames, one work queue
     if (f64) return launch<double, kRenderWarps, false, false, true>(ctx, p, grid, smem, st);
     return re ? launch<float, kRenderWarps, false, true, true>(ctx, p, grid, smem, st)

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libsphdvr.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, EOVERFLOW, EDEVICE, ENOTFOUND = range(9)
 KERNELS = {"m4": 0, "wendland_c2": 1, "wendland_c4": 2, "poly6": 3}
-PRECISIONS = {"fp32_anchored": 0, "fp32_naive": 1, "fp64_naive": 2, "fp32_reinit": 3}
+PRECISIONS = {"fp32_anchored": 0, "fp32_naive": 1, "fp64_naive": 2, "fp32_reinit": 3, "int64_quant": 4}
 
 
 class SphdvrError(RuntimeError):
@@ -61,6 +61,8 @@ class RenderOpts(ctypes.Structure):
         ("window_h", ctypes.c_float),
         ("reinit_dt", ctypes.c_float),
         ("reserved", ctypes.c_int * 2),
+        ("quant_tau", ctypes.c_double),
+        ("quant_sigma", ctypes.c_double),
     ]
 
 
@@ -190,6 +192,8 @@ def opts_struct(opts=None):
     o.persistent = int(opts.get("persistent", 1))
     o.window_h = float(opts.get("window_h", 0.0))
     o.reinit_dt = float(opts.get("reinit_dt", 0.0))
+    o.quant_tau = float(opts.get("quant_tau", 0.0))
+    o.quant_sigma = float(opts.get("quant_sigma", 0.0))
     return o
 
 

@@ -1,0 +1,154 @@
+"""GPU parity of the quantised fixed-point path (precision INT64_QUANT, Sec. 4.2-4.4).
+
+The CUDA path quantises every candidate's knots and difference coefficients
+(Sec. 4.3) and runs the coefficient update in exact 64-bit integers inside its
+windows; the oracle (``oracle.quant``) quantises the same candidates with
+Python integers and sums each interval's coefficients explicitly.  The two
+take their rounding decisions from different FP arithmetic (device: FP32
+table, FP64 products; oracle: FP64 table), so a knot may land one quantum
+apart and a free coefficient differ in its last bits: the field is compared in
+relative L2 (1e-5), the pixels per channel (2e-4), like the other modes.
+"""
+import numpy as np
+import pytest
+
+from oracle import quant as Q
+from paper_2401_02896_b300 import synthetic as SY
+
+from _helpers import FIELD_REL_L2, PIXEL_ABS, field_rel_l2, oracle_lut
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2401_02896_b300 import sphdvr
+
+    return sphdvr
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    c = S.sphdvr_create(0)
+    yield c
+    S.sphdvr_destroy(c)
+
+
+def _parts(P):
+    return dict(pos=P["pos"], h=P["h"], amp=SY.particles_to_amp(P["mass"], P["value"], P["density"]))
+
+
+def _quanta(S, P, kernel, D, lut, cam, pix, margin=2.0):
+    """tau and sigma of Sec. 4.4 for 64-bit integers: sigma = A_max / 2^63 with A_max `margin` times
+    the largest field value the oracle finds on the sampled rays, tau minimising Q_E for the median
+    particle."""
+    import oracle
+
+    parts = _parts(P)
+    R = oracle.render(parts, lut, cam, SY.tf_bumps(), np.asarray(pix, np.int32), field_cap=1 << 14)
+    fmax = 0.0
+    for r in range(len(pix)):
+        F = R["field"][r][: int(R["stats"][r, 5])]
+        if len(F):
+            ts = np.linspace(F[0, 0], F[-1, 1], 4001)
+            fmax = max(fmax, float(np.abs(oracle.field_eval(F, ts)).max()))
+    h_rep = float(np.median(P["h"]))
+    pc_rep = float(np.median(parts["amp"] / P["h"].astype(np.float64) ** 3))
+    ratio = margin * fmax / (float(oracle.kernel_w(kernel, 0.0)) * pc_rep)
+    tau_rel, sig_rel, qe = S.sphdvr_quant_params(kernel, D, 64, ratio)
+    return tau_rel * h_rep, sig_rel * pc_rep, qe
+
+
+def _mk(S, ctx, P, lut):
+    ds = S.sphdvr_dataset_create(ctx, P["pos"], P["h"], P["mass"], P["density"], P["value"])
+    lt = S.sphdvr_lut_create(ctx, lut["kernel"], lut["K"], lut["D"], lut["n_lambda"], lut["theta"], lut["pieces"])
+    return ds, lt
+
+
+@pytest.mark.parametrize("kernel,K,D", [("m4", 4, 3), ("m4", 3, 3), ("wendland_c2", 4, 2)])
+def test_quantised_rays_match_the_quantised_oracle(S, ctx, kernel, K, D):
+    P = SY.uniform_cube()
+    lut = oracle_lut(kernel, K, D, 1025)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.ortho_camera_z(32, 32)
+    tf = SY.tf_bumps()
+    pix = np.concatenate([SY.pixel_sample(32, 32, 14, seed=61), [0, 31, 32 * 31, 32 * 32 - 1]]).astype(np.int32)
+    tau, sigma, qe = _quanta(S, P, kernel, D, lut, cam, pix)
+    opts = dict(precision="int64_quant", quant_tau=tau, quant_sigma=sigma, ert_eps=0.0)
+    try:
+        g = S.sphdvr_debug_rays(ctx, ds, lt, cam, tf, opts, pix, cand_cap=4096, field_cap=1 << 14, D=D)
+        assert not g["overflow"]
+        R = Q.quant_render(_parts(P), lut, cam, tf, pix, tau, sigma)
+        worst_f, worst_p = 0.0, 0.0
+        for r in range(len(pix)):
+            mine = g["field"][r, : int(g["counts"][r, 2])]
+            ref = R["field"][r]
+            if len(ref) == 0:
+                assert np.abs(mine[:, 2:]).max(initial=0.0) == 0.0
+                continue
+            worst_f = max(worst_f, field_rel_l2(mine, ref, D))
+        worst_p = float(np.abs(g["rgba"] - R["rgba"]).max())
+        print("quantised %s K=%d D=%d: tau %.3g sigma %.3g Q_E %.2g; field %.3g, pixel %.3g"
+              % (kernel, K, D, tau, sigma, qe, worst_f, worst_p))
+        assert worst_f <= FIELD_REL_L2
+        assert worst_p <= PIXEL_ABS
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
+
+
+def test_quantised_frame_through_the_render_entry(S, ctx):
+    """The full-frame kernel (work queue, 4 warps per CTA) gives the parity hook's pixels and agrees with the
+    other drift-free mode, FP32 with re-anchored windows, within the quantisation error.  (The naive FP64
+    recurrence is not a reference at scale: its coefficients keep the FP32 rounding residue of every finished
+    particle and drift, Sec. 4.1.)  One length quantum serves all particles (Sec. 4.4), so the data set has
+    one smoothing length; sigma bounds the field with a margin of 4 over the sampled rays' maximum."""
+    import torch
+
+    P = SY.uniform_cube(4000, h=0.05, seed=SY.BASE_SEED + 41)
+    lut = oracle_lut("m4", 4, 3, 1025)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.orbit_camera(64, 48)
+    tf = SY.tf_bumps()
+    pix = SY.pixel_sample(64, 48, 12, seed=62)
+    tau, sigma, qe = _quanta(S, P, "m4", 3, lut, cam, pix, margin=4.0)
+    opts = dict(precision="int64_quant", quant_tau=tau, quant_sigma=sigma, ert_eps=0.0)
+    try:
+        a = torch.zeros((48, 64, 4), dtype=torch.float32, device="cuda")
+        b = torch.zeros_like(a)
+        S.sphdvr_render(ctx, ds, lt, cam, tf, opts, a.data_ptr())
+        S.sphdvr_render(ctx, ds, lt, cam, tf, dict(ert_eps=0.0), b.data_ptr())
+        torch.cuda.synchronize()
+        g = S.sphdvr_debug_rays(ctx, ds, lt, cam, tf, opts, pix)
+        img = a.cpu().numpy().reshape(-1, 4)
+        assert np.abs(img[pix] - g["rgba"]).max() <= 1e-6
+        assert float((a - b).abs().max()) <= 1e-3
+        assert a[..., 3].max().item() > 0.05
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
+
+
+def test_quantised_option_errors(S, ctx):
+    import torch
+
+    P = SY.uniform_cube()
+    lut = oracle_lut("m4", 4, 3, 1025)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.ortho_camera_z(16, 16)
+    o = torch.zeros((16, 16, 4), dtype=torch.float32, device="cuda")
+    try:
+        for bad in (dict(precision="int64_quant"), dict(precision="int64_quant", quant_tau=1e-4),
+                    dict(precision="int64_quant", quant_tau=-1.0, quant_sigma=1e-12),
+                    dict(precision="int64_quant", quant_tau=float("inf"), quant_sigma=1e-12)):
+            with pytest.raises(S.SphdvrError) as e:
+                S.sphdvr_render(ctx, ds, lt, cam, SY.tf_bumps(), bad, o.data_ptr())
+            assert e.value.status == S.EINVAL
+        with pytest.raises(S.SphdvrError) as e:
+            S.sphdvr_render_batch(ctx, ds, lt, [cam, cam], SY.tf_bumps(),
+                                  dict(precision="int64_quant", quant_tau=1e-4, quant_sigma=1e-12),
+                                  [o.data_ptr(), o.data_ptr()])
+        assert e.value.status == S.EINVAL
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
