@@ -49,6 +49,22 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x ma
 PROFILED_DRAM_BYTES = {("halo16m", 2048): 249.19e9 + 833.20e9}
 
 
+def replica_rate(total_ms, rays, dist=None, device="cpu"):
+    """Whole-job rate of N replicas (one frame stream per rank, no data-path collective):
+    (slowest rank's time in ms, all ranks' rays / that time in Mrays/s).  The only
+    collectives are a MAX over the ranks' times and a SUM of their rays."""
+    t_max, rays_all = float(total_ms), float(rays)
+    if dist is not None:
+        import torch
+
+        t = torch.tensor([t_max], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        r = torch.tensor([rays_all], dtype=torch.float64, device=device)
+        dist.all_reduce(r, op=dist.ReduceOp.SUM)
+        t_max, rays_all = float(t.item()), float(r.item())
+    return t_max, rays_all / (t_max / 1e3) / 1e6
+
+
 def flops_per_segment(K, D):
     """Algorithmic FP32 operations per particle-ray segment (FMA = 2):
     candidate test 20; knot generation 3 + 2(K+1) + 2D(K+1); per knot the
@@ -246,13 +262,7 @@ def main():
     frame_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     total_ms = sum(frame_ms)
     clocks = clocks_stop(proc, fh, clk_path, local)
-    t_max = total_ms
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    rays = W * H * args.steps * world
-    value = rays / (t_max / 1e3) / 1e6
+    t_max, value = replica_rate(total_ms, W * H * args.steps, dist, dev)
 
     # ---- end to end: host output buffer, copies inside the call
     host = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True).numpy()
