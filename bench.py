@@ -315,8 +315,20 @@ def main():
             S.sphdvr_render_batch(ctx, ds, lut, cams_b, tf, opts, [o_.data_ptr() for o_ in outs_b], stream=stream,
                                   allow_overflow=True)
 
+        # the same frames from a frame plan captured into one CUDA graph
+        pairs_max = 0
+        for c_, o_ in zip(cams_b, outs_b):
+            S.sphdvr_render(ctx, ds, lut, c_, tf, opts, o_.data_ptr(), stream=stream, allow_overflow=True)
+            pairs_max = max(pairs_max, S.sphdvr_frame_stats(ctx)["pairs"])
+        plan = S.FramePlan(ctx, ds, lut, tf, opts, rb, rb, int(1.5 * pairs_max) + 64)
+        gs = torch.cuda.Stream(dev)
+        graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=gs, capture_error_mode="thread_local"):
+            for c_, o_ in zip(cams_b, outs_b):
+                plan.render(c_, o_.data_ptr(), stream=gs.cuda_stream)
         tb = {}
-        for name, fn in (("separate", separate), ("batched", batched)):
+        for name, fn in (("separate", separate), ("batched", batched), ("graph", graph.replay)):
             fn()
             torch.cuda.synchronize()
             best = float("inf")
@@ -326,9 +338,14 @@ def main():
                 torch.cuda.synchronize()
                 best = min(best, time.perf_counter() - t0)
             tb[name] = best
+        plan_overflow = plan.overflowed()
+        del graph
+        plan.destroy()
         batching = dict(frames=nb, size=rb, separate_ms=tb["separate"] * 1e3, batched_ms=tb["batched"] * 1e3,
-                        speedup=tb["separate"] / tb["batched"],
-                        note="wall time incl. binning, best of 3; batched = one render launch for all frames")
+                        speedup=tb["separate"] / tb["batched"], graph_ms=tb["graph"] * 1e3,
+                        graph_pair_overflow=plan_overflow,
+                        note="wall time incl. binning, best of 3; batched = one render launch for all frames; "
+                             "graph = one replay of the frames captured from a frame plan")
         del outs_b
 
     # ---- quantised fixed-point path (Sec. 4.2-4.4) beside FP32 anchored: uniform 1M particles, one

@@ -274,6 +274,32 @@ sphdvr_status sphdvr_render_batch(sphdvr_ctx* ctx, const sphdvr_dataset* ds, con
                                   const sphdvr_camera* cams, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
                                   float* const* rgba_out, void* stream);
 
+/* Frame plans (no counterpart in the paper: a serving service).  A plan holds
+ * every device buffer of a frame of at most max_width x max_height pixels and
+ * the uploaded transfer function, so that sphdvr_frame_plan_render neither
+ * allocates, synchronises with the host nor copies from the host: it only
+ * enqueues kernels, device copies and memsets on `stream`, and can be
+ * captured into a CUDA graph (stream capture) and replayed; a replay renders
+ * the captured camera into the captured image.  The chunk-tile pairs of a
+ * frame go into buffers of `pair_cap` entries (the count is never read back;
+ * the unused entries are sorted along, so a frame costs the sort of pair_cap
+ * entries): size it from sphdvr_frame_stats()[4] of a representative frame
+ * with a margin.  A frame with more pairs drops the excess (its image is then
+ * wrong) and sets a flag that sphdvr_frame_plan_overflowed reads and clears
+ * (synchronising).  Data set, table, options and transfer function are fixed
+ * at creation; the data set and table must outlive the plan, the plan its
+ * context.  Renders of one plan must not overlap (they share its buffers).
+ * EINVAL for sizes out of [1, 32768], pair_cap out of [2, 2^31 - 1], a NULL
+ * argument, or a camera larger than the plan. */
+typedef struct sphdvr_frame_plan sphdvr_frame_plan;
+sphdvr_status sphdvr_frame_plan_create(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+                                       const sphdvr_tf* tf, const sphdvr_render_opts* opts, int max_width,
+                                       int max_height, int64_t pair_cap, sphdvr_frame_plan** plan);
+sphdvr_status sphdvr_frame_plan_render(sphdvr_frame_plan* plan, const sphdvr_camera* cam, float* rgba_out,
+                                       void* stream);
+sphdvr_status sphdvr_frame_plan_overflowed(sphdvr_frame_plan* plan, int* overflowed);
+sphdvr_status sphdvr_frame_plan_destroy(sphdvr_frame_plan* plan);
+
 /* Allocation-free form of sphdvr_render (no counterpart in the paper: a
  * library service for callers that must not allocate device memory while
  * they render, e.g. a server whose device memory is all handed to its own

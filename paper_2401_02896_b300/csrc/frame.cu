@@ -105,12 +105,18 @@ __global__ void k_chunk_project(int n_chunks, const float4* clo, const float4* c
   ntile[c] = cnt;
 }
 
+// cap: pairs beyond it are dropped (capacity-bound binning sets *ovf instead)
 __global__ void k_emit_pairs(int n_chunks, const float4* rect, const unsigned* front_ord, const uint32_t* ntile,
-                             const uint32_t* off, int tiles_x, int tiles_y, uint64_t* keys, uint32_t* vals) {
+                             const uint32_t* off, int tiles_x, int tiles_y, uint64_t* keys, uint32_t* vals,
+                             uint32_t cap, unsigned* ovf) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_chunks) return;
   uint32_t n = ntile[c];
   if (!n) return;
+  if ((uint64_t)off[c] + n > cap) {
+    if (ovf) atomicOr(ovf, 1u);
+    n = off[c] < cap ? cap - off[c] : 0;
+  }
   float4 r = rect[c];
   int tx0 = max(0, (int)floorf(r.x / kTile)), tx1 = min(tiles_x - 1, (int)floorf(r.z / kTile));
   int ty0 = max(0, (int)floorf(r.y / kTile));
@@ -126,6 +132,26 @@ __global__ void k_emit_pairs(int n_chunks, const float4* rect, const unsigned* f
 
 // [first, end) of each tile's pairs, as indices into the pair arrays that
 // start `base` entries before `keys`
+// Capacity-bound binning: the entries [min(*total, cap), cap) get the largest
+// key, so that a sort of all cap entries leaves the frame's pairs in front.
+__global__ void k_pad_pairs(const uint32_t* total, uint32_t cap, uint64_t* keys, uint32_t* vals) {
+  const uint32_t n = min(*total, cap);
+  for (uint32_t i = n + blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+    keys[i] = ~0ull;
+    vals[i] = 0;
+  }
+}
+
+// k_tile_ranges for the first min(*total, cap) of cap sorted entries
+__global__ void k_tile_ranges_dev(const uint32_t* total, uint32_t cap, const uint64_t* keys, int2* range) {
+  const int64_t n = min(*total, cap);
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int t = (int)(keys[i] >> 32);
+  if (i == 0 || (int)(keys[i - 1] >> 32) != t) range[t].x = (int)i;
+  if (i == n - 1 || (int)(keys[i + 1] >> 32) != t) range[t].y = (int)(i + 1);
+}
+
 __global__ void k_tile_ranges(int64_t n, const uint64_t* keys, int2* range, int base) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -351,7 +377,7 @@ static sphdvr_status sort_frame(sphdvr_ctx* ctx, const RenderArgs& a, const floa
   uint64_t* keys = w.pair_key + base;
   uint32_t* vals = w.pair_val + base;
   k_emit_pairs<<<(nc + 255) / 256, 256, 0, st>>>(nc, rect, w.chunk_front, w.chunk_ntile, w.chunk_off, tiles_x,
-                                                 tiles_y, keys, vals);
+                                                 tiles_y, keys, vals, 0xffffffffu, nullptr);
   ++ctx->launches;
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(ctx, e, "k_emit_pairs");
   int tbits = 0;
@@ -459,6 +485,53 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
   const size_t smem = render_smem_bytes(a.tf_n, dbg ? 1 : kRenderWarps);
   return dispatch_render(ctx, a.lut->D, prec == SPHDVR_PREC_FP64_NAIVE, dbg, false, prec == SPHDVR_PREC_INT64_QUANT, p,
                          grid, smem, st);
+}
+
+sphdvr_status render_frame_planned(sphdvr_ctx* ctx, const RenderArgs& a, const FrameWork& w, int grid, unsigned* ovf,
+                                   cudaStream_t st) {
+  const sphdvr_dataset* ds = a.ds;
+  const int tiles_x = (a.cam.width + kTile - 1) / kTile, tiles_y = (a.cam.height + kTile - 1) / kTile;
+  const int n_tiles = tiles_x * tiles_y;
+  const int nc = ds->n_chunks;
+  const uint32_t cap = (uint32_t)std::min<size_t>(w.pair_cap, 0xffffffffu);
+  if (cap < 2 || w.tmp_words < sort_tmp_words(cap)) return set_err(ctx, SPHDVR_EINVAL, "plan: pair buffers too small");
+  sphdvr_status s;
+  cudaError_t e;
+  if ((s = project_frame(ctx, a, w.chunk_rect, w, st, nullptr)) != SPHDVR_OK) return s;
+  const uint32_t* d_total = w.chunk_off + nc;
+  k_emit_pairs<<<(nc + 255) / 256, 256, 0, st>>>(nc, w.chunk_rect, w.chunk_front, w.chunk_ntile, w.chunk_off, tiles_x,
+                                                 tiles_y, w.pair_key, w.pair_val, cap, ovf);
+  ++ctx->launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(ctx, e, "k_emit_pairs");
+  k_pad_pairs<<<std::max(1u, std::min(1024u, (cap + 255) / 256)), 256, 0, st>>>(d_total, cap, w.pair_key, w.pair_val);
+  ++ctx->launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(ctx, e, "k_pad_pairs");
+  int tbits = 0;
+  while ((1 << tbits) < n_tiles) ++tbits;
+  if ((s = radix_sort_u64(ctx, w.pair_key, w.pair_val, w.pair_key2, w.pair_val2, cap, 32 + tbits, w.tmp, st)) !=
+      SPHDVR_OK)
+    return s;
+  if ((e = cudaMemsetAsync(w.tile_range, 0, (size_t)n_tiles * sizeof(int2), st)) != cudaSuccess)
+    return cuda_err(ctx, e, "tile range memset");
+  k_tile_ranges_dev<<<(cap + 255) / 256, 256, 0, st>>>(d_total, cap, w.pair_key, w.tile_range);
+  ++ctx->launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(ctx, e, "k_tile_ranges_dev");
+  if ((s = clear_counters(ctx, w, st)) != SPHDVR_OK) return s;
+  RenderParams p;
+  common_params(a, w, p);
+  p.cam = a.cam;
+  p.chunk_rect = w.chunk_rect;
+  p.pair_key = w.pair_key;
+  p.pair_val = w.pair_val;
+  p.tile_range = w.tile_range;
+  p.tiles_x = tiles_x;
+  p.tiles_y = tiles_y;
+  p.out = a.out;
+  p.n_items = n_tiles * kTile * kTile;
+  const int prec = a.opts ? a.opts->precision : SPHDVR_PREC_FP32_ANCHORED;
+  const size_t smem = render_smem_bytes(a.tf_n, kRenderWarps);
+  return dispatch_render(ctx, a.lut->D, prec == SPHDVR_PREC_FP64_NAIVE, false, false, prec == SPHDVR_PREC_INT64_QUANT,
+                         p, std::min(grid, w.table_ctas), smem, st);
 }
 
 sphdvr_status render_batch_sized(sphdvr_ctx* ctx, const RenderArgs* a, int n, cudaStream_t st, PairSizer sizer,

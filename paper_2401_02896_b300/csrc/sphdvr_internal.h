@@ -194,6 +194,13 @@ sphdvr_status render_frame_sized(sphdvr_ctx* ctx, const RenderArgs& a, cudaStrea
 // pair buffers are sized by `sizer` for the pairs of all frames.
 sphdvr_status render_batch_sized(sphdvr_ctx* ctx, const RenderArgs* a, int n, cudaStream_t st, PairSizer sizer,
                                  void* user);
+// Capacity-bound frame (no host synchronisation, allocation or host copy, so
+// it can be captured into a CUDA graph): bins into w's pair buffers of
+// w.pair_cap entries (pairs beyond are dropped and *ovf is set), sorts all
+// w.pair_cap entries, and renders with `grid` CTAs.  w.tf must already hold
+// the transfer function.
+sphdvr_status render_frame_planned(sphdvr_ctx* ctx, const RenderArgs& a, const FrameWork& w, int grid, unsigned* ovf,
+                                   cudaStream_t st);
 // The sizer of render_frame: grows the context's pair buffers.
 sphdvr_status ctx_pair_sizer(sphdvr_ctx* ctx, FrameWork& w, size_t pairs, void* user);
 // Device bytes a frame needs besides its pair buffers, and the pair buffers'

@@ -88,6 +88,11 @@ def _load():
                                          ctypes.POINTER(RenderOpts), vp, vp]),
         "sphdvr_render_batch": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                                ctypes.POINTER(RenderOpts), ctypes.POINTER(vp), vp]),
+        "sphdvr_frame_plan_create": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Tf), ctypes.POINTER(RenderOpts),
+                                                    ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(vp)]),
+        "sphdvr_frame_plan_render": (ctypes.c_int, [vp, ctypes.POINTER(Camera), vp, vp]),
+        "sphdvr_frame_plan_overflowed": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
+        "sphdvr_frame_plan_destroy": (ctypes.c_int, [vp]),
         "sphdvr_render_host": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                               ctypes.POINTER(RenderOpts), vp, vp]),
         "sphdvr_render_static_scratch": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
@@ -351,6 +356,33 @@ def sphdvr_debug_rays(ctx, ds, lut, camera, tf, opts, pixels, cand_cap=0, field_
                                 _p(rgba), _p(counts), _p(cands), int(cand_cap), _p(field), int(field_cap))
     _check(st, ctx, (EOVERFLOW,))
     return dict(rgba=rgba, counts=counts, cand_ids=cands, field=field, overflow=st == EOVERFLOW)
+
+
+class FramePlan:
+    """Preallocated frame (no allocation, host synchronisation or host copy per render: capturable)."""
+
+    def __init__(self, ctx, ds, lut, tf, opts, max_width, max_height, pair_cap):
+        self.ctx = ctx
+        t, o = tf_struct(tf), opts_struct(opts)
+        h = ctypes.c_void_p()
+        _check(_lib.sphdvr_frame_plan_create(ctx, ds, lut, ctypes.byref(t), ctypes.byref(o), int(max_width),
+                                             int(max_height), int(pair_cap), ctypes.byref(h)), ctx)
+        self.h = h
+
+    def render(self, camera, out_ptr, stream=None):
+        c = camera_struct(camera)
+        _check(_lib.sphdvr_frame_plan_render(self.h, ctypes.byref(c), ctypes.c_void_p(out_ptr),
+                                             ctypes.c_void_p(stream) if stream else None), self.ctx)
+
+    def overflowed(self):
+        v = ctypes.c_int()
+        _check(_lib.sphdvr_frame_plan_overflowed(self.h, ctypes.byref(v)), self.ctx)
+        return bool(v.value)
+
+    def destroy(self):
+        if self.h is not None:
+            _check(_lib.sphdvr_frame_plan_destroy(self.h))
+            self.h = None
 
 
 class Server:
