@@ -189,6 +189,8 @@ def main():
     ap.add_argument("--batch-frames", type=int, default=8,
                     help="small frames timed separately and as one batched launch after the timed region (<2: skip)")
     ap.add_argument("--batch-res", type=int, default=128)
+    ap.add_argument("--scatter-frame", type=int, default=1,
+                    help="time the paper's scatter-sort pass order against ray gathering on a 1M-particle frame (0: skip)")
     ap.add_argument("--quant-frame", type=int, default=1,
                     help="time the quantised integer path against FP32 anchored on a 1M-particle frame (0: skip)")
     args = ap.parse_args()
@@ -386,6 +388,40 @@ def main():
         S.sphdvr_dataset_free(dsq)
         del oq, ref_q
 
+    # ---- the paper's pass order (scatter knots per particle, one sort, accumulate per ray) against ray
+    # gathering on the 1M-particle halo mixture, 256x256
+    scatter = None
+    if args.scatter_frame:
+        w1 = WORKLOADS["halo1m"]
+        P1, tf1 = make_inputs(w1, "cuda")
+        t1 = {k: torch.from_numpy(np.ascontiguousarray(P1[k])).to(dev) for k in ("pos", "h", "mass", "density", "value")}
+        ds1 = S.sphdvr_dataset_create(ctx, t1["pos"], t1["h"], t1["mass"], t1["density"], t1["value"])
+        del t1
+        cam1 = SY.orbit_camera(256, 256)
+        ga = torch.empty((256, 256, 4), dtype=torch.float32, device=dev)
+        sc = torch.empty_like(ga)
+        ts_ = {}
+        for name, fn in (("gather", lambda: S.sphdvr_render(ctx, ds1, lut, cam1, tf1, None, ga.data_ptr(),
+                                                             stream=stream, allow_overflow=True)),
+                         ("scatter", lambda: S.sphdvr_render_scatter(ctx, ds1, lut, cam1, tf1, None, sc.data_ptr(),
+                                                                     stream=stream))):
+            fn()
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(2):
+                t0 = time.perf_counter()
+                fn()
+                torch.cuda.synchronize()
+                best = min(best, time.perf_counter() - t0)
+            ts_[name] = (best, S.sphdvr_frame_stats(ctx)["knots"])
+        scatter = dict(workload="halo mixture 1,000,000 particles, perspective 256x256", gather_ms=ts_["gather"][0] * 1e3,
+                       scatter_ms=ts_["scatter"][0] * 1e3, knots=ts_["scatter"][1],
+                       slowdown=ts_["scatter"][0] / ts_["gather"][0],
+                       max_pixel_diff=float((ga - sc).abs().max()),
+                       note="wall time incl. binning / scatter and sort, best of 2")
+        S.sphdvr_dataset_free(ds1)
+        del ga, sc
+
     if rank == 0:
         seg_per_frame = segs / args.steps
         fps = flops_per_segment(w["K"], w["D"])
@@ -420,6 +456,8 @@ def main():
             line["batching"] = batching
         if quant:
             line["quantised"] = quant
+        if scatter:
+            line["scatter_order"] = scatter
         info = S.sphdvr_dataset_info(ds)
         line["dataset_build"] = dict(ms=t_build * 1e3, particles_per_s=w["n"] / t_build,
                                      input_bytes=int(w["n"] * 28), resident_bytes=int(info["bytes"]),

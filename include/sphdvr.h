@@ -274,6 +274,22 @@ sphdvr_status sphdvr_render_batch(sphdvr_ctx* ctx, const sphdvr_dataset* ds, con
                                   const sphdvr_camera* cams, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
                                   float* const* rgba_out, void* stream);
 
+/* The pass order the paper states (Sec. 2, "Method Overview"), as an
+ * alternative to sphdvr_render's ray gathering: (1) every particle computes
+ * its knots on every ray it meets and scatters them into one frame-wide list,
+ * (2) the list is sorted by (ray, position), (3) every ray runs the
+ * coefficient update over its sorted knots and composites.  The update is the
+ * plain recurrence in FP64, with each knot's difference coefficients taken in
+ * FP64 as the difference of the particle's adjacent pieces, so that every
+ * particle's differences cancel to FP64 rounding and the recurrence keeps no
+ * FP32 residue (the drift of Sec. 4.1 stays at FP64 level).  Same arguments and image layout as sphdvr_render; opts: only
+ * ert_eps is used.  The frame's knots are held at once (24 bytes each with
+ * the sort's second buffer): EOVERFLOW (nothing rendered) beyond 2^31 - 1
+ * knots; at most 2^29 particles. */
+sphdvr_status sphdvr_render_scatter(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+                                    const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
+                                    float* rgba_out, void* stream);
+
 /* Frame plans (no counterpart in the paper: a serving service).  A plan holds
  * every device buffer of a frame of at most max_width x max_height pixels and
  * the uploaded transfer function, so that sphdvr_frame_plan_render neither

@@ -476,6 +476,34 @@ sphdvr_status sphdvr_render_batch(sphdvr_ctx* ctx, const sphdvr_dataset* ds, con
   return SPHDVR_OK;
 }
 
+sphdvr_status sphdvr_render_scatter(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+                                    const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
+                                    float* rgba_out, void* stream) {
+  if (!ctx) return SPHDVR_EINVAL;
+  if (!rgba_out) return set_err(ctx, SPHDVR_EINVAL, "render_scatter: rgba_out is NULL");
+  sphdvr_status s = check_common(ctx, ds, lut);
+  if (s != SPHDVR_OK) return s;
+  if ((s = check_opts(ctx, opts)) != SPHDVR_OK) return s;
+  RenderArgs a{};
+  a.ds = ds;
+  a.lut = &lut->d;
+  if ((s = check_camera(ctx, cam, &a.cam)) != SPHDVR_OK) return s;
+  std::vector<float4> tfh;
+  if ((s = pack_tf(ctx, tf, tfh)) != SPHDVR_OK) return s;
+  a.tf_n = tf->n;
+  a.tf_lo = (float)tf->lo;
+  a.tf_hi = (float)tf->hi;
+  a.tf_host = tfh.data();
+  a.opts = opts;
+  a.out = rgba_out;
+  ctx->frame_launch0 = ctx->launches;
+  const cudaStream_t st = (cudaStream_t)stream;
+  if ((s = render_scatter(ctx, a, st)) != SPHDVR_OK) return s;
+  ctx->last_stream = st;
+  ctx->stats_pending = true;
+  return SPHDVR_OK;
+}
+
 sphdvr_status sphdvr_render_host(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
                                  const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
                                  float* rgba_host, void* stream) {

@@ -487,6 +487,16 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
                          grid, smem, st);
 }
 
+sphdvr_status project_chunk_rects(sphdvr_ctx* ctx, const RenderArgs& a, float4* rect, unsigned* front, uint32_t* ntile,
+                                  cudaStream_t st) {
+  const int tiles_x = (a.cam.width + kTile - 1) / kTile, tiles_y = (a.cam.height + kTile - 1) / kTile;
+  const int nc = a.ds->n_chunks;
+  k_chunk_project<<<(nc + 255) / 256, 256, 0, st>>>(nc, a.ds->chunk_lo, a.ds->chunk_hi, a.cam, a.lut->q, a.lut->reach,
+                                                    tiles_x, tiles_y, rect, front, ntile);
+  ++ctx->launches;
+  return cuda_err(ctx, cudaGetLastError(), "k_chunk_project");
+}
+
 sphdvr_status render_frame_planned(sphdvr_ctx* ctx, const RenderArgs& a, const FrameWork& w, int grid, unsigned* ovf,
                                    cudaStream_t st) {
   const sphdvr_dataset* ds = a.ds;

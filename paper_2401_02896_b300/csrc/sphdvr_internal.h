@@ -194,6 +194,13 @@ sphdvr_status render_frame_sized(sphdvr_ctx* ctx, const RenderArgs& a, cudaStrea
 // pair buffers are sized by `sizer` for the pairs of all frames.
 sphdvr_status render_batch_sized(sphdvr_ctx* ctx, const RenderArgs* a, int n, cudaStream_t st, PairSizer sizer,
                                  void* user);
+// Pixel rectangles of the chunks (rect[c] = x0, y0, x1, y1: the ray of pixel
+// (px, py) can meet a particle of chunk c only if x0 - 0.5 <= px <= x1 + 0.5
+// and y0 - 0.5 <= py <= y1 + 0.5).
+sphdvr_status project_chunk_rects(sphdvr_ctx* ctx, const RenderArgs& a, float4* rect, unsigned* front, uint32_t* ntile,
+                                  cudaStream_t st);
+// The particle-centric pass order of Sec. 2 (scatter.cu).
+sphdvr_status render_scatter(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st);
 // Capacity-bound frame (no host synchronisation, allocation or host copy, so
 // it can be captured into a CUDA graph): bins into w's pair buffers of
 // w.pair_cap entries (pairs beyond are dropped and *ovf is set), sorts all

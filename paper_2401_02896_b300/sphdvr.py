@@ -93,6 +93,8 @@ def _load():
         "sphdvr_frame_plan_render": (ctypes.c_int, [vp, ctypes.POINTER(Camera), vp, vp]),
         "sphdvr_frame_plan_overflowed": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
         "sphdvr_frame_plan_destroy": (ctypes.c_int, [vp]),
+        "sphdvr_render_scatter": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
+                                                 ctypes.POINTER(RenderOpts), vp, vp]),
         "sphdvr_render_host": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                               ctypes.POINTER(RenderOpts), vp, vp]),
         "sphdvr_render_static_scratch": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
@@ -312,6 +314,14 @@ def sphdvr_render_batch(ctx, ds, lut, cameras, tf, opts, out_ptrs, stream=None, 
     st = _lib.sphdvr_render_batch(ctx, ds, lut, n, cams, ctypes.byref(t), ctypes.byref(o), outs,
                                   ctypes.c_void_p(stream) if stream else None)
     return _check(st, ctx, (EOVERFLOW,) if allow_overflow else ())
+
+
+def sphdvr_render_scatter(ctx, ds, lut, camera, tf, opts, out_ptr, stream=None):
+    """The paper's pass order: scatter knots per particle, sort per ray, accumulate and composite."""
+    c, t, o = camera_struct(camera), tf_struct(tf), opts_struct(opts)
+    st = _lib.sphdvr_render_scatter(ctx, ds, lut, ctypes.byref(c), ctypes.byref(t), ctypes.byref(o),
+                                    ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream) if stream else None)
+    return _check(st, ctx)
 
 
 def sphdvr_render_static_scratch(ctx, ds, lut, camera, tf, opts, out_ptr, stream=None):
