@@ -209,8 +209,8 @@ __global__ void __launch_bounds__(128) k_scatter_composite(ScatterParams sp) {
           const uint32_t vv = sp.vals[idx];
           const int i = (int)(vv >> 3), k = (int)(vv & 7u);
           const float4 P = p.pos[i];
-          Hit h;
-          hit_test(o, v, P, p.q, -INFINITY, h);
+          Hit h{0.0, 0.0};
+          hit_test(o, v, P, p.q, -INFINITY, h);  // passed in pass 1 with the same arithmetic
           const int j = min((int)floor(h.d / (double)P.w * (nl - 1) / (double)p.q + 0.5), nl - 1);
           const float2 th = __ldg(p.theta + j);
           t = h.tc + (double)knot_sigma(K, p.m, th, k) * (double)P.w;
@@ -363,7 +363,7 @@ sphdvr_status render_scatter(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t 
   p.stats = (unsigned long long*)ctx->stats.p;
   sp.rect = rect;
   sp.n_chunks = nc;
-  sp.cnt = (uint32_t*)ctx->dbg_counts.p;
+  sp.cnt = (uint32_t*)ctx->dbg_counts.p;  // (the parity hook's buffer, free outside its calls)
   sp.off = (uint32_t*)ctx->chunk_off.p;
   sp.total = (unsigned long long*)ctx->work.p;
   // pass 1a: knots per particle, then their offsets and the frame's total

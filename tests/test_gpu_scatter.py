@@ -27,12 +27,14 @@ def ctx(S):
     S.sphdvr_destroy(c)
 
 
-@pytest.mark.parametrize("case", ["cube_ortho", "halo_perspective"])
+@pytest.mark.parametrize("case", ["cube_ortho", "cube_odd_K", "halo_perspective"])
 def test_scatter_order_matches_oracle_and_gather(S, ctx, case):
     import torch
 
     if case == "cube_ortho":
         P, cam, lut, tf = SY.uniform_cube(), SY.ortho_camera_z(64, 64), oracle_lut("m4", 4, 3, 1025), SY.tf_bumps()
+    elif case == "cube_odd_K":
+        P, cam, lut, tf = SY.uniform_cube(), SY.orbit_camera(48, 40), oracle_lut("m4", 3, 2, 1025), SY.tf_bumps()
     else:
         P = SY.halo_mixture(60_000, seed=SY.BASE_SEED + 71)
         cam, lut, tf = SY.orbit_camera(96, 64, azimuth_deg=50.0), oracle_lut("wendland_c2", 4, 3, 1025), None
