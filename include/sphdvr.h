@@ -212,6 +212,21 @@ sphdvr_status sphdvr_lut_create(sphdvr_ctx* ctx, int kernel, int K, int D, int n
                                 const double* pieces, sphdvr_lut** out);
 sphdvr_status sphdvr_lut_free(sphdvr_lut* lut);
 
+/* Table files (the table is built once, offline, Sec. 3.1).  Layout, little
+ * endian: 8 bytes "SPHDVRLT", uint32 version 1, int32 kernel, K, D, n_lambda,
+ * int32 0, float64 q, then float64 theta[n_lambda][m], pieces[n_lambda][m][D+1] and
+ * err[n_lambda] in the layouts of sphdvr_lut_build (m = ceil(K/2)).
+ * sphdvr_lut_save writes one (err may be NULL: zeros); sphdvr_lut_read_header
+ * reads kernel, K, D and n_lambda; sphdvr_lut_read fills caller arrays of
+ * those sizes (err may be NULL); sphdvr_lut_load reads a file and makes it a
+ * device table as sphdvr_lut_create does.  ENOTFOUND if the file cannot be
+ * opened, EINVAL for a short or malformed file or bad arguments. */
+sphdvr_status sphdvr_lut_save(const char* path, int kernel, int K, int D, int n_lambda, const double* theta,
+                              const double* pieces, const double* err);
+sphdvr_status sphdvr_lut_read_header(const char* path, int* kernel, int* K, int* D, int* n_lambda);
+sphdvr_status sphdvr_lut_read(const char* path, double* theta, double* pieces, double* err);
+sphdvr_status sphdvr_lut_load(sphdvr_ctx* ctx, const char* path, sphdvr_lut** out);
+
 /* ---------------------------------------------------------------------------
  * Particle data sets, resident on the device.
  * ------------------------------------------------------------------------- */

@@ -232,6 +232,105 @@ sphdvr_status sphdvr_last_error(const sphdvr_ctx* c, char* buf, size_t len) {
   return SPHDVR_OK;
 }
 
+// ---- table files ---------------------------------------------------------
+namespace {
+struct LutFileHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t kernel, K, D, n_lambda;
+  int32_t reserved;  // 0
+  double q;
+};
+static_assert(sizeof(LutFileHeader) == 40, "table file header layout");
+constexpr char kLutMagic[8] = {'S', 'P', 'H', 'D', 'V', 'R', 'L', 'T'};
+
+bool lut_dims_ok(int kernel, int K, int D, int n_lambda) {
+  return kernel >= 0 && kernel <= 3 && K >= 1 && K <= 4 && D >= 1 && D <= 6 && n_lambda >= 2 && n_lambda <= 65536;
+}
+
+// open a table file and read and check its header; *f is left after the header
+sphdvr_status lut_open(const char* path, LutFileHeader& h, std::FILE** f) {
+  if (!path) return SPHDVR_EINVAL;
+  *f = std::fopen(path, "rb");
+  if (!*f) return SPHDVR_ENOTFOUND;
+  if (std::fread(&h, sizeof(h), 1, *f) != 1 || std::memcmp(h.magic, kLutMagic, 8) != 0 || h.version != 1 ||
+      !lut_dims_ok(h.kernel, h.K, h.D, h.n_lambda)) {
+    std::fclose(*f);
+    *f = nullptr;
+    return SPHDVR_EINVAL;
+  }
+  return SPHDVR_OK;
+}
+}  // namespace
+
+sphdvr_status sphdvr_lut_save(const char* path, int kernel, int K, int D, int n_lambda, const double* theta,
+                              const double* pieces, const double* err) {
+  if (!path || !theta || !pieces || !lut_dims_ok(kernel, K, D, n_lambda)) return SPHDVR_EINVAL;
+  const size_t n = (size_t)n_lambda, m = (size_t)(K + 1) / 2;
+  LutFileHeader h;
+  std::memcpy(h.magic, kLutMagic, 8);
+  h.version = 1;
+  h.kernel = kernel;
+  h.K = K;
+  h.D = D;
+  h.n_lambda = n_lambda;
+  h.reserved = 0;
+  h.q = kernel == 3 ? 1.0 : 2.0;
+  std::FILE* f = std::fopen(path, "wb");
+  if (!f) return SPHDVR_ENOTFOUND;
+  std::vector<double> zeros(err ? 0 : n, 0.0);
+  bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(theta, sizeof(double), n * m, f) == n * m &&
+            std::fwrite(pieces, sizeof(double), n * m * (D + 1), f) == n * m * (D + 1) &&
+            std::fwrite(err ? err : zeros.data(), sizeof(double), n, f) == n;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? SPHDVR_OK : SPHDVR_EINVAL;
+}
+
+sphdvr_status sphdvr_lut_read_header(const char* path, int* kernel, int* K, int* D, int* n_lambda) {
+  if (!kernel || !K || !D || !n_lambda) return SPHDVR_EINVAL;
+  LutFileHeader h;
+  std::FILE* f = nullptr;
+  sphdvr_status s = lut_open(path, h, &f);
+  if (s != SPHDVR_OK) return s;
+  std::fclose(f);
+  *kernel = h.kernel;
+  *K = h.K;
+  *D = h.D;
+  *n_lambda = h.n_lambda;
+  return SPHDVR_OK;
+}
+
+sphdvr_status sphdvr_lut_read(const char* path, double* theta, double* pieces, double* err) {
+  if (!theta || !pieces) return SPHDVR_EINVAL;
+  LutFileHeader h;
+  std::FILE* f = nullptr;
+  sphdvr_status s = lut_open(path, h, &f);
+  if (s != SPHDVR_OK) return s;
+  const size_t n = (size_t)h.n_lambda, m = (size_t)(h.K + 1) / 2, np = n * m * (h.D + 1);
+  std::vector<double> e(n);
+  bool ok = std::fread(theta, sizeof(double), n * m, f) == n * m && std::fread(pieces, sizeof(double), np, f) == np &&
+            std::fread(e.data(), sizeof(double), n, f) == n;
+  char extra;
+  ok = ok && std::fread(&extra, 1, 1, f) == 0;  // nothing after the table
+  std::fclose(f);
+  if (!ok) return SPHDVR_EINVAL;
+  if (err) std::memcpy(err, e.data(), n * sizeof(double));
+  return SPHDVR_OK;
+}
+
+sphdvr_status sphdvr_lut_load(sphdvr_ctx* ctx, const char* path, sphdvr_lut** out) {
+  if (!ctx || !out) return SPHDVR_EINVAL;
+  *out = nullptr;
+  int kernel, K, D, n;
+  sphdvr_status s = sphdvr_lut_read_header(path, &kernel, &K, &D, &n);
+  if (s != SPHDVR_OK) return set_err(ctx, s, "lut_load: cannot read the table file header");
+  const size_t m = (size_t)(K + 1) / 2;
+  std::vector<double> th((size_t)n * m), pc((size_t)n * m * (D + 1));
+  if ((s = sphdvr_lut_read(path, th.data(), pc.data(), nullptr)) != SPHDVR_OK)
+    return set_err(ctx, s, "lut_load: short or malformed table file");
+  return sphdvr_lut_create(ctx, kernel, K, D, n, th.data(), pc.data(), out);
+}
+
 sphdvr_status sphdvr_quant_error(int kernel, int D, double tau, double sigma, double* qe) {
   return quant_error_host(kernel, D, tau, sigma, qe) == 0 ? SPHDVR_OK : SPHDVR_EINVAL;
 }

@@ -80,6 +80,10 @@ def _load():
         "sphdvr_lut_build": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, vp, vp]),
         "sphdvr_lut_create": (ctypes.c_int, [vp] + [ctypes.c_int] * 4 + [vp, vp, ctypes.POINTER(vp)]),
         "sphdvr_lut_free": (ctypes.c_int, [vp]),
+        "sphdvr_lut_save": (ctypes.c_int, [ctypes.c_char_p] + [ctypes.c_int] * 4 + [vp, vp, vp]),
+        "sphdvr_lut_read_header": (ctypes.c_int, [ctypes.c_char_p] + [ctypes.POINTER(ctypes.c_int)] * 4),
+        "sphdvr_lut_read": (ctypes.c_int, [ctypes.c_char_p, vp, vp, vp]),
+        "sphdvr_lut_load": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.POINTER(vp)]),
         "sphdvr_dataset_create": (ctypes.c_int, [vp, ctypes.c_int64, vp, vp, vp, vp, vp, ctypes.c_int, vp,
                                                  ctypes.POINTER(vp)]),
         "sphdvr_dataset_free": (ctypes.c_int, [vp]),
@@ -258,6 +262,33 @@ def sphdvr_lut_create(ctx, kernel, K, D, n_lambda, theta, pieces):
     pc = np.ascontiguousarray(pieces, dtype=np.float64)
     h = ctypes.c_void_p()
     _check(_lib.sphdvr_lut_create(ctx, _kid(kernel), K, D, n_lambda, _p(th), _p(pc), ctypes.byref(h)), ctx)
+    return h
+
+
+def sphdvr_lut_save(path, kernel, K, D, n_lambda, theta, pieces, err=None):
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    pc = np.ascontiguousarray(pieces, dtype=np.float64)
+    e = np.ascontiguousarray(err, dtype=np.float64) if err is not None else None
+    _check(_lib.sphdvr_lut_save(os.fsencode(path), _kid(kernel), int(K), int(D), int(n_lambda), _p(th), _p(pc),
+                                _p(e) if e is not None else None))
+
+
+def sphdvr_lut_read(path):
+    """(kernel id, K, D, n_lambda, theta, pieces, err) of a table file."""
+    k, K, D, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib.sphdvr_lut_read_header(os.fsencode(path), ctypes.byref(k), ctypes.byref(K), ctypes.byref(D),
+                                       ctypes.byref(n)))
+    m = (K.value + 1) // 2
+    th = np.zeros((n.value, m))
+    pc = np.zeros((n.value, m, D.value + 1))
+    err = np.zeros(n.value)
+    _check(_lib.sphdvr_lut_read(os.fsencode(path), _p(th), _p(pc), _p(err)))
+    return k.value, K.value, D.value, n.value, th, pc, err
+
+
+def sphdvr_lut_load(ctx, path):
+    h = ctypes.c_void_p()
+    _check(_lib.sphdvr_lut_load(ctx, os.fsencode(path), ctypes.byref(h)), ctx)
     return h
 
 

@@ -170,3 +170,29 @@ def test_quant_functions_reject_bad_arguments():
         with pytest.raises(S.SphdvrError) as e:
             S.sphdvr_quant_params(*args)
         assert e.value.status == S.EINVAL
+
+
+def test_table_file_roundtrip_and_malformed_files(tmp_path):
+    """sphdvr_lut_save / sphdvr_lut_read give back the built table bit for bit; bad files are refused."""
+    th, pc, err = S.sphdvr_lut_build("m4", 3, 2, 33)
+    path = str(tmp_path / "m4_K3_D2.lut")
+    S.sphdvr_lut_save(path, "m4", 3, 2, 33, th, pc, err)
+    k, K, D, n, th2, pc2, err2 = S.sphdvr_lut_read(path)
+    assert (k, K, D, n) == (oracle.KERNELS["m4"], 3, 2, 33)
+    assert np.array_equal(th2, th) and np.array_equal(pc2, pc) and np.array_equal(err2, err)
+    raw = open(path, "rb").read()
+    assert len(raw) == 40 + 8 * (33 * 2 + 33 * 2 * 3 + 33)
+    cases = {"magic": b"X" + raw[1:], "short": raw[:-8], "trailing": raw + b"\0",
+             "bad_K": raw[:16] + (9).to_bytes(4, "little") + raw[20:]}
+    for name, data in cases.items():
+        bad = str(tmp_path / (name + ".lut"))
+        open(bad, "wb").write(data)
+        with pytest.raises(S.SphdvrError) as e:
+            S.sphdvr_lut_read(bad)
+        assert e.value.status == S.EINVAL, name
+    with pytest.raises(S.SphdvrError) as e:
+        S.sphdvr_lut_read(str(tmp_path / "missing.lut"))
+    assert e.value.status == S.ENOTFOUND
+    with pytest.raises(S.SphdvrError) as e:
+        S.sphdvr_lut_save(path, "m4", 9, 2, 33, th, pc, err)
+    assert e.value.status == S.EINVAL

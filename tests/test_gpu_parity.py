@@ -346,3 +346,28 @@ def test_reinitialisation_knots(S, ctx):
     finally:
         S.sphdvr_dataset_free(ds)
         S.sphdvr_lut_free(lt)
+
+
+def test_table_file_load_renders_like_create(S, ctx, tmp_path):
+    """A table saved to a file and loaded back (sphdvr_lut_load) renders the same image bit for bit."""
+    import torch
+
+    P = SY.uniform_cube()
+    lut = oracle_lut("m4", 4, 3, 1025)
+    path = str(tmp_path / "m4.lut")
+    S.sphdvr_lut_save(path, "m4", 4, 3, 1025, lut["theta"], lut["pieces"], lut["err"])
+    ds, lt = _mk(S, ctx, P, lut)
+    lt2 = S.sphdvr_lut_load(ctx, path)
+    cam = SY.orbit_camera(64, 48)
+    tf = SY.tf_bumps()
+    try:
+        a = torch.zeros((48, 64, 4), dtype=torch.float32, device="cuda")
+        b = torch.full_like(a, -1.0)
+        S.sphdvr_render(ctx, ds, lt, cam, tf, None, a.data_ptr())
+        S.sphdvr_render(ctx, ds, lt2, cam, tf, None, b.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.equal(a, b) and a[..., 3].max().item() > 0.05
+    finally:
+        S.sphdvr_lut_free(lt2)
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
