@@ -21,6 +21,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -240,7 +241,8 @@ def main():
     torch.cuda.synchronize()
     st0 = S.sphdvr_frame_stats(ctx)
     # ---- timed region: device time, CUDA events on the render stream
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+    # the clock samples of the timed region (directory: $SPHDVR_BENCH_LOG_DIR, else the temp directory)
+    clk_path = os.path.join(os.environ.get("SPHDVR_BENCH_LOG_DIR") or tempfile.gettempdir(),
                             "bench_clocks_r%d.csv" % rank)
     proc, fh = clocks_start(clk_path)
     time.sleep(0.5)
