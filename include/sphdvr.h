@@ -82,7 +82,7 @@ typedef enum {
    * quantisation error of Sec. 4.4 (sphdvr_quant_params gives quanta and
    * estimate).  quant_sigma must bound the field as Sec. 4.4 prescribes
    * (A_max / 2^63) so that every coefficient fits 64 bits; compositing is
-   * FP32 as in the other modes.  Not available in batched launches. */
+   * FP32 as in the other modes. */
   SPHDVR_PREC_INT64_QUANT = 4
 } sphdvr_precision;
 

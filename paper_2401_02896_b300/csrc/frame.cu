@@ -548,8 +548,6 @@ sphdvr_status render_batch_sized(sphdvr_ctx* ctx, const RenderArgs* a, int n, cu
                                  void* user) {
   if (n < 1 || n > SPHDVR_MAX_BATCH) return set_err(ctx, SPHDVR_EINVAL, "batch: frame count out of range");
   if (n == 1) return render_frame_sized(ctx, a[0], st, sizer, user);
-  if (a[0].opts && a[0].opts->precision == SPHDVR_PREC_INT64_QUANT)
-    return set_err(ctx, SPHDVR_EINVAL, "batch: the quantised path renders one frame per launch");
   const int grid = render_grid_batch(ctx, a, n);
   const int nc = a[0].ds->n_chunks;
   int64_t tiles = 0, rays = 0;
@@ -608,8 +606,8 @@ sphdvr_status render_batch_sized(sphdvr_ctx* ctx, const RenderArgs* a, int n, cu
   p.n_items = (int)items;
   const int prec = a[0].opts ? a[0].opts->precision : SPHDVR_PREC_FP32_ANCHORED;
   const size_t smem = render_smem_bytes(a[0].tf_n, kRenderWarps);
-  return dispatch_render(ctx, a[0].lut->D, prec == SPHDVR_PREC_FP64_NAIVE, false, true, false, p,
-                         std::min(grid, w.table_ctas), smem, st);
+  return dispatch_render(ctx, a[0].lut->D, prec == SPHDVR_PREC_FP64_NAIVE, false, true,
+                         prec == SPHDVR_PREC_INT64_QUANT, p, std::min(grid, w.table_ctas), smem, st);
 }
 
 }  // namespace sphdvr

@@ -34,6 +34,7 @@ sphdvr_status launch_render_d3(sphdvr_ctx* ctx, bool f64, bool dbg, bool batch, 
   const bool re = p.reinit_dt > 0.f;  // FP32 only
   if (qt) {  // quantised path: integer knots and coefficients, FP32 compositing
     if (dbg) return launch<float, 1, true, false, false, true>(ctx, p, grid, smem, st);
+    if (batch) return launch<float, kRenderWarps, false, false, true, true>(ctx, p, grid, smem, st);
     return launch<float, kRenderWarps, false, false, false, true>(ctx, p, grid, smem, st);
   }
   if (batch) {  // several frames, one work queue

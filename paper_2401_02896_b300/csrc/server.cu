@@ -173,9 +173,9 @@ bool same_launch(const Request* x, const Request* y) {
   if (std::memcmp(x->tf.data(), y->tf.data(), x->tf.size() * sizeof(float4)) != 0) return false;
   if (!x->has_opts) return true;
   const sphdvr_render_opts &a = x->opts, &b = y->opts;
-  if (a.precision == SPHDVR_PREC_INT64_QUANT) return false;  // one frame per launch
   return a.precision == b.precision && a.anchor_every == b.anchor_every && a.window_h == b.window_h &&
-         a.ert_eps == b.ert_eps && a.persistent == b.persistent && a.reinit_dt == b.reinit_dt;
+         a.ert_eps == b.ert_eps && a.persistent == b.persistent && a.reinit_dt == b.reinit_dt &&
+         a.quant_tau == b.quant_tau && a.quant_sigma == b.quant_sigma;
 }
 
 // Render the requests `rs` with one launch and complete them.
