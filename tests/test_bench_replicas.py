@@ -29,7 +29,7 @@ def _rank(rank, world, port, out):
 @pytest.mark.parametrize("world", [2, 3])
 def test_replica_rate_over_gloo(world):
     port = 29517 + world
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()  # no fork of this multi-threaded process
     mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
     t_slowest = 1000.0 + 500.0 * (world - 1)
     rays = sum(2_000_000 * (r + 1) for r in range(world))
