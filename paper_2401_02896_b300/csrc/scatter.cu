@@ -9,8 +9,9 @@
 // paper's own formulation and for comparison.
 //
 // Pass 1 runs one warp per chunk (a lane per particle) over the pixels of the
-// chunk's screen rectangle: the candidate test is the oracle's, in FP64
-// (distance from the ray below q h, far exit beyond t_near), and a hit emits
+// chunk's screen rectangle: a conservative FP32 distance test skips clear
+// misses, then the candidate test is the oracle's, in FP64 (distance from the
+// ray below q h, far exit beyond t_near), and a hit emits
 // the particle's K + 1 knots with the key (ray << 32 | ordered FP32 position).
 // Pass 3 runs one warp per ray over its knots, 32 at a time: each lane
 // rebuilds its knot's localized difference coefficients from the particle
@@ -51,6 +52,29 @@ __device__ __forceinline__ void pixel_ray(const DevCamera& c, int px, int py, do
     for (int i = 0; i < 3; ++i) {
       o[i] = c.eye[i] + sx * c.half_w * c.r[i] + sy * c.half_h * c.u[i];
       v[i] = c.f[i];
+    }
+  }
+}
+
+// FP32 ray of a pixel, for a conservative pre-test only
+__device__ __forceinline__ void pixel_ray_f(const DevCamera& c, int px, int py, float* o, float* v) {
+  const float sx = 2.f * (px + 0.5f) / c.width - 1.f, sy = 1.f - 2.f * (py + 0.5f) / c.height;
+  if (c.proj == 0) {
+    const float ax = sx * (float)(c.tan_half * c.aspect), ay = sy * (float)c.tan_half;
+    float n = 0.f;
+    for (int i = 0; i < 3; ++i) {
+      v[i] = (float)c.f[i] + ax * (float)c.r[i] + ay * (float)c.u[i];
+      n += v[i] * v[i];
+    }
+    n = rsqrtf(n);
+    for (int i = 0; i < 3; ++i) {
+      v[i] *= n;
+      o[i] = (float)c.eye[i];
+    }
+  } else {
+    for (int i = 0; i < 3; ++i) {
+      o[i] = (float)(c.eye[i] + sx * c.half_w * c.r[i] + sy * c.half_h * c.u[i]);
+      v[i] = (float)c.f[i];
     }
   }
 }
@@ -145,6 +169,16 @@ __global__ void k_scatter_knots(ScatterParams sp, int emit) {
   if (mine && x0 <= x1 && y0 <= y1) {
     for (int py = y0; py <= y1; ++py)
       for (int px = x0; px <= x1; ++px) {
+        {
+          // FP32 pre-test: the squared ray-centre distance with a margin far above
+          // its FP32 error (positions and distances of order 1 or below)
+          float of[3], vf[3];
+          pixel_ray_f(p.cam, px, py, of, vf);
+          const float a0 = P.x - of[0], a1 = P.y - of[1], a2 = P.z - of[2];
+          const float c0 = a1 * vf[2] - a2 * vf[1], c1 = a2 * vf[0] - a0 * vf[2], c2 = a0 * vf[1] - a1 * vf[0];
+          const float R = p.q * P.w, mg = 1e-4f * (1.f + fabsf(a0) + fabsf(a1) + fabsf(a2));
+          if (c0 * c0 + c1 * c1 + c2 * c2 > (R + mg) * (R + mg)) continue;
+        }
         double o[3], v[3];
         pixel_ray(p.cam, px, py, o, v);
         Hit h;
