@@ -204,6 +204,20 @@ sphdvr_status sphdvr_quant_error(int kernel, int D, double tau, double sigma, do
 sphdvr_status sphdvr_quant_params(int kernel, int D, int int_bits, double variance_ratio, double* tau_rel,
                                   double* sigma_rel, double* qe);
 
+/* Quantum values for a resident data set (Sec. 4.4's "short analysis of the
+ * data set"): a_max, a rigorous upper bound of |field| (every particle's peak
+ * |c| w(0), c = m v / (rho h^3), summed over the cells its support meets of a
+ * grid of cells about q times the median h wide (at most 128 per axis); the
+ * largest sum, plus 1 %), sigma = a_max / 2^(int_bits-1),
+ * and tau minimising Q_E for the representative particle (median h, median
+ * c), with that Q_E.  One tau serves every particle: particles far smaller
+ * than the median get coarse knots, and where h << tau the local
+ * coefficients may not fit int_bits (data with h over decades).  Copies the
+ * data set's particles to the host once (synchronising).  EINVAL on bad
+ * arguments or an empty data set. */
+sphdvr_status sphdvr_dataset_quant_params(sphdvr_ctx* ctx, const sphdvr_dataset* ds, int kernel, int D, int int_bits,
+                                          double* tau, double* sigma, double* qe, double* a_max);
+
 /* Upload a table (host arrays in the layout above, e.g. from
  * sphdvr_lut_build) to the context's device as FP32 knots, difference
  * coefficients (Sec. 2) and pieces.  The library keeps no reference to the

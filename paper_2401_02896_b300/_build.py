@@ -14,7 +14,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libsphdvr.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-CU = ["api.cu", "sort.cu", "dataset.cu", "frame.cu", "server.cu", "static_scratch.cu", "plan.cu", "scatter.cu"] + ["render_d%d.cu" % d for d in range(1, 7)]
+CU = ["api.cu", "sort.cu", "dataset.cu", "frame.cu", "server.cu", "static_scratch.cu", "plan.cu", "scatter.cu", "quanta.cu"] + ["render_d%d.cu" % d for d in range(1, 7)]
 CPP = ["lutgen.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -529,6 +529,8 @@ int quant_error_host(int kernel, int D, double tau, double sigma, double* qe) {
   return 0;
 }
 
+double kernel_peak_host(int kernel) { return (double)kernel_value(kernel, 0); }
+
 int quant_params_host(int kernel, int D, int int_bits, double ratio, double* tau, double* sigma, double* qe) {
   if (kernel < 0 || kernel > 3 || D < 0 || D > 16 || int_bits < 8 || int_bits > 1024 || !(ratio > 0) ||
       !std::isfinite(ratio) || !tau || !sigma || !qe)

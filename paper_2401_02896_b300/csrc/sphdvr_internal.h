@@ -19,6 +19,8 @@ int lut_error_measure_host(int kernel, int n_lambda, const double* err, double* 
 // for a bit length and data variance ratio.  Return 0 on success.
 int quant_error_host(int kernel, int D, double tau, double sigma, double* qe);
 int quant_params_host(int kernel, int D, int int_bits, double ratio, double* tau, double* sigma, double* qe);
+// w(0), the kernel's peak value
+double kernel_peak_host(int kernel);
 
 constexpr int kChunk = 32;       // particles per chunk of the acceleration structure
 constexpr int kTile = 16;        // binning tile edge in pixels

@@ -110,6 +110,8 @@ def _load():
         "sphdvr_quant_params": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]
                                 + [ctypes.POINTER(ctypes.c_double)] * 3),
         "sphdvr_frame_stats": (ctypes.c_int, [vp, i64p]),
+        "sphdvr_dataset_quant_params": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                                        + [ctypes.POINTER(ctypes.c_double)] * 4),
         "sphdvr_server_create": (ctypes.c_int, [vp, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]),
         "sphdvr_server_submit": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                                 ctypes.POINTER(RenderOpts), vp, ctypes.POINTER(ctypes.c_uint64)]),
@@ -317,6 +319,14 @@ def sphdvr_dataset_create(ctx, pos, h, mass=None, density=None, value=None, stre
 
 def sphdvr_dataset_free(ds):
     return _check(_lib.sphdvr_dataset_free(ds))
+
+
+def sphdvr_dataset_quant_params(ctx, ds, kernel, D, int_bits=64):
+    """dict(tau, sigma, qe, a_max): quantum values for a resident data set (Sec. 4.4)."""
+    v = [ctypes.c_double() for _ in range(4)]
+    _check(_lib.sphdvr_dataset_quant_params(ctx, ds, _kid(kernel), int(D), int(int_bits), *[ctypes.byref(x) for x in v]),
+           ctx)
+    return dict(zip(("tau", "sigma", "qe", "a_max"), (x.value for x in v)))
 
 
 def sphdvr_dataset_info(ds):

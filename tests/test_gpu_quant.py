@@ -174,3 +174,58 @@ def test_quantised_option_errors(S, ctx):
     finally:
         S.sphdvr_dataset_free(ds)
         S.sphdvr_lut_free(lt)
+
+
+def _field_max(P, lut, cam, pix):
+    import oracle
+
+    R = oracle.render(_parts(P), lut, cam, SY.tf_bumps(), np.asarray(pix, np.int32), field_cap=1 << 15)
+    fmax = 0.0
+    for r in range(len(pix)):
+        F = R["field"][r][: int(R["stats"][r, 5])]
+        if len(F):
+            ts = np.linspace(F[0, 0], F[-1, 1], 8001)
+            fmax = max(fmax, float(np.abs(oracle.field_eval(F, ts)).max()))
+    return fmax
+
+
+def test_dataset_quanta_bound_the_field_and_render_like_the_oracle(S, ctx):
+    """sphdvr_dataset_quant_params: a_max bounds the field (on uniform and halo data), sigma = a_max / 2^63,
+    tau is Q_E's minimiser for the median particle, and frames rendered with these quanta match the oracle's."""
+    import oracle
+
+    P = SY.uniform_cube()
+    lut = oracle_lut("m4", 4, 3, 1025)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.ortho_camera_z(32, 32)
+    tf = SY.tf_bumps()
+    pix = SY.pixel_sample(32, 32, 12, seed=64)
+    try:
+        qp = S.sphdvr_dataset_quant_params(ctx, ds, "m4", 3, 64)
+        fmax = _field_max(P, lut, cam, pix)
+        assert fmax <= qp["a_max"] <= 100 * fmax
+        assert abs(qp["sigma"] * 2.0 ** 63 / qp["a_max"] - 1) < 1e-12
+        # the representative particle: the upper medians (element n // 2 in order) of h and c
+        n = len(P["h"])
+        h_med = float(np.sort(P["h"].astype(np.float64))[n // 2])
+        amp = P["mass"].astype(np.float32) * P["value"].astype(np.float32) / P["density"].astype(np.float32)
+        c_med = float(np.sort(amp.astype(np.float64) / P["h"].astype(np.float64) ** 3)[n // 2])
+        t_rel, s_rel, qe = S.sphdvr_quant_params("m4", 3, 64, qp["a_max"] / (oracle.kernel_w("m4", 0.0) * c_med))
+        assert abs(qp["tau"] / (t_rel * h_med) - 1) < 1e-5 and abs(qp["qe"] / qe - 1) < 1e-5
+        opts = dict(precision="int64_quant", quant_tau=qp["tau"], quant_sigma=qp["sigma"], ert_eps=0.0)
+        g = S.sphdvr_debug_rays(ctx, ds, lt, cam, tf, opts, pix)
+        R = Q.quant_render(_parts(P), lut, cam, tf, pix, qp["tau"], qp["sigma"])
+        assert np.abs(g["rgba"] - R["rgba"]).max() <= PIXEL_ABS
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
+    P2 = SY.halo_mixture(60_000, seed=SY.BASE_SEED + 43)
+    lut2 = oracle_lut("wendland_c2", 4, 3, 1025)
+    ds2, lt2 = _mk(S, ctx, P2, lut2)
+    try:
+        qp2 = S.sphdvr_dataset_quant_params(ctx, ds2, "wendland_c2", 3, 64)
+        cam2 = SY.orbit_camera(64, 64)
+        assert _field_max(P2, lut2, cam2, SY.pixel_sample(64, 64, 16, seed=65)) <= qp2["a_max"]
+    finally:
+        S.sphdvr_dataset_free(ds2)
+        S.sphdvr_lut_free(lt2)
