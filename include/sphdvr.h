@@ -9,6 +9,9 @@
  * CUDA device pointers on the context's device; "host" pointers are ordinary
  * host memory (pinned memory makes the copies faster but is not required).
  * Calls on one context are not thread-safe; use one context per host thread.
+ * Frames rendered through one context share its work buffers: on one stream
+ * they are ordered; on different streams they must not overlap in time (use
+ * a context per stream, as the frame server's workers do).
  *
  * Method (paper sections):
  *   Sec. 1     SPH field f(x) = sum_i a_i / l_i^3 w(|x - chi_i| / l_i), with
