@@ -159,3 +159,15 @@ def test_server_without_batching(env, limits):
     for o, ref in zip(outs, refs):
         assert torch.equal(o, ref)
     assert bs["launches"] == len(cams) and bs["largest"] == 1
+
+
+def test_batch_with_degenerate_frames(env):
+    """A 1x1 frame and a frame that sees no particle, batched with an ordinary one."""
+    S, torch, ctx, lut, lt, P, ds, _, tf, _ = env
+    away = SY.orbit_camera(24, 16, distance=2.0)
+    away = dict(away, target=[2 * away["eye"][i] - 0.5 for i in range(3)])  # looking away from the data
+    cams = [SY.orbit_camera(1, 1), away, SY.orbit_camera(33, 17, azimuth_deg=123.0)]
+    ref = _single(S, torch, ctx, ds, lt, cams, tf, None)
+    for a, b in zip(_batch(S, torch, ctx, ds, lt, cams, tf, None), ref):
+        assert torch.equal(a, b)
+    assert float(ref[1].abs().max()) == 0.0

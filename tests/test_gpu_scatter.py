@@ -77,3 +77,30 @@ def test_scatter_argument_errors(S, ctx):
     finally:
         S.sphdvr_dataset_free(ds)
         S.sphdvr_lut_free(lt)
+
+
+def test_scatter_degenerate_frames(S, ctx):
+    """No particle in view: a transparent image; a 1x1 frame equals the gathering path's pixel."""
+    import torch
+
+    P = SY.uniform_cube()
+    lut = oracle_lut("m4", 4, 3, 1025)
+    ds = S.sphdvr_dataset_create(ctx, P["pos"], P["h"], P["mass"], P["density"], P["value"])
+    lt = S.sphdvr_lut_create(ctx, lut["kernel"], lut["K"], lut["D"], lut["n_lambda"], lut["theta"], lut["pieces"])
+    try:
+        away = SY.orbit_camera(16, 16)
+        away = dict(away, target=[2 * away["eye"][i] - 0.5 for i in range(3)])
+        o = torch.full((16, 16, 4), -1.0, dtype=torch.float32, device="cuda")
+        S.sphdvr_render_scatter(ctx, ds, lt, away, SY.tf_bumps(), None, o.data_ptr())
+        torch.cuda.synchronize()
+        assert float(o.abs().max()) == 0.0
+        one = SY.orbit_camera(1, 1)
+        a = torch.zeros((1, 1, 4), dtype=torch.float32, device="cuda")
+        b = torch.zeros_like(a)
+        S.sphdvr_render_scatter(ctx, ds, lt, one, SY.tf_bumps(), dict(ert_eps=0.0), a.data_ptr())
+        S.sphdvr_render(ctx, ds, lt, one, SY.tf_bumps(), dict(ert_eps=0.0), b.data_ptr())
+        torch.cuda.synchronize()
+        assert float((a - b).abs().max()) <= PIXEL_ABS
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
