@@ -153,10 +153,11 @@ def test_quantised_particle_tends_to_the_table_approximation(K, D):
     assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-5
 
 
-def test_ray_field_recurrence_equals_explicit_sums_and_tends_to_the_unquantised_field():
+@pytest.mark.parametrize("K,D,n_lambda", [(4, 3, 4096), (3, 2, 1025)])
+def test_ray_field_recurrence_equals_explicit_sums_and_tends_to_the_unquantised_field(K, D, n_lambda):
     P = SY.uniform_cube()
     parts = dict(pos=P["pos"], h=P["h"], amp=SY.particles_to_amp(P["mass"], P["value"], P["density"]))
-    lut = oracle_lut("m4", 4, 3, 4096)
+    lut = oracle_lut("m4", K, D, n_lambda)
     cam = SY.ortho_camera_z(32, 32)
     h_rep = float(np.median(P["h"]))
     pc_rep = float(np.median(parts["amp"] / P["h"].astype(np.float64) ** 3))
@@ -169,17 +170,17 @@ def test_ray_field_recurrence_equals_explicit_sums_and_tends_to_the_unquantised_
         fr = oracle.field_eval(ref, ts)
         prev = None
         for bits in (40, 64, 128):
-            tau_rel, sig_rel, qe = Q.quant_params("m4", 3, bits, 1e3)
+            tau_rel, sig_rel, qe = Q.quant_params("m4", D, bits, 1e3)
             tau, sigma = tau_rel * h_rep, sig_rel * pc_rep
             rows = Q.quant_ray_int(lut, cands, tau, sigma)
             if bits == 64:
                 # the recurrence over all knots of the ray gives the same integers at every interval start
                 kn = sorted((x for tc, h, c, j in cands for x in Q.quantise_particle(lut, j, tc, h, c, tau, sigma)),
                             key=lambda x: x[0])
-                rec = dict(_recurrence(kn, 3))
+                rec = dict(_recurrence(kn, D))
                 for a, b, A in rows:
                     assert rec[a] == A
-                assert _recurrence(kn, 3)[-1][1] == [0, 0, 0, 0]
+                assert _recurrence(kn, D)[-1][1] == [0] * (D + 1)
             F = Q.int_rows_to_field(rows, tau, sigma)
             err = np.sqrt(np.mean((oracle.field_eval(F, ts) - fr) ** 2) / np.mean(fr ** 2))
             assert err < 50 * qe + 1e-12
