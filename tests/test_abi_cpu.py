@@ -196,3 +196,16 @@ def test_table_file_roundtrip_and_malformed_files(tmp_path):
     with pytest.raises(S.SphdvrError) as e:
         S.sphdvr_lut_save(path, "m4", 9, 2, 33, th, pc, err)
     assert e.value.status == S.EINVAL
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/sphdvr.h is a C ABI: it compiles as pedantic C99 (and as C++)."""
+    import subprocess
+
+    src = tmp_path / "h.c"
+    src.write_text('#include "sphdvr.h"\nint main(void) { return SPHDVR_OK + SPHDVR_MAX_BATCH - 8; }\n')
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
+                   check=True)
+    subprocess.run(["g++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, "-x", "c++", str(src)],
+                   check=True)
