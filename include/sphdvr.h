@@ -380,7 +380,9 @@ sphdvr_status sphdvr_render_static_scratch(sphdvr_ctx* ctx, const sphdvr_dataset
  * stream): out[0] rays, [1] candidate particle-ray segments, [2] knots,
  * [3] windows, [4] chunk-tile pairs, [5] particle tests, [6] max table
  * occupancy, [7] flags (bit 0 table overflow, bit 1 window overflow, bit 3 a
- * knot arrived behind the processed part of its ray), [8] rays stopped
+ * knot arrived behind the processed part of its ray, bit 4 INT64_QUANT: a
+ * particle's rounded coefficient beyond 2^62, the quanta too fine for it),
+ * [8] rays stopped
  * by early termination, [9] device time of the render kernel in ns (CUDA
  * events on the render stream), [10] kernel launches of the frame,
  * [11] largest number of particles active at one point of a ray, [12] windows

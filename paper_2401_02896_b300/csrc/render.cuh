@@ -429,11 +429,14 @@ __device__ __forceinline__ u64 qknot_pos(const RenderParams& p, float4 E, float2
 // +-theta_s take [tau^d c s^_sd / (sigma h^d)], mirrored with (-1)^(d+1); the
 // odd orders of the middle knot (even K), resp. of the knots +-theta_1 (odd K,
 // in decreasing order), follow from exact shifted evenness about tbar_0.
+// Returns false if a rounded coefficient is beyond 2^62 (the quanta are too
+// fine for this particle: its integers may wrap).
 template <int D>
-__device__ __noinline__ void qknot_coef(const RenderParams& p, float4 E, float2 th, int j, int k, u64* out) {
+__device__ __noinline__ bool qknot_coef(const RenderParams& p, float4 E, float2 th, int j, int k, u64* out) {
   const int K = p.K, m = p.m;
   u64 fr[2][D + 1], off[2];
   const double r = p.q_tau / (double)E.z, f = (double)E.w / p.q_sigma;
+  bool ok = true;
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     off[s] = (u64)__double2ll_rn((double)E.z * (double)(s == 0 ? th.x : th.y) * p.q_inv_tau);
@@ -442,7 +445,9 @@ __device__ __noinline__ void qknot_coef(const RenderParams& p, float4 E, float2 
 #pragma unroll
     for (int d = 1; d <= D; ++d) {
       g *= r;
-      fr[s][d] = s < m ? (u64)__double2ll_rn(g * (double)__ldg(jr + d - 1)) : 0ull;
+      const double v = s < m ? g * (double)__ldg(jr + d - 1) : 0.0;
+      ok = ok && fabs(v) < 4.6116860184273879e18;  // 2^62
+      fr[s][d] = (u64)__double2ll_rn(v);
     }
     fr[s][0] = 0;
   }
@@ -485,6 +490,7 @@ __device__ __noinline__ void qknot_coef(const RenderParams& p, float4 E, float2 
   const int s = knot_slot(K, m, k, mir);
 #pragma unroll
   for (int d = 1; d <= D; ++d) out[d] = s == 0 ? mid[d] : (mir ? neg(s - 1, d) : fr[s - 1][d]);
+  return ok;
 }
 
 __device__ __forceinline__ int knots_done(const RayScratch& T, int e) { return (T.knc[e >> 3] >> (4 * (e & 7))) & 15; }
@@ -1324,7 +1330,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
               if (QT) {
                 const float2 th = __ldg(p.theta + T.jj[e]);
                 u64 qa[D + 1];
-                qknot_coef<D>(p, E, th, T.jj[e], k, qa);
+                if (!qknot_coef<D>(p, E, th, T.jj[e], k, qa)) st_flags |= 16;
 #pragma unroll
                 for (int d = 0; d < D; ++d) qd[(r * D + d) * 32 + lane] = qa[d + 1];
                 qt[r * 32 + lane] = qknot_pos(p, E, th, k);

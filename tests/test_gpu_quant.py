@@ -229,3 +229,28 @@ def test_dataset_quanta_bound_the_field_and_render_like_the_oracle(S, ctx):
     finally:
         S.sphdvr_dataset_free(ds2)
         S.sphdvr_lut_free(lt2)
+
+
+def test_quanta_too_fine_are_flagged(S, ctx):
+    """A value quantum far below the field's bound makes the particles' integers exceed 2^62: flag bit 4."""
+    import torch
+
+    P = SY.uniform_cube()
+    lut = oracle_lut("m4", 4, 3, 1025)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.ortho_camera_z(16, 16)
+    o = torch.zeros((16, 16, 4), dtype=torch.float32, device="cuda")
+    try:
+        qp = S.sphdvr_dataset_quant_params(ctx, ds, "m4", 3, 64)
+        S.sphdvr_render(ctx, ds, lt, cam, SY.tf_bumps(),
+                        dict(precision="int64_quant", quant_tau=qp["tau"], quant_sigma=qp["sigma"]), o.data_ptr())
+        torch.cuda.synchronize()
+        assert not S.sphdvr_frame_stats(ctx)["overflow"] & 16
+        S.sphdvr_render(ctx, ds, lt, cam, SY.tf_bumps(),
+                        dict(precision="int64_quant", quant_tau=qp["tau"], quant_sigma=qp["sigma"] * 1e-9),
+                        o.data_ptr(), allow_overflow=True)
+        torch.cuda.synchronize()
+        assert S.sphdvr_frame_stats(ctx)["overflow"] & 16
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
