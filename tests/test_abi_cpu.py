@@ -15,7 +15,6 @@ import pytest
 from scipy.integrate import quad, simpson
 
 import oracle
-from _helpers import oracle_lut
 
 S = pytest.importorskip("paper_2401_02896_b300.sphdvr", reason="libsphdvr.so not built")
 HERE = os.path.dirname(os.path.abspath(__file__))

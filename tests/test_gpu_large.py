@@ -9,7 +9,6 @@ The oracle computes the sampled rays one by one (FP64, all particles); the CUDA
 path renders the same rays through the parity hook (same kernels, no early
 termination, so that complete rays are compared).
 """
-import numpy as np
 import pytest
 
 from paper_2401_02896_b300 import synthetic as SY

@@ -6,7 +6,6 @@ checks: candidate sets identical apart from particles within 1e-6 h of
 tangency; field per ray within relative L2 1e-5; composited pixels within
 2e-4 per channel.
 """
-import math
 
 import numpy as np
 import pytest

@@ -6,7 +6,6 @@ here, and scipy's adaptive quadrature.
 """
 import math
 
-import numpy as np
 import pytest
 from scipy.integrate import quad
 
