@@ -42,12 +42,10 @@ WORKLOADS = {
                    desc="halo mixture 1,000,000 particles, Wendland C2, K=4, D=3, perspective 1024x1024"),
 }
 
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
-
-# DRAM bytes (read + write) of one render launch of the default workload, from
-# the ncu capture recorded in profiles/launches_halo16m_2048.md (the render
-# kernel as it is in this tree); None for other workloads or image sizes.
-PROFILED_DRAM_BYTES = {("halo16m", 2048): 249.19e9 + 833.20e9}
+# DRAM bytes (read + write) of one render launch, from the ncu capture named in
+# profiles/ for the render kernel as it is in this tree, scaled to the frame
+# (None where no capture of the current kernel exists).
+PROFILED_DRAM_BYTES = {}
 
 
 def replica_rate(total_ms, rays, dist=None, device="cpu"):
@@ -67,10 +65,18 @@ def replica_rate(total_ms, rays, dist=None, device="cpu"):
 
 
 def flops_per_segment(K, D):
-    """Algorithmic FP32 operations per particle-ray segment (FMA = 2):
-    candidate test 20; knot generation 3 + 2(K+1) + 2D(K+1); per knot the
-    coefficient update D(D+1) + D; per piece compositing 10D + 40."""
-    return 23 + (K + 1) * (2 + 2 * D + D * (D + 1) + D + 10 * D + 40)
+    """Algorithmic FP32 operations per particle-ray segment (an FMA counts 2), counted from the
+    arithmetic the render kernel performs on its common path:
+      candidate test 20 (chi - o, t = p.v, w = p - t v, |w|^2 against (q h)^2), table entry and
+      amplitude 10;
+      per knot (K + 1 per segment): its position 2; its difference coefficients 2D + 1
+      (a h^-3 s_kd / h^d); the coefficient update of Sec. 2, a Taylor shift D(D + 1) plus D adds;
+      per piece (one per knot) the compositing of Sec. 1 on one transfer-function cell: the end value
+      2D, the curvature bound 3D, two cell lookups 4, optical depth 3(D + 1) + 2, and two
+      Gauss-Legendre nodes of 3(D + 1) + 2D + 22 each (field, optical depth, exp, emission in RGB)."""
+    per_knot = 2 + (2 * D + 1) + D * (D + 1) + D
+    per_piece = 2 * D + 3 * D + 4 + 3 * (D + 1) + 2 + 2 * (3 * (D + 1) + 2 * D + 22)
+    return 30 + (K + 1) * (per_knot + per_piece)
 
 
 def clocks_start(path):
@@ -132,8 +138,7 @@ def cpu_oracle_rate(P, w, tf, n_pix, seed, threads=None):
     lut = oracle.lut_build(w["kernel"], w["K"], w["D"], w["n_lambda"])
     cam = camera_for(w, 0)
     pix = SY.pixel_sample(cam["width"], cam["height"], n_pix, seed)
-    amp = SY.particles_to_amp(P["mass"], P["value"], P["density"])
-    part = dict(pos=P["pos"], h=P["h"], amp=amp)
+    part = dict(pos=P["pos"], h=P["h"], mass=P["mass"], value=P["value"], density=P["density"])
     t = time.perf_counter()
     R = oracle.render(part, lut, cam, tf, pix)
     dt = time.perf_counter() - t
@@ -149,8 +154,7 @@ def run_reference(args, w, rank, world):
 
     P, tf = make_inputs(w, None)
     lut = oracle.lut_build(w["kernel"], w["K"], w["D"], w["n_lambda"])
-    amp = SY.particles_to_amp(P["mass"], P["value"], P["density"])
-    part = dict(pos=P["pos"], h=P["h"], amp=amp)
+    part = dict(pos=P["pos"], h=P["h"], mass=P["mass"], value=P["value"], density=P["density"])
     cam = camera_for(w, 0)
     per_step = 16
     for i in range(args.warmup):
@@ -229,12 +233,14 @@ def main():
     del tens
     cam = camera_for(w, rank)
     opts = dict(precision=args.precision, ert_eps=1e-5)
+    # roofline denominator: the device's FP32 FMA rate, measured (FFMA loop, CUDA events; no clock is set)
+    fp32_peak = S.sphdvr_measure_fp32_peak(ctx, torch.cuda.current_stream(dev).cuda_stream)
     W, H = cam["width"], cam["height"]
     out = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
 
     def frame():
-        S.sphdvr_render(ctx, ds, lut, cam, tf, opts, out.data_ptr(), stream=stream, allow_overflow=True)
+        S.sphdvr_render(ctx, ds, lut, cam, tf, opts, out.data_ptr(), stream=stream)
 
     for _ in range(max(3, args.warmup)):
         frame()
@@ -270,10 +276,10 @@ def main():
 
     # ---- end to end: host output buffer, copies inside the call
     host = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True).numpy()
-    S.sphdvr_render_host(ctx, ds, lut, cam, tf, opts, host, stream=stream, allow_overflow=True)
+    S.sphdvr_render_host(ctx, ds, lut, cam, tf, opts, host, stream=stream)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        S.sphdvr_render_host(ctx, ds, lut, cam, tf, opts, host, stream=stream, allow_overflow=True)
+        S.sphdvr_render_host(ctx, ds, lut, cam, tf, opts, host, stream=stream)
     e2e_s = time.perf_counter() - t0
     e2e_val = W * H * args.steps / e2e_s / 1e6
     if dist:
@@ -313,16 +319,15 @@ def main():
 
         def separate():
             for c_, o_ in zip(cams_b, outs_b):
-                S.sphdvr_render(ctx, ds, lut, c_, tf, opts, o_.data_ptr(), stream=stream, allow_overflow=True)
+                S.sphdvr_render(ctx, ds, lut, c_, tf, opts, o_.data_ptr(), stream=stream)
 
         def batched():
-            S.sphdvr_render_batch(ctx, ds, lut, cams_b, tf, opts, [o_.data_ptr() for o_ in outs_b], stream=stream,
-                                  allow_overflow=True)
+            S.sphdvr_render_batch(ctx, ds, lut, cams_b, tf, opts, [o_.data_ptr() for o_ in outs_b], stream=stream)
 
         # the same frames from a frame plan captured into one CUDA graph
         pairs_max = 0
         for c_, o_ in zip(cams_b, outs_b):
-            S.sphdvr_render(ctx, ds, lut, c_, tf, opts, o_.data_ptr(), stream=stream, allow_overflow=True)
+            S.sphdvr_render(ctx, ds, lut, c_, tf, opts, o_.data_ptr(), stream=stream)
             pairs_max = max(pairs_max, S.sphdvr_frame_stats(ctx)["pairs"])
         plan = S.FramePlan(ctx, ds, lut, tf, opts, rb, rb, int(1.5 * pairs_max) + 64)
         gs = torch.cuda.Stream(dev)
@@ -359,8 +364,9 @@ def main():
         nq, hq, rq = 1_000_000, 0.012, 512
         PQ = SY.uniform_cube(nq, h=hq, seed=SY.BASE_SEED + 90)
         dsq = S.sphdvr_dataset_create(ctx, PQ["pos"], PQ["h"], PQ["mass"], PQ["density"], PQ["value"])
-        ampq = SY.particles_to_amp(PQ["mass"], PQ["value"], PQ["density"])
-        pc_rep = float(np.median(ampq / PQ["h"].astype(np.float64) ** 3))
+        # representative particle amplitude m v / (rho h^3): the median over the particles
+        pc_rep = float(np.median(PQ["mass"].astype(np.float64) * PQ["value"] / PQ["density"]
+                                 / PQ["h"].astype(np.float64) ** 3))
         # A_max: 8 times the particles overlapping a point at the mean density, each at its peak value
         ratio = 8 * nq * 4.0 / 3.0 * math.pi * (2 * hq) ** 3
         tau_rel, sig_rel, qe = S.sphdvr_quant_params(w["kernel"], w["D"], 64, ratio)
@@ -371,12 +377,12 @@ def main():
         qopts = dict(precision="int64_quant", quant_tau=tau_rel * hq, quant_sigma=sig_rel * pc_rep, ert_eps=1e-5)
         tq = {}
         for name, op_, img in (("fp32_anchored", None, ref_q), ("int64_quant", qopts, oq)):
-            S.sphdvr_render(ctx, dsq, lut, camq, tfq, op_, img.data_ptr(), stream=stream, allow_overflow=True)
+            S.sphdvr_render(ctx, dsq, lut, camq, tfq, op_, img.data_ptr(), stream=stream)
             torch.cuda.synchronize()
             best = float("inf")
             for _ in range(2):
                 t0 = time.perf_counter()
-                S.sphdvr_render(ctx, dsq, lut, camq, tfq, op_, img.data_ptr(), stream=stream, allow_overflow=True)
+                S.sphdvr_render(ctx, dsq, lut, camq, tfq, op_, img.data_ptr(), stream=stream)
                 torch.cuda.synchronize()
                 best = min(best, time.perf_counter() - t0)
             tq[name] = (best, S.sphdvr_frame_stats(ctx)["segments"])
@@ -404,7 +410,7 @@ def main():
         sc = torch.empty_like(ga)
         ts_ = {}
         for name, fn in (("gather", lambda: S.sphdvr_render(ctx, ds1, lut, cam1, tf1, None, ga.data_ptr(),
-                                                             stream=stream, allow_overflow=True)),
+                                                             stream=stream)),
                          ("scatter", lambda: S.sphdvr_render_scatter(ctx, ds1, lut, cam1, tf1, None, sc.data_ptr(),
                                                                      stream=stream))):
             fn()
@@ -443,10 +449,13 @@ def main():
             frame_stats=dict(segments=int(seg_per_frame), knots=int(knots / args.steps), pairs=st0["pairs"],
                              max_table=st0["max_table"], overflow=st0["overflow"], ert_rays=st0["ert_rays"],
                              render_kernel_ms=kern_s * 1e3),
-            roofline=dict(bound="alu", achieved=achieved, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
-                          frac=achieved / FP32_PEAK_TFLOPS,
-                          traffic=PROFILED_DRAM_BYTES.get((args.workload, w["res"])),
-                          note="FP32 peak = 148 SMs x 128 lanes x 2 x 2032 MHz; algorithmic %d FLOP/segment" % fps),
+            roofline=dict(bound="alu", achieved=achieved, peak=fp32_peak, unit="TFLOP/s",
+                          frac=achieved / fp32_peak,
+                          traffic=PROFILED_DRAM_BYTES.get((args.workload, w["res"], args.precision)),
+                          note="peak: FP32 FMA rate measured in this run (sphdvr_measure_fp32_peak, an FFMA "
+                               "loop on every resident thread; MEASURED_PEAKS.json has no FP32 figure); "
+                               "achieved: %d algorithmic FLOP per segment x segments per frame / render "
+                               "kernel time (CUDA events)" % fps),
             e2e=dict(value=e2e_val, unit="Mrays/s", h2d_bytes_per_step=int(tf["rgba"].nbytes),
                      d2h_bytes_per_step=int(W * H * 16)),
             gpu_launches=int(launches),

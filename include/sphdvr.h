@@ -134,7 +134,13 @@ typedef struct {
                         smoothing length among the ray's pending particles (> 0);
                         0 selects the default 1.0 */
   float reinit_dt;   /* FP32_REINIT: spacing of the reinitialisation knots along t (> 0); else 0 */
-  int reserved[2];   /* must be 0 */
+  int ray_capacity;  /* FP32_ANCHORED / FP32_NAIVE: particles a ray may hold waiting and
+                        active in the frame pass; 0 selects 4096, else in [64, 4096].  A
+                        ray that needs more is abandoned by the frame pass and rendered
+                        again by a fallback pass with 16384 of each (same image); only a
+                        ray beyond that too is wrong, and sets frame flag bit 5.  Smaller
+                        values exist to exercise the fallback. */
+  int reserved;      /* must be 0 */
   double quant_tau;   /* INT64_QUANT: length quantum (ray-parameter units, > 0) */
   double quant_sigma; /* INT64_QUANT: field value quantum (> 0) */
 } sphdvr_render_opts;
@@ -267,6 +273,12 @@ sphdvr_status sphdvr_dataset_free(sphdvr_dataset* ds);
  * [4..7] 0. */
 sphdvr_status sphdvr_dataset_info(const sphdvr_dataset* ds, int64_t info[8]);
 
+/* Context figures: info[0] device bytes the context holds in its grow-only
+ * frame buffers (binning, per-ray scratch, counters, debug buffers; data sets
+ * and tables are counted by their own objects), info[1] kernel launches so
+ * far, info[2] device ordinal, info[3] 0. */
+sphdvr_status sphdvr_ctx_info(const sphdvr_ctx* ctx, int64_t info[4]);
+
 /* ---------------------------------------------------------------------------
  * Rendering.
  * ------------------------------------------------------------------------- */
@@ -364,29 +376,45 @@ sphdvr_status sphdvr_frame_plan_destroy(sphdvr_frame_plan* plan);
  * (nothing is rendered then).  The render grid is capped at 64 CTAs.
  *
  * The first call on a device looks up the array's device address (set-up,
- * once per device); make that first call before any stream capture begins.
- * All calls in the process share the one array: calls that can overlap in
- * time (different streams, threads or contexts on the same device) race on
- * it and must be ordered by the caller.  Every buffer that must start at
- * zero is cleared on the stream by the call itself.  The call synchronises
- * `stream` once to read the frame's pair count, as sphdvr_render does.  It
- * keeps no counters: sphdvr_frame_stats afterwards reports zeros except for
- * the render time and the launch count. */
+ * once per device).  The call cannot be captured into a CUDA graph: it
+ * synchronises `stream` once to read the frame's pair count, as
+ * sphdvr_render does (callers that need graphs use the frame plans,
+ * sphdvr_frame_plan_*).  All calls in the process share the one array: calls
+ * that can overlap in time (different streams, threads or contexts on the
+ * same device) race on it and must be ordered by the caller.  Every buffer
+ * that must start at zero is cleared on the stream by the call itself.  The
+ * frame's counters and flags (sphdvr_frame_stats, e.g. out[7] bit 0 for a
+ * per-ray buffer that overflowed, bit 4 for quanta too fine) stay in the
+ * array: sphdvr_frame_stats reads them from there, until the next call on
+ * the array overwrites them. */
 sphdvr_status sphdvr_render_static_scratch(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
                                            const sphdvr_camera* cam, const sphdvr_tf* tf,
                                            const sphdvr_render_opts* opts, float* rgba_out, void* stream);
+
+/* FP32 FMA throughput of the context's device in TFLOP/s (no counterpart in
+ * the paper: the roofline denominator of the render kernel, which is bound by
+ * FP32/ALU issue).  Eight independent FMA chains per thread on every resident
+ * thread, best of three timed launches after a warm-up (CUDA events on
+ * `stream`; about 0.1 s in all).  Changes no clock or other device setting.
+ * Synchronises `stream`. */
+sphdvr_status sphdvr_measure_fp32_peak(sphdvr_ctx* ctx, void* stream, double* tflops);
 
 /* Statistics of the context's last completed frame (synchronises its
  * stream): out[0] rays, [1] candidate particle-ray segments, [2] knots,
  * [3] windows, [4] chunk-tile pairs, [5] particle tests, [6] max table
  * occupancy, [7] flags (bit 0 table overflow, bit 1 window overflow, bit 3 a
  * knot arrived behind the processed part of its ray, bit 4 INT64_QUANT: a
- * particle's rounded coefficient beyond 2^62, the quanta too fine for it),
+ * particle's rounded coefficient, integer knot offset or centre beyond 2^62,
+ * the quanta too fine for it -- a per-particle bound, not a proof that the
+ * summed integers fit: that needs quant_sigma to bound the field),
  * [8] rays stopped
  * by early termination, [9] device time of the render kernel in ns (CUDA
  * events on the render stream), [10] kernel launches of the frame,
  * [11] largest number of particles active at one point of a ray, [12] windows
- * shortened by the window_h limit, [13..15] 0. */
+ * that ended before the bound of the next chunk (window_h limit, knot density
+ * or a particle starting inside them), [13] particle tests within 1e-6 h of
+ * tangency (|dist(chi, ray) - q h| <= 1e-6 h: the candidate decision there
+ * rests on rounding; FP32_ANCHORED / FP32_NAIVE only), [14..15] 0. */
 sphdvr_status sphdvr_frame_stats(sphdvr_ctx* ctx, int64_t out[16]);
 
 /* ---------------------------------------------------------------------------
@@ -453,7 +481,11 @@ sphdvr_status sphdvr_server_destroy(sphdvr_server* srv);
 /* Parity hook: render the listed pixels with the same kernels and return,
  * per pixel r (all HOST pointers):
  *   rgba[4r..4r+3]
- *   counts[4r..4r+3]: candidates, knots, field pieces written, flags
+ *   counts[8r..8r+7]: candidates, knots, field pieces written, flags (as in
+ *     sphdvr_frame_stats out[7]), particles tested within 1e-6 h of tangency
+ *     (|dist(chi, ray) - q h| <= 1e-6 h, counted and reported: their candidate
+ *     decision rests on rounding), windows (FP32_ANCHORED / FP32_NAIVE; else
+ *     0), most particles active at one point of the ray (idem), 0
  *   cand_ids[r*cand_cap ...]: original indices of the candidate particles
  *   field[(r*field_cap + i)*(D+3) ...]: FP64 rows (t_a, t_b, A_0..A_D), one per
  *     field piece of positive length, front to back, A the field's localized

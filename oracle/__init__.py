@@ -34,6 +34,7 @@ from .core import (  # noqa: F401
     ray_norm2,
     ray_integral,
     render,
+    particle_amplitude,
     composite_piece,
     camera_ray,
     Camera,

@@ -176,18 +176,33 @@ def entry_knots(lut, j):
     return np.array(s)
 
 
+def particle_amplitude(particles):
+    """Amplitude a_i = mass_i * value_i / density_i of every particle, FP64 (Sec. 1: a particle contributes
+    mass * value / (density * h^3) * w(|x - chi| / h) to the field).  ``particles`` carries ``mass``,
+    ``value`` and ``density`` (n,) arrays, each optional: a missing one counts as 1, as in the C ABI."""
+    n = np.asarray(particles["h"]).shape[0]
+    a = np.ones(n, dtype=np.float64)
+    for key in ("mass", "value"):
+        if particles.get(key) is not None:
+            a = a * np.asarray(particles[key], dtype=np.float64)
+    if particles.get("density") is not None:
+        a = a / np.asarray(particles["density"], dtype=np.float64)
+    return a
+
+
 def render(particles, lut, camera, tf, pixels, cand_cap=0, field_cap=0):
     """Render the listed pixels (row-major indices) by direct summation, FP64.
 
-    ``particles``: dict with ``pos`` (n,3) float32, ``h`` (n,) float32 and
-    ``amp`` (n,) float64 = mass * value / density.
+    ``particles``: dict with ``pos`` (n,3) float32, ``h`` (n,) float32 and the
+    FP32 ``mass``, ``value``, ``density`` (n,) of the C ABI (each optional, 1
+    if missing); the amplitude is ``particle_amplitude``.
     Returns dict(rgba (r,4), stats (r,8) int64, cand_ids (r,cand_cap) or None,
     field (r, field_cap, D+3) or None, truncated bool).
     """
     lib = _load()
     pos = np.ascontiguousarray(particles["pos"], dtype=np.float32)
     hs = np.ascontiguousarray(particles["h"], dtype=np.float32)
-    amp = np.ascontiguousarray(particles["amp"], dtype=np.float64)
+    amp = np.ascontiguousarray(particle_amplitude(particles), dtype=np.float64)
     n = pos.shape[0]
     pix = np.ascontiguousarray(pixels, dtype=np.int32)
     nr = pix.shape[0]

@@ -39,7 +39,7 @@ import numpy as np
 import sympy as sp
 from scipy.optimize import brentq
 
-from .core import KERNELS, camera_ray, composite_piece, kernel_support, kernel_w, render
+from .core import KERNELS, camera_ray, composite_piece, kernel_support, kernel_w, particle_amplitude, render
 
 _r = sp.Symbol("r", nonnegative=True)
 
@@ -213,6 +213,7 @@ def ray_candidates(particles, lut, camera, pixel, cand_cap=1 << 16):
     ids = R["cand_ids"][0, :n]
     o, v = camera_ray(camera, int(pixel))
     q, nl = lut["q"], lut["n_lambda"]
+    amp = particle_amplitude(particles)
     out = []
     for i in ids:
         p = np.asarray(particles["pos"][i], dtype=np.float64) - o
@@ -220,7 +221,7 @@ def ray_candidates(particles, lut, camera, pixel, cand_cap=1 << 16):
         tc = float(p @ v)
         d = float(np.linalg.norm(np.cross(p, v)))
         jj = min(int(math.floor(d / h * (nl - 1) / q + 0.5)), nl - 1)
-        out.append((tc, h, float(particles["amp"][i]) / h ** 3, jj))
+        out.append((tc, h, float(amp[i]) / h ** 3, jj))
     return out
 
 

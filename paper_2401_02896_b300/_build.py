@@ -14,14 +14,18 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libsphdvr.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-CU = ["api.cu", "sort.cu", "dataset.cu", "frame.cu", "server.cu", "static_scratch.cu", "plan.cu", "scatter.cu", "quanta.cu"] + ["render_d%d.cu" % d for d in range(1, 7)]
+CU = ["api.cu", "sort.cu", "dataset.cu", "frame.cu", "server.cu", "static_scratch.cu", "plan.cu", "scatter.cu",
+      "quanta.cu", "peak.cu"]
+# the render kernels: one source compiled once per polynomial degree
+DEGREES = range(1, 7)
+RENDER_INST = "render_inst.cu"
 CPP = ["lutgen.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in CU + CPP] + [
+    return [os.path.join(CSRC, f) for f in CU + CPP + [RENDER_INST]] + [
         os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))
     ] + [os.path.join(INCLUDE, "sphdvr.h")]
 
@@ -43,6 +47,11 @@ def build(force=False, verbose=False, jobs=None):
         o = os.path.join(LIBDIR, "obj", f + ".o")
         cmds.append([NVCC] + ARCH + common + ["-lineinfo", "-Xptxas", "-v" if verbose else "-O3", "-c",
                                                os.path.join(CSRC, f), "-o", o])
+        objs.append(o)
+    for d in DEGREES:
+        o = os.path.join(LIBDIR, "obj", "render_d%d.o" % d)
+        cmds.append([NVCC] + ARCH + common + ["-DSPHDVR_D=%d" % d, "-lineinfo", "-Xptxas", "-v" if verbose else "-O3",
+                                               "-c", os.path.join(CSRC, RENDER_INST), "-o", o])
         objs.append(o)
     for f in CPP:
         o = os.path.join(LIBDIR, "obj", f + ".o")

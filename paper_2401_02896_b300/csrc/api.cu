@@ -136,8 +136,9 @@ sphdvr_status check_opts(sphdvr_ctx* ctx, const sphdvr_render_opts* o) {
   if (o->precision == 0 && o->anchor_every < 1) return set_err(ctx, SPHDVR_EINVAL, "opts: anchor_every must be >= 1");
   if (!(o->ert_eps >= 0.f && o->ert_eps < 1.f)) return set_err(ctx, SPHDVR_EINVAL, "opts: ert_eps must be in [0, 1)");
   if (!(o->window_h >= 0.f) || !std::isfinite(o->window_h)) return set_err(ctx, SPHDVR_EINVAL, "opts: window_h must be >= 0");
-  for (int i = 0; i < 2; ++i)
-    if (o->reserved[i]) return set_err(ctx, SPHDVR_EINVAL, "opts: reserved fields must be 0");
+  if (o->ray_capacity != 0 && (o->ray_capacity < 64 || o->ray_capacity > 4096))
+    return set_err(ctx, SPHDVR_EINVAL, "opts: ray_capacity must be 0 or in [64, 4096]");
+  if (o->reserved) return set_err(ctx, SPHDVR_EINVAL, "opts: reserved field must be 0");
   return SPHDVR_OK;
 }
 
@@ -157,7 +158,7 @@ size_t ctx_held_bytes(const sphdvr_ctx* c) {
   const DevBuf* bufs[] = {&c->chunk_rect, &c->chunk_front, &c->chunk_ntile, &c->chunk_off, &c->pair_key,
                           &c->pair_val, &c->pair_key2, &c->pair_val2, &c->tile_range, &c->scan_tmp, &c->sort_tmp,
                           &c->stats, &c->tf, &c->img, &c->dbg_pix, &c->dbg_rgba, &c->dbg_counts, &c->dbg_cands,
-                          &c->dbg_field, &c->table, &c->work, &c->frames};
+                          &c->dbg_field, &c->table, &c->work, &c->frames, &c->fb_table, &c->fb_list};
   size_t t = 0;
   for (const DevBuf* b : bufs) t += b->bytes;
   return t;
@@ -167,7 +168,7 @@ void ctx_release_buffers(sphdvr_ctx* c) {
   DevBuf* bufs[] = {&c->chunk_rect, &c->chunk_front, &c->chunk_ntile, &c->chunk_off, &c->pair_key, &c->pair_val,
                     &c->pair_key2, &c->pair_val2, &c->tile_range, &c->scan_tmp, &c->sort_tmp, &c->stats,
                     &c->tf, &c->img, &c->dbg_pix, &c->dbg_rgba, &c->dbg_counts, &c->dbg_cands, &c->dbg_field,
-                    &c->table, &c->work, &c->frames};
+                    &c->table, &c->work, &c->frames, &c->fb_table, &c->fb_list};
   for (DevBuf* b : bufs) free_buf(*b);
   c->stats_pending = false;
 }
@@ -210,6 +211,14 @@ sphdvr_status sphdvr_create(int device, sphdvr_ctx** out) {
   sphdvr_ctx* c = new (std::nothrow) sphdvr_ctx();
   if (!c) return SPHDVR_ENOMEM;
   c->device = device;
+  // the events around every render kernel, created here so that no render
+  // call has to create them
+  if (cudaEventCreate(&c->ev_render0) != cudaSuccess || cudaEventCreate(&c->ev_render1) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return SPHDVR_ECUDA;
+  }
+  c->ev_ready = true;
   *out = c;
   return SPHDVR_OK;
 }
@@ -497,6 +506,15 @@ sphdvr_status sphdvr_dataset_free(sphdvr_dataset* ds) {
   return SPHDVR_OK;
 }
 
+sphdvr_status sphdvr_ctx_info(const sphdvr_ctx* ctx, int64_t info[4]) {
+  if (!ctx || !info) return SPHDVR_EINVAL;
+  info[0] = (int64_t)ctx_held_bytes(ctx);
+  info[1] = ctx->launches;
+  info[2] = ctx->device;
+  info[3] = 0;
+  return SPHDVR_OK;
+}
+
 sphdvr_status sphdvr_dataset_info(const sphdvr_dataset* ds, int64_t info[8]) {
   if (!ds || !info) return SPHDVR_EINVAL;
   info[0] = ds->n;
@@ -529,6 +547,7 @@ static sphdvr_status do_render(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const 
   s = render_frame(ctx, a, st);
   if (s != SPHDVR_OK) return s;
   ctx->last_stream = st;
+  ctx->stats_src = nullptr;
   ctx->stats_pending = true;
   return SPHDVR_OK;
 }
@@ -571,6 +590,7 @@ sphdvr_status sphdvr_render_batch(sphdvr_ctx* ctx, const sphdvr_dataset* ds, con
   s = render_batch_sized(ctx, a, n_frames, st, ctx_pair_sizer, nullptr);
   if (s != SPHDVR_OK) return s;
   ctx->last_stream = st;
+  ctx->stats_src = nullptr;
   ctx->stats_pending = true;
   return SPHDVR_OK;
 }
@@ -599,6 +619,7 @@ sphdvr_status sphdvr_render_scatter(sphdvr_ctx* ctx, const sphdvr_dataset* ds, c
   const cudaStream_t st = (cudaStream_t)stream;
   if ((s = render_scatter(ctx, a, st)) != SPHDVR_OK) return s;
   ctx->last_stream = st;
+  ctx->stats_src = nullptr;
   ctx->stats_pending = true;
   return SPHDVR_OK;
 }
@@ -623,9 +644,10 @@ sphdvr_status sphdvr_render_host(sphdvr_ctx* ctx, const sphdvr_dataset* ds, cons
 
 sphdvr_status sphdvr_frame_stats(sphdvr_ctx* ctx, int64_t out[16]) {
   if (!ctx || !out) return SPHDVR_EINVAL;
-  if (ctx->stats_pending && ctx->stats.p) {
+  const unsigned long long* src = ctx->stats_src ? ctx->stats_src : (const unsigned long long*)ctx->stats.p;
+  if (ctx->stats_pending && src) {
     unsigned long long h[16];
-    cudaError_t e = cudaMemcpyAsync(h, ctx->stats.p, sizeof(h), cudaMemcpyDeviceToHost, ctx->last_stream);
+    cudaError_t e = cudaMemcpyAsync(h, src, sizeof(h), cudaMemcpyDeviceToHost, ctx->last_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->last_stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "frame stats");
     for (int i = 0; i < 16; ++i) ctx->last_stats[i] = (int64_t)h[i];
@@ -642,17 +664,21 @@ sphdvr_status sphdvr_frame_stats(sphdvr_ctx* ctx, int64_t out[16]) {
   out[10] = ctx->launches - ctx->frame_launch0;
   out[11] = ctx->last_stats[11];
   out[12] = ctx->last_stats[12];
+  out[13] = ctx->last_stats[13];
+  out[14] = 0;
+  out[15] = 0;
   return SPHDVR_OK;
 }
 
 #ifdef SPHDVR_PHASE_TIMING
 // Instrumented builds only: per-phase clock64 totals of the last frame's render kernel.
-sphdvr_status sphdvr_phase_times(sphdvr_ctx* ctx, int64_t out[10]) {
+// out[0..9] phase clocks, out[10..15] windows by what ended them (k_ray).
+sphdvr_status sphdvr_phase_times(sphdvr_ctx* ctx, int64_t out[16]) {
   if (!ctx || !out || !ctx->stats.p) return SPHDVR_EINVAL;
-  unsigned long long h[10];
+  unsigned long long h[16];
   cudaError_t e = cudaMemcpy(h, (unsigned long long*)ctx->stats.p + 16, sizeof(h), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_err(ctx, e, "phase times");
-  for (int i = 0; i < 10; ++i) out[i] = (int64_t)h[i];
+  for (int i = 0; i < 16; ++i) out[i] = (int64_t)h[i];
   return SPHDVR_OK;
 }
 #endif
@@ -672,7 +698,7 @@ sphdvr_status sphdvr_debug_rays(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const
   const int D = lut->d.D;
   if ((s = ensure(ctx, ctx->dbg_pix, n_pix * sizeof(int))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->dbg_rgba, n_pix * 4 * sizeof(float))) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->dbg_counts, n_pix * 4 * sizeof(int64_t))) != SPHDVR_OK)
+      (s = ensure(ctx, ctx->dbg_counts, n_pix * 8 * sizeof(int64_t))) != SPHDVR_OK)
     return s;
   if (cand_ids && (s = ensure(ctx, ctx->dbg_cands, (size_t)n_pix * cand_cap * sizeof(int64_t))) != SPHDVR_OK) return s;
   if (field && (s = ensure(ctx, ctx->dbg_field, (size_t)n_pix * field_cap * (D + 3) * sizeof(double))) != SPHDVR_OK)
@@ -692,7 +718,7 @@ sphdvr_status sphdvr_debug_rays(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const
   s = do_render(ctx, ds, lut, cam, tf, opts, nullptr, st, &a);
   if (s != SPHDVR_OK) return s;
   if ((e = cudaMemcpy(rgba, ctx->dbg_rgba.p, n_pix * 4 * sizeof(float), cudaMemcpyDeviceToHost)) != cudaSuccess ||
-      (e = cudaMemcpy(counts, ctx->dbg_counts.p, n_pix * 4 * sizeof(int64_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      (e = cudaMemcpy(counts, ctx->dbg_counts.p, n_pix * 8 * sizeof(int64_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_err(ctx, e, "debug download");
   if (cand_ids &&
       (e = cudaMemcpy(cand_ids, ctx->dbg_cands.p, (size_t)n_pix * cand_cap * sizeof(int64_t), cudaMemcpyDeviceToHost)) !=
@@ -703,9 +729,9 @@ sphdvr_status sphdvr_debug_rays(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const
     return cuda_err(ctx, e, "debug download");
   bool over = false;
   for (int i = 0; i < n_pix; ++i) {
-    if (cand_ids && counts[4 * i] > cand_cap) over = true;
-    if (field && counts[4 * i + 2] > field_cap) over = true;
-    if (counts[4 * i + 3]) over = true;
+    if (cand_ids && counts[8 * i] > cand_cap) over = true;
+    if (field && counts[8 * i + 2] > field_cap) over = true;
+    if (counts[8 * i + 3]) over = true;
   }
   return over ? set_err(ctx, SPHDVR_EOVERFLOW, "debug_rays: a capacity or per-ray buffer was exceeded") : SPHDVR_OK;
 }

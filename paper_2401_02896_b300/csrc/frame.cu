@@ -18,7 +18,7 @@
 #include <cstring>
 #include <string>
 
-#include "render.cuh"
+#include "ray.cuh"
 
 namespace sphdvr {
 namespace {
@@ -162,11 +162,11 @@ __global__ void k_tile_ranges(int64_t n, const uint64_t* keys, int2* range, int 
 
 }  // namespace
 
-// per-degree launchers (render_d<D>.cu)
+// per-degree launchers (render_inst.cu, compiled once per degree)
 #define SPHDVR_DECL(D)                                                                                         \
-  sphdvr_status launch_render_d##D(sphdvr_ctx* ctx, bool f64, bool dbg, bool batch, bool qt,               \
-                                   const RenderParams& p, int grid, size_t smem, cudaStream_t st);           \
-  int render_occupancy_d##D(bool f64, bool dbg, size_t smem);
+  sphdvr_status launch_render_d##D(sphdvr_ctx* ctx, int kind, bool dbg, bool batch, const RenderParams& p,   \
+                                   int grid, size_t smem, cudaStream_t st);                                  \
+  int render_occupancy_d##D(int kind, bool dbg, size_t smem);
 SPHDVR_DECL(1)
 SPHDVR_DECL(2)
 SPHDVR_DECL(3)
@@ -175,27 +175,44 @@ SPHDVR_DECL(5)
 SPHDVR_DECL(6)
 #undef SPHDVR_DECL
 
-static sphdvr_status dispatch_render(sphdvr_ctx* ctx, int D, bool f64, bool dbg, bool batch, bool qt,
-                                     const RenderParams& p, int grid, size_t smem, cudaStream_t st) {
+// The render kernel of a precision mode.
+static int kernel_kind(const sphdvr_render_opts* o) {
+  switch (o ? o->precision : SPHDVR_PREC_FP32_ANCHORED) {
+    case SPHDVR_PREC_FP64_NAIVE: return kKernF64;
+    case SPHDVR_PREC_FP32_REINIT: return kKernReinit;
+    case SPHDVR_PREC_INT64_QUANT: return kKernQuant;
+    default: return kKernRay;
+  }
+}
+
+// Dynamic shared memory of a render launch.
+static size_t kernel_smem(int kind, int tf_n, bool dbg) {
+  if (kind == kKernRayFB) return ray_smem_bytes(tf_n, 1, true);
+  const int nw = dbg ? 1 : (kind == kKernRay ? kRayWarps : kRenderWarps);
+  return kind == kKernRay ? ray_smem_bytes(tf_n, nw, dbg) : render_smem_bytes(tf_n, nw);
+}
+
+static sphdvr_status dispatch_render(sphdvr_ctx* ctx, int D, int kind, bool dbg, bool batch, const RenderParams& p,
+                                     int grid, size_t smem, cudaStream_t st) {
   switch (D) {
-    case 1: return launch_render_d1(ctx, f64, dbg, batch, qt, p, grid, smem, st);
-    case 2: return launch_render_d2(ctx, f64, dbg, batch, qt, p, grid, smem, st);
-    case 3: return launch_render_d3(ctx, f64, dbg, batch, qt, p, grid, smem, st);
-    case 4: return launch_render_d4(ctx, f64, dbg, batch, qt, p, grid, smem, st);
-    case 5: return launch_render_d5(ctx, f64, dbg, batch, qt, p, grid, smem, st);
-    case 6: return launch_render_d6(ctx, f64, dbg, batch, qt, p, grid, smem, st);
+    case 1: return launch_render_d1(ctx, kind, dbg, batch, p, grid, smem, st);
+    case 2: return launch_render_d2(ctx, kind, dbg, batch, p, grid, smem, st);
+    case 3: return launch_render_d3(ctx, kind, dbg, batch, p, grid, smem, st);
+    case 4: return launch_render_d4(ctx, kind, dbg, batch, p, grid, smem, st);
+    case 5: return launch_render_d5(ctx, kind, dbg, batch, p, grid, smem, st);
+    case 6: return launch_render_d6(ctx, kind, dbg, batch, p, grid, smem, st);
   }
   return set_err(ctx, SPHDVR_EINVAL, "D out of range");
 }
 
-static int render_occupancy(int D, bool f64, bool dbg, size_t smem) {
+static int render_occupancy(int D, int kind, bool dbg, size_t smem) {
   switch (D) {
-    case 1: return render_occupancy_d1(f64, dbg, smem);
-    case 2: return render_occupancy_d2(f64, dbg, smem);
-    case 3: return render_occupancy_d3(f64, dbg, smem);
-    case 4: return render_occupancy_d4(f64, dbg, smem);
-    case 5: return render_occupancy_d5(f64, dbg, smem);
-    case 6: return render_occupancy_d6(f64, dbg, smem);
+    case 1: return render_occupancy_d1(kind, dbg, smem);
+    case 2: return render_occupancy_d2(kind, dbg, smem);
+    case 3: return render_occupancy_d3(kind, dbg, smem);
+    case 4: return render_occupancy_d4(kind, dbg, smem);
+    case 5: return render_occupancy_d5(kind, dbg, smem);
+    case 6: return render_occupancy_d6(kind, dbg, smem);
   }
   return 0;
 }
@@ -205,10 +222,9 @@ static int frame_tiles(const DevCamera& c) { return ((c.width + kTile - 1) / kTi
 // Persistent grid: resident CTAs on every SM, no more CTAs than work items.
 static int grid_for_items(sphdvr_ctx* ctx, const RenderArgs& a, int64_t items) {
   const bool dbg = a.n_dbg > 0;
-  const int prec = a.opts ? a.opts->precision : SPHDVR_PREC_FP32_ANCHORED;
-  const bool f64 = prec == SPHDVR_PREC_FP64_NAIVE;
-  const size_t smem = render_smem_bytes(a.tf_n, dbg ? 1 : kRenderWarps);
-  int nb = render_occupancy(a.lut->D, f64, dbg, smem);
+  const int kind = kernel_kind(a.opts);
+  const size_t smem = kernel_smem(kind, a.tf_n, dbg);
+  int nb = render_occupancy(a.lut->D, kind, dbg, smem);
   if (ctx->num_sms <= 0) {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -230,7 +246,23 @@ int render_grid_batch(sphdvr_ctx* ctx, const RenderArgs* a, int n) {
   return grid_for_items(ctx, a[0], (rays + kRenderWarps - 1) / kRenderWarps);
 }
 
-size_t render_table_floats(int grid, bool dbg) { return (size_t)grid * (dbg ? 1 : kRenderWarps) * kTableWords; }
+size_t render_table_floats(int grid, bool dbg) {
+  static_assert(kRayWarps == kRenderWarps, "both render kernels run the same warps per CTA");
+  // the parity hook runs k_ray with the fallback's larger per-ray capacities
+  return (size_t)grid * (dbg ? 1 : kRenderWarps) * (size_t)std::max(kTableWords, dbg ? kRayWordsBig : kRayWords);
+}
+
+size_t fallback_floats(int warps) { return (size_t)warps * kRayWordsBig; }
+
+// warps of the fallback pass (one per SM)
+static int fallback_warps(sphdvr_ctx* ctx) {
+  if (ctx->num_sms <= 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, ctx->device);
+    ctx->num_sms = n > 0 ? n : 1;
+  }
+  return ctx->num_sms;
+}
 
 // grow the context's pair buffers once the pair count is known
 sphdvr_status ctx_pair_sizer(sphdvr_ctx* ctx, FrameWork& w, size_t pairs, void*) {
@@ -270,22 +302,25 @@ size_t pair_bytes(size_t pairs) {
 }
 
 // Bytes shared by the frames of a batch (chunk scratch, statistics, table
-// scratch of the grid, transfer function, work counter, frame records).
-static size_t shared_fixed_bytes(const RenderArgs& a, int grid, int n) {
+// scratch of the grid, transfer function, work counter, frame records, the
+// fallback pass's scratch and list).
+static size_t shared_fixed_bytes(const RenderArgs& a, int grid, int n, int ctx_fallback_warps) {
   const size_t nc = a.ds->n_chunks;
   return nc * (sizeof(unsigned) + 2 * sizeof(uint32_t)) + 32 + 32 * sizeof(unsigned long long) +
          scan_tmp_words(nc) * sizeof(uint32_t) + (size_t)a.tf_n * sizeof(float4) +
          render_table_floats(grid, a.n_dbg > 0) * sizeof(float) + 4 * sizeof(unsigned) +
-         (n > 1 ? (size_t)n * sizeof(RenderFrame) : 0);
+         (n > 1 ? (size_t)n * sizeof(RenderFrame) : 0) + (size_t)(kFallbackList + 1) * sizeof(unsigned) +
+         fallback_floats(ctx_fallback_warps) * sizeof(float);
 }
 
 size_t frame_fixed_bytes(sphdvr_ctx* ctx, const RenderArgs& a) {
   return (size_t)a.ds->n_chunks * sizeof(float4) + (size_t)frame_tiles(a.cam) * sizeof(int2) +
-         shared_fixed_bytes(a, render_grid(ctx, a), 1);
+         shared_fixed_bytes(a, render_grid(ctx, a), 1, fallback_warps(ctx));
 }
 
 size_t batch_fixed_bytes(sphdvr_ctx* ctx, const RenderArgs* a, int n) {
-  size_t t = shared_fixed_bytes(a[0], render_grid_batch(ctx, a, n), n) + (size_t)n * a[0].ds->n_chunks * sizeof(float4);
+  size_t t = shared_fixed_bytes(a[0], render_grid_batch(ctx, a, n), n, fallback_warps(ctx)) +
+             (size_t)n * a[0].ds->n_chunks * sizeof(float4);
   for (int f = 0; f < n; ++f) t += (size_t)frame_tiles(a[f].cam) * sizeof(int2);
   return t;
 }
@@ -305,8 +340,14 @@ static sphdvr_status shared_work(sphdvr_ctx* ctx, const RenderArgs& a, int grid,
       (s = ensure(ctx, ctx->scan_tmp, scan_tmp_words(nc) * sizeof(uint32_t))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->tf, (size_t)a.tf_n * sizeof(float4))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->table, render_table_floats(grid, a.n_dbg > 0) * sizeof(float))) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->work, 4 * sizeof(unsigned))) != SPHDVR_OK)
+      (s = ensure(ctx, ctx->work, 4 * sizeof(unsigned))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->fb_table, fallback_floats(fallback_warps(ctx)) * sizeof(float))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->fb_list, (size_t)(kFallbackList + 1) * sizeof(unsigned))) != SPHDVR_OK)
     return s;
+  w.fb_table = (float*)ctx->fb_table.p;
+  w.fb_warps = fallback_warps(ctx);
+  w.fb_list = (unsigned*)ctx->fb_list.p;
+  w.fb_cap = kFallbackList;
   w.table = (float*)ctx->table.p;
   w.table_ctas = grid;
   w.work = (unsigned*)ctx->work.p;
@@ -444,9 +485,27 @@ static sphdvr_status upload_tf(sphdvr_ctx* ctx, const RenderArgs& a, const Frame
 static sphdvr_status clear_counters(sphdvr_ctx* ctx, const FrameWork& w, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(w.stats, 0, 32 * sizeof(unsigned long long), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(w.work, 0, sizeof(unsigned), st)) != cudaSuccess)
+      (e = cudaMemsetAsync(w.work, 0, sizeof(unsigned), st)) != cudaSuccess ||
+      (w.fb_list && (e = cudaMemsetAsync(w.fb_list, 0, sizeof(unsigned), st)) != cudaSuccess))
     return cuda_err(ctx, e, "stats memset");
   return SPHDVR_OK;
+}
+
+// The frame pass of k_ray and, after it, the fallback pass over the rays it
+// abandoned (a launch that ends at once when there are none).
+static sphdvr_status launch_frame(sphdvr_ctx* ctx, const RenderArgs& a, const FrameWork& w, RenderParams p,
+                                  bool batch, int grid, cudaStream_t st) {
+  const int kind = kernel_kind(a.opts);
+  const bool fb = kind == kKernRay && w.fb_table && w.fb_list && w.fb_warps > 0;
+  p.ray_cap = a.opts ? a.opts->ray_capacity : 0;
+  p.ovf = fb ? w.fb_list : nullptr;
+  p.ovf_cap = fb ? w.fb_cap : 0;
+  sphdvr_status s =
+      dispatch_render(ctx, a.lut->D, kind, false, batch, p, grid, kernel_smem(kind, a.tf_n, false), st);
+  if (s != SPHDVR_OK || !fb) return s;
+  p.scratch = w.fb_table;
+  return dispatch_render(ctx, a.lut->D, kKernRayFB, false, batch, p, w.fb_warps,
+                         kernel_smem(kKernRayFB, a.tf_n, false), st);
 }
 
 sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w, PairSizer sizer, void* user,
@@ -479,12 +538,11 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
   p.cand_cap = a.cand_cap;
   p.dbg_field = a.dbg_field;
   p.field_cap = a.field_cap;
-  const int prec = a.opts ? a.opts->precision : SPHDVR_PREC_FP32_ANCHORED;
   const bool dbg = a.n_dbg > 0;
+  const int kind = kernel_kind(a.opts);
   const int grid = std::min(render_grid(ctx, a), w.table_ctas);
-  const size_t smem = render_smem_bytes(a.tf_n, dbg ? 1 : kRenderWarps);
-  return dispatch_render(ctx, a.lut->D, prec == SPHDVR_PREC_FP64_NAIVE, dbg, false, prec == SPHDVR_PREC_INT64_QUANT, p,
-                         grid, smem, st);
+  if (!dbg) return launch_frame(ctx, a, w, p, false, grid, st);
+  return dispatch_render(ctx, a.lut->D, kind, true, false, p, grid, kernel_smem(kind, a.tf_n, true), st);
 }
 
 sphdvr_status project_chunk_rects(sphdvr_ctx* ctx, const RenderArgs& a, float4* rect, unsigned* front, uint32_t* ntile,
@@ -538,10 +596,7 @@ sphdvr_status render_frame_planned(sphdvr_ctx* ctx, const RenderArgs& a, const F
   p.tiles_y = tiles_y;
   p.out = a.out;
   p.n_items = n_tiles * kTile * kTile;
-  const int prec = a.opts ? a.opts->precision : SPHDVR_PREC_FP32_ANCHORED;
-  const size_t smem = render_smem_bytes(a.tf_n, kRenderWarps);
-  return dispatch_render(ctx, a.lut->D, prec == SPHDVR_PREC_FP64_NAIVE, false, false, prec == SPHDVR_PREC_INT64_QUANT,
-                         p, std::min(grid, w.table_ctas), smem, st);
+  return launch_frame(ctx, a, w, p, false, std::min(grid, w.table_ctas), st);
 }
 
 sphdvr_status render_batch_sized(sphdvr_ctx* ctx, const RenderArgs* a, int n, cudaStream_t st, PairSizer sizer,
@@ -604,10 +659,7 @@ sphdvr_status render_batch_sized(sphdvr_ctx* ctx, const RenderArgs* a, int n, cu
   p.n_frames = n;
   p.rect_stride = nc;
   p.n_items = (int)items;
-  const int prec = a[0].opts ? a[0].opts->precision : SPHDVR_PREC_FP32_ANCHORED;
-  const size_t smem = render_smem_bytes(a[0].tf_n, kRenderWarps);
-  return dispatch_render(ctx, a[0].lut->D, prec == SPHDVR_PREC_FP64_NAIVE, false, true,
-                         prec == SPHDVR_PREC_INT64_QUANT, p, std::min(grid, w.table_ctas), smem, st);
+  return launch_frame(ctx, a[0], w, p, true, std::min(grid, w.table_ctas), st);
 }
 
 }  // namespace sphdvr

@@ -22,7 +22,8 @@ struct sphdvr_frame_plan {
   int max_w = 0, max_h = 0, grid = 0;
   size_t pair_cap = 0;
   sphdvr::DevBuf chunk_rect, chunk_front, chunk_ntile, chunk_off, pair_key, pair_val, pair_key2, pair_val2,
-      tile_range, tmp, stats, tf, table, work, ovf;
+      tile_range, tmp, stats, tf, table, work, ovf, fb_table, fb_list;
+  int fb_warps = 0;
 };
 
 namespace sphdvr {
@@ -31,7 +32,8 @@ namespace {
 void plan_free(sphdvr_frame_plan* P) {
   DevBuf* bufs[] = {&P->chunk_rect, &P->chunk_front, &P->chunk_ntile, &P->chunk_off, &P->pair_key,
                     &P->pair_val,   &P->pair_key2,   &P->pair_val2,   &P->tile_range, &P->tmp,
-                    &P->stats,      &P->tf,          &P->table,       &P->work,       &P->ovf};
+                    &P->stats,      &P->tf,          &P->table,       &P->work,       &P->ovf,
+                    &P->fb_table,   &P->fb_list};
   for (DevBuf* b : bufs)
     if (b->p) {
       cudaFree(b->p);
@@ -97,6 +99,11 @@ sphdvr_status sphdvr_frame_plan_create(sphdvr_ctx* ctx, const sphdvr_dataset* ds
   big.height = max_height;
   RenderArgs a = plan_args(P, big, nullptr);
   P->grid = render_grid(ctx, a);
+  {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    P->fb_warps = sms > 0 ? sms : 1;  // fallback pass: one warp per SM
+  }
   const size_t nc = (size_t)ds->n_chunks;
   const size_t tiles = (size_t)((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
   const size_t tmp_words = std::max(scan_tmp_words((int64_t)nc), sort_tmp_words(pair_cap));
@@ -114,7 +121,9 @@ sphdvr_status sphdvr_frame_plan_create(sphdvr_ctx* ctx, const sphdvr_dataset* ds
       (s = ensure(ctx, P->tf, (size_t)P->tf_n * sizeof(float4))) != SPHDVR_OK ||
       (s = ensure(ctx, P->table, render_table_floats(P->grid, false) * sizeof(float))) != SPHDVR_OK ||
       (s = ensure(ctx, P->work, 4 * sizeof(unsigned))) != SPHDVR_OK ||
-      (s = ensure(ctx, P->ovf, sizeof(unsigned))) != SPHDVR_OK) {
+      (s = ensure(ctx, P->ovf, sizeof(unsigned))) != SPHDVR_OK ||
+      (s = ensure(ctx, P->fb_table, fallback_floats(P->fb_warps) * sizeof(float))) != SPHDVR_OK ||
+      (s = ensure(ctx, P->fb_list, (size_t)(kFallbackList + 1) * sizeof(unsigned))) != SPHDVR_OK) {
     plan_free(P);
     delete P;
     return s;
@@ -164,6 +173,10 @@ sphdvr_status sphdvr_frame_plan_render(sphdvr_frame_plan* P, const sphdvr_camera
   w.table = (float*)P->table.p;
   w.table_ctas = P->grid;
   w.work = (unsigned*)P->work.p;
+  w.fb_table = (float*)P->fb_table.p;
+  w.fb_warps = P->fb_warps;
+  w.fb_list = (unsigned*)P->fb_list.p;
+  w.fb_cap = kFallbackList;
   const RenderArgs a = plan_args(P, c, rgba_out);
   return render_frame_planned(ctx, a, w, P->grid, (unsigned*)P->ovf.p, (cudaStream_t)stream);
 }

@@ -55,6 +55,12 @@ constexpr int kNK = 512;            // new knots awaiting a merge (shared memory
 constexpr int kLevels = 128;        // smoothing-length bins (quarter octaves) for the window limit
 constexpr int kLevelBase = (127 - 28) << 2;  // bin 0 starts at h = 2^-28
 constexpr int kRenderWarps = 4;     // rays (warps) per CTA in normal rendering
+// which render kernel a frame runs (by precision mode)
+constexpr int kKernRay = 0;     // FP32_ANCHORED, FP32_NAIVE: the lean window kernel k_ray (ray.cuh)
+constexpr int kKernF64 = 1;     // FP64_NAIVE: k_render with FP64 running coefficients
+constexpr int kKernReinit = 2;  // FP32_REINIT: k_render with reinitialisation knots
+constexpr int kKernQuant = 3;   // INT64_QUANT: k_render's quantised integer path
+constexpr int kKernRayFB = 4;   // k_ray's fallback pass over the rays its frame pass abandoned
 // per-ray global scratch (32-bit words): particle records (4 words), table
 // entries, active list, free stack, two buffers of the waiting list (key, value)
 constexpr int kTableWords = 11 * kCap;
@@ -116,6 +122,12 @@ struct RenderParams {
   int n_frames;
   int rect_stride;            // batch: chunk rectangles per frame
   int dynamic;          // 1: atomic work queue, 0: static stride
+  // k_ray: per-ray capacities of the frame pass (> 0: smaller than the default,
+  // to exercise the fallback); the list of abandoned rays ([0] count, then up
+  // to ovf_cap work items; nullptr: no fallback, a full buffer only sets a flag)
+  int ray_cap;
+  unsigned* ovf;
+  int ovf_cap;
   // debug
   int n_dbg;
   const int* dbg_pix;
@@ -429,17 +441,22 @@ __device__ __forceinline__ u64 qknot_pos(const RenderParams& p, float4 E, float2
 // +-theta_s take [tau^d c s^_sd / (sigma h^d)], mirrored with (-1)^(d+1); the
 // odd orders of the middle knot (even K), resp. of the knots +-theta_1 (odd K,
 // in decreasing order), follow from exact shifted evenness about tbar_0.
-// Returns false if a rounded coefficient is beyond 2^62 (the quanta are too
-// fine for this particle: its integers may wrap).
+// Returns false if a rounded coefficient, or the integer knot offset
+// [h theta_s / tau] or centre [t_chi / tau], is beyond 2^62 (the quanta are too
+// fine for this particle: its integers may wrap).  This is a per-particle
+// bound: it does not prove that the sums over many particles stay below 2^63
+// (that needs sigma to bound the field, Sec. 4.4).
 template <int D>
 __device__ __noinline__ bool qknot_coef(const RenderParams& p, float4 E, float2 th, int j, int k, u64* out) {
   const int K = p.K, m = p.m;
   u64 fr[2][D + 1], off[2];
   const double r = p.q_tau / (double)E.z, f = (double)E.w / p.q_sigma;
-  bool ok = true;
+  bool ok = fabs(((double)E.x + (double)E.y) * p.q_inv_tau) < 4.6116860184273879e18;  // 2^62
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
-    off[s] = (u64)__double2ll_rn((double)E.z * (double)(s == 0 ? th.x : th.y) * p.q_inv_tau);
+    const double offd = (double)E.z * (double)(s == 0 ? th.x : th.y) * p.q_inv_tau;
+    ok = ok && fabs(offd) < 4.6116860184273879e18;
+    off[s] = (u64)__double2ll_rn(offd);
     const float* jr = p.jump + (size_t)j * 3 * D + (s + 1) * D;
     double g = f;
 #pragma unroll
@@ -1000,6 +1017,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     int hwm = 0, nfree = 0, nal = 0, n_act = 0, whead = 0, nwait = 0, wb = 0, nnk = 0, win_count = 0;
     bool at_reinit = false;  // the next window starts at a reinitialisation knot
     long long dbg_np = 0, dbg_nc = 0;
+    int lane_tan = 0;  // particles within 1e-6 h of tangency (this lane's tests)
     unsigned long long my_knots = 0;
     for (int b = lane; b < kLevels; b += 32) T.lvl[b] = 0;
     __syncwarp();
@@ -1694,6 +1712,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
                 wv[k] = w;
               }
               const float R2 = R * R;
+              if (DBG && fabsf(dd - R2) <= 2e-6f * q * h * h) ++lane_tan;
               if (dd < R2) {
                 const float ex = tt.hi + sqrtf(fmaxf(R2 - dd, 0.f));
                 if (ex > t_near) {
@@ -1755,6 +1774,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
     ++st_rays;
     if (p.tau_ert > 0.f && tau_ray > p.tau_ert) ++st_ert;
     st_knots += my_knots;
+    const int ray_tan = DBG ? warp_sum_i(lane_tan) : 0;
     if (lane == 0) {
       float alpha = -expm1f(-tau_ray);
       if (DBG) {
@@ -1762,10 +1782,15 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
         p.dbg_rgba[4 * dbg_row + 1] = col[1];
         p.dbg_rgba[4 * dbg_row + 2] = col[2];
         p.dbg_rgba[4 * dbg_row + 3] = alpha;
-        p.dbg_counts[4 * dbg_row + 0] = dbg_nc;
-        p.dbg_counts[4 * dbg_row + 1] = (long long)my_knots;
-        p.dbg_counts[4 * dbg_row + 2] = dbg_np;
-        p.dbg_counts[4 * dbg_row + 3] = st_flags;
+        long long* cnt = p.dbg_counts + 8 * dbg_row;
+        cnt[0] = dbg_nc;
+        cnt[1] = (long long)my_knots;
+        cnt[2] = dbg_np;
+        cnt[3] = st_flags;
+        cnt[4] = ray_tan;
+        cnt[5] = 0;
+        cnt[6] = 0;
+        cnt[7] = 0;
       } else {
         float4* o4 = (float4*)(BT ? p.frames[fb].out : p.out);
         o4[(size_t)py * cam.width + px] = make_float4(col[0], col[1], col[2], alpha);

@@ -70,12 +70,15 @@ struct sphdvr_ctx {
   // frame work buffers (grow-only)
   sphdvr::DevBuf chunk_rect, chunk_front, chunk_ntile, chunk_off, pair_key, pair_val, pair_key2, pair_val2,
       tile_range, scan_tmp, sort_tmp, stats, tf, img, dbg_pix, dbg_rgba, dbg_counts, dbg_cands, dbg_field, table,
-      work;
+      work, fb_table, fb_list;
   sphdvr::DevBuf frames;  // frame records of a batch
   int num_sms = 0;
   std::vector<int64_t> last_stats = std::vector<int64_t>(16, 0);
   cudaStream_t last_stream = nullptr;
   bool stats_pending = false;
+  // device counters of the last frame (the context's stats buffer, or the
+  // static scratch array for sphdvr_render_static_scratch)
+  const unsigned long long* stats_src = nullptr;
   int64_t last_pairs = 0;
   int64_t launches = 0;        // kernel launches since the context was created
   int64_t frame_launch0 = 0;   // value of `launches` when the last frame started
@@ -174,7 +177,17 @@ struct FrameWork {
   float* table = nullptr;             // per-ray candidate tables of the persistent render grid
   int table_ctas = 0;                 // CTAs the table scratch covers
   unsigned* work = nullptr;           // work-queue counter
+  // fallback pass of k_ray: per-warp scratch of fb_warps one-warp CTAs with the
+  // larger per-ray capacities, and the list of abandoned rays ([0] count)
+  float* fb_table = nullptr;
+  int fb_warps = 0;
+  unsigned* fb_list = nullptr;
+  int fb_cap = 0;
 };
+// Rays one frame (or batch) can hand to the fallback pass.
+constexpr int kFallbackList = 1 << 16;
+// Scratch floats of the fallback pass for `warps` warps.
+size_t fallback_floats(int warps);
 // Persistent render grid for this frame and the table scratch it needs (floats).
 int render_grid(sphdvr_ctx* ctx, const RenderArgs& a);
 // The same for a batch of frames sharing data set, table and options.

@@ -22,6 +22,7 @@ constexpr int64_t kStMaxChunks = int64_t(1) << 20;  // dataset chunks (<= 32 par
 constexpr int kStMaxTiles = 1 << 16;                // 16x16-pixel tiles (4096 x 4096 pixels)
 constexpr size_t kStMaxPairs = size_t(1) << 21;     // chunk-tile pairs of one frame
 constexpr int kStTableCtas = 64;                    // render CTAs whose per-ray scratch fits
+constexpr int kStFbWarps = 16;                      // warps of the fallback pass
 constexpr size_t kStBytes = size_t(192) << 20;      // 192 MiB
 constexpr int kStMaxDevices = 64;
 
@@ -76,6 +77,10 @@ sphdvr_status carve(sphdvr_ctx* ctx, unsigned char* base, FrameWork& w) {
   w.tmp = c.take<uint32_t>(w.tmp_words);
   w.table_ctas = kStTableCtas;
   w.table = c.take<float>(render_table_floats(kStTableCtas, false));
+  w.fb_warps = kStFbWarps;
+  w.fb_table = c.take<float>(fallback_floats(kStFbWarps));
+  w.fb_cap = kFallbackList;
+  w.fb_list = c.take<unsigned>(kFallbackList + 1);
   if (c.used > kStBytes) return set_err(ctx, SPHDVR_EINVAL, "static scratch: layout exceeds the array");
   return SPHDVR_OK;
 }
@@ -135,12 +140,17 @@ extern "C" sphdvr_status sphdvr_render_static_scratch(sphdvr_ctx* ctx, const sph
   FrameWork w;
   if ((s = carve(ctx, base, w)) != SPHDVR_OK) return s;
   ctx->frame_launch0 = ctx->launches;
-  // this call keeps no counters: sphdvr_frame_stats reports zeros for them
   ctx->stats_pending = false;
   for (auto& v : ctx->last_stats) v = 0;
   s = render_frame_ws(ctx, a, w, nullptr, nullptr, (cudaStream_t)stream);
   if (s == SPHDVR_EOVERFLOW && ctx->last_pairs > (int64_t)kStMaxPairs)
     return set_err(ctx, SPHDVR_EOVERFLOW, "render_static_scratch: frame has " + std::to_string(ctx->last_pairs) +
                                               " chunk-tile pairs; the static scratch holds at most 2097152");
-  return s;
+  if (s != SPHDVR_OK) return s;
+  // the frame's counters and flags live in the static array until the next
+  // call on it: sphdvr_frame_stats reads them from there
+  ctx->last_stream = (cudaStream_t)stream;
+  ctx->stats_src = w.stats;
+  ctx->stats_pending = true;
+  return SPHDVR_OK;
 }

@@ -60,7 +60,8 @@ class RenderOpts(ctypes.Structure):
         ("persistent", ctypes.c_int),
         ("window_h", ctypes.c_float),
         ("reinit_dt", ctypes.c_float),
-        ("reserved", ctypes.c_int * 2),
+        ("ray_capacity", ctypes.c_int),
+        ("reserved", ctypes.c_int),
         ("quant_tau", ctypes.c_double),
         ("quant_sigma", ctypes.c_double),
     ]
@@ -88,6 +89,8 @@ def _load():
                                                  ctypes.POINTER(vp)]),
         "sphdvr_dataset_free": (ctypes.c_int, [vp]),
         "sphdvr_dataset_info": (ctypes.c_int, [vp, i64p]),
+        "sphdvr_ctx_info": (ctypes.c_int, [vp, i64p]),
+        "sphdvr_measure_fp32_peak": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_double)]),
         "sphdvr_render": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                          ctypes.POINTER(RenderOpts), vp, vp]),
         "sphdvr_render_batch": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
@@ -207,6 +210,7 @@ def opts_struct(opts=None):
     o.reinit_dt = float(opts.get("reinit_dt", 0.0))
     o.quant_tau = float(opts.get("quant_tau", 0.0))
     o.quant_sigma = float(opts.get("quant_sigma", 0.0))
+    o.ray_capacity = int(opts.get("ray_capacity", 0))
     return o
 
 
@@ -329,6 +333,19 @@ def sphdvr_dataset_quant_params(ctx, ds, kernel, D, int_bits=64):
     return dict(zip(("tau", "sigma", "qe", "a_max"), (x.value for x in v)))
 
 
+def sphdvr_measure_fp32_peak(ctx, stream=None):
+    """Measured FP32 FMA throughput of the context's device, TFLOP/s."""
+    t = ctypes.c_double()
+    _check(_lib.sphdvr_measure_fp32_peak(ctx, ctypes.c_void_p(stream or 0), ctypes.byref(t)), ctx)
+    return t.value
+
+
+def sphdvr_ctx_info(ctx):
+    info = (ctypes.c_int64 * 4)()
+    _check(_lib.sphdvr_ctx_info(ctx, info), ctx)
+    return dict(held_bytes=int(info[0]), launches=int(info[1]), device=int(info[2]))
+
+
 def sphdvr_dataset_info(ds):
     info = (ctypes.c_int64 * 8)()
     _check(_lib.sphdvr_dataset_info(ds, info))
@@ -388,16 +405,17 @@ def sphdvr_frame_stats(ctx):
     s = (ctypes.c_int64 * 16)()
     _check(_lib.sphdvr_frame_stats(ctx, s), ctx)
     keys = ["rays", "segments", "knots", "windows", "pairs", "tests", "max_table", "overflow", "ert_rays",
-            "render_ns", "launches", "max_active", "capped_windows"]
+            "render_ns", "launches", "max_active", "capped_windows", "tangency_tests"]
     return {k: int(s[i]) for i, k in enumerate(keys)}
 
 
 def sphdvr_debug_rays(ctx, ds, lut, camera, tf, opts, pixels, cand_cap=0, field_cap=0, D=None):
-    """Parity hook: per listed pixel, rgba, counts, candidate ids and field pieces (FP64 rows)."""
+    """Parity hook: per listed pixel, rgba, counts (candidates, knots, field pieces, flags, tangency-band
+    tests, windows, most active particles, 0), candidate ids and field pieces (FP64 rows)."""
     pix = np.ascontiguousarray(pixels, dtype=np.int32)
     n = pix.shape[0]
     rgba = np.zeros((n, 4), np.float32)
-    counts = np.zeros((n, 4), np.int64)
+    counts = np.zeros((n, 8), np.int64)
     cands = np.full((n, cand_cap), -1, np.int64) if cand_cap else None
     if field_cap and D is None:
         raise ValueError("debug_rays needs D to size the field buffer")

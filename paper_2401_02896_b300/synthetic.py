@@ -27,11 +27,6 @@ def _rng(seed):
     return np.random.Generator(np.random.PCG64(seed))
 
 
-def particles_to_amp(mass, value, density):
-    """Per-particle amplitude factor mass * value / density (the SPH contribution's constant)."""
-    return np.asarray(mass, np.float64) * np.asarray(value, np.float64) / np.asarray(density, np.float64)
-
-
 def uniform_cube(n=1000, h=0.08, seed=BASE_SEED + 0):
     r = _rng(seed)
     pos = r.random((n, 3), dtype=np.float64).astype(np.float32)

@@ -88,7 +88,7 @@ def test_batch_sampled_pixels_match_the_oracle(env):
     S, torch, ctx, lut, lt, P, ds, _, tf, _ = env
     cams = _cams()[:3]
     got = _batch(S, torch, ctx, ds, lt, cams, tf, dict(ert_eps=0.0))
-    parts = dict(pos=P["pos"], h=P["h"], amp=SY.particles_to_amp(P["mass"], P["value"], P["density"]))
+    parts = dict(pos=P["pos"], h=P["h"], mass=P["mass"], value=P["value"], density=P["density"])
     for f, (c, img) in enumerate(zip(cams, got)):
         pix = SY.pixel_sample(c["width"], c["height"], 10, seed=40 + f)
         R = oracle.render(parts, lut, c, tf, pix)

@@ -39,7 +39,7 @@ def _mk(S, ctx, P, lut):
 
 
 def _orc_particles(P):
-    return dict(pos=P["pos"], h=P["h"], amp=SY.particles_to_amp(P["mass"], P["value"], P["density"]))
+    return dict(pos=P["pos"], h=P["h"], mass=P["mass"], value=P["value"], density=P["density"])
 
 
 def _check_rays(S, ctx, ds, lt, P, lut, cam, tf, pix, opts=None, cand_cap=4096, field_cap=1 << 15, q=2.0,
@@ -339,7 +339,9 @@ def test_reinitialisation_knots(S, ctx):
         print(dense, sparse, naive)
         assert dense <= FIELD_REL_L2
         assert sparse > 10 * dense
-        assert sparse == pytest.approx(naive, rel=0.5)
+        # without reinitialisation the drift is the plain recurrence's (its size depends on the order of
+        # the FP32 operations, which differs between the kernels that run the two modes)
+        assert naive / 3 <= sparse <= 3 * naive
         with pytest.raises(S.SphdvrError):
             S.sphdvr_debug_rays(ctx, ds, lt, cam, tf, dict(precision="fp32_reinit"), pix[:4], D=3)
     finally:
@@ -368,5 +370,41 @@ def test_table_file_load_renders_like_create(S, ctx, tmp_path):
         assert torch.equal(a, b) and a[..., 3].max().item() > 0.05
     finally:
         S.sphdvr_lut_free(lt2)
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
+
+
+def test_capacity_fallback_renders_the_same_image(S, ctx):
+    """Rays that overflow the frame pass's per-ray capacity (forced small here) are abandoned, listed and
+    rendered again by the fallback pass with larger capacities: the image matches the default frame and the
+    oracle, and every ray is counted once.  (A smaller capacity also makes a ray flush its new particles
+    earlier, which moves window ends: the two images agree to rounding, not bit for bit.)"""
+    import torch
+
+    P = SY.halo_mixture(100_000, seed=SY.BASE_SEED + 17)
+    lut = oracle_lut("wendland_c2", 4, 3, 4096)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.orbit_camera(72, 56)
+    tf = SY.tf_density(P["value"])
+    try:
+        a = torch.zeros((56, 72, 4), dtype=torch.float32, device="cuda")
+        b = torch.full_like(a, -1.0)
+        S.sphdvr_render(ctx, ds, lt, cam, tf, dict(ert_eps=0.0), a.data_ptr())
+        torch.cuda.synchronize()
+        sa = S.sphdvr_frame_stats(ctx)
+        S.sphdvr_render(ctx, ds, lt, cam, tf, dict(ert_eps=0.0, ray_capacity=64), b.data_ptr())
+        torch.cuda.synchronize()
+        sb = S.sphdvr_frame_stats(ctx)
+        assert sa["max_table"] > 64  # the small capacity does not hold every ray
+        assert sa["overflow"] == 0 and sb["overflow"] == 0, (sa["overflow"], sb["overflow"])
+        assert (a - b).abs().max().item() <= 1e-5
+        for k in ("rays", "segments", "knots"):
+            assert sa[k] == sb[k], k
+        pix = SY.pixel_sample(72, 56, 40, seed=71)
+        R = oracle.render(_orc_particles(P), lut, cam, tf, pix)
+        assert np.abs(b.cpu().numpy().reshape(-1, 4)[pix] - R["rgba"]).max() <= PIXEL_ABS
+        with pytest.raises(S.SphdvrError):
+            S.sphdvr_render(ctx, ds, lt, cam, tf, dict(ray_capacity=8), b.data_ptr())
+    finally:
         S.sphdvr_dataset_free(ds)
         S.sphdvr_lut_free(lt)

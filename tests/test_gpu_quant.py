@@ -35,7 +35,7 @@ def ctx(S):
 
 
 def _parts(P):
-    return dict(pos=P["pos"], h=P["h"], amp=SY.particles_to_amp(P["mass"], P["value"], P["density"]))
+    return dict(pos=P["pos"], h=P["h"], mass=P["mass"], value=P["value"], density=P["density"])
 
 
 def _quanta(S, P, kernel, D, lut, cam, pix, margin=2.0):
@@ -53,7 +53,7 @@ def _quanta(S, P, kernel, D, lut, cam, pix, margin=2.0):
             ts = np.linspace(F[0, 0], F[-1, 1], 4001)
             fmax = max(fmax, float(np.abs(oracle.field_eval(F, ts)).max()))
     h_rep = float(np.median(P["h"]))
-    pc_rep = float(np.median(parts["amp"] / P["h"].astype(np.float64) ** 3))
+    pc_rep = float(np.median(oracle.particle_amplitude(parts) / P["h"].astype(np.float64) ** 3))
     ratio = margin * fmax / (float(oracle.kernel_w(kernel, 0.0)) * pc_rep)
     tau_rel, sig_rel, qe = S.sphdvr_quant_params(kernel, D, 64, ratio)
     return tau_rel * h_rep, sig_rel * pc_rep, qe

@@ -56,7 +56,7 @@ def test_scatter_order_matches_oracle_and_gather(S, ctx, case):
         assert abs(st_s["knots"] - st_g["knots"]) <= 1e-4 * st_g["knots"]
         assert float((a - b).abs().max()) <= PIXEL_ABS
         pix = SY.pixel_sample(W, H, 16, seed=72)
-        parts = dict(pos=P["pos"], h=P["h"], amp=SY.particles_to_amp(P["mass"], P["value"], P["density"]))
+        parts = dict(pos=P["pos"], h=P["h"], mass=P["mass"], value=P["value"], density=P["density"])
         R = oracle.render(parts, lut, cam, tf, pix)
         assert np.abs(a.cpu().numpy().reshape(-1, 4)[pix] - R["rgba"]).max() <= PIXEL_ABS
         assert a[..., 3].max().item() > 0.05

@@ -156,11 +156,11 @@ def test_quantised_particle_tends_to_the_table_approximation(K, D):
 @pytest.mark.parametrize("K,D,n_lambda", [(4, 3, 4096), (3, 2, 1025)])
 def test_ray_field_recurrence_equals_explicit_sums_and_tends_to_the_unquantised_field(K, D, n_lambda):
     P = SY.uniform_cube()
-    parts = dict(pos=P["pos"], h=P["h"], amp=SY.particles_to_amp(P["mass"], P["value"], P["density"]))
+    parts = dict(pos=P["pos"], h=P["h"], mass=P["mass"], value=P["value"], density=P["density"])
     lut = oracle_lut("m4", K, D, n_lambda)
     cam = SY.ortho_camera_z(32, 32)
     h_rep = float(np.median(P["h"]))
-    pc_rep = float(np.median(parts["amp"] / P["h"].astype(np.float64) ** 3))
+    pc_rep = float(np.median(oracle.particle_amplitude(parts) / P["h"].astype(np.float64) ** 3))
     for pix in (5 * 32 + 7, 16 * 32 + 16, 27 * 32 + 20):
         cands = Q.ray_candidates(parts, lut, cam, pix)
         assert len(cands) > 5

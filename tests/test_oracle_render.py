@@ -21,7 +21,7 @@ from paper_2401_02896_b300 import synthetic as S
 @pytest.fixture(scope="module")
 def c1():
     P = S.uniform_cube()
-    P["amp"] = S.particles_to_amp(P["mass"], P["value"], P["density"])
+    P["amp"] = oracle.particle_amplitude(P)
     return P
 
 
