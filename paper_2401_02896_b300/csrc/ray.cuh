@@ -29,9 +29,23 @@
 
 namespace sphdvr {
 
-constexpr int kRayAS = 384;     // active particles held in shared memory (per warp)
-constexpr int kRayWarps = 4;    // warps (rays in flight) per CTA
-constexpr int kRayWcap = 448;   // knots composited per window (14 per lane)
+#ifndef SPHDVR_RAY_AS
+#define SPHDVR_RAY_AS 384
+#endif
+#ifndef SPHDVR_RAY_MINB
+#define SPHDVR_RAY_MINB 3
+#endif
+#ifndef SPHDVR_RAY_NK
+#define SPHDVR_RAY_NK 512
+#endif
+#ifndef SPHDVR_RAY_FILL
+#define SPHDVR_RAY_FILL 0.85f
+#endif
+constexpr int kRayAS = SPHDVR_RAY_AS;    // active particles held in shared memory (per warp)
+constexpr int kRayWarps = 4;             // warps (rays in flight) per CTA
+constexpr int kRayMinBlocks = SPHDVR_RAY_MINB;  // CTAs per SM the register budget is set for
+constexpr int kRayNK = SPHDVR_RAY_NK;    // window / new-particle buffer (knots)
+constexpr int kRayWcap = kRayNK - 64;  // knots composited per window
 
 // Per-ray capacities.  The frame pass holds up to 4096 waiting particles
 // (gathered, not started) and 4096 active ones per ray; a ray that needs more
@@ -43,9 +57,9 @@ struct RayCaps {
   static constexpr int WC = BIG ? 16384 : 4096;   // waiting slots
   static constexpr int ACT = BIG ? 16384 : 4096;  // active particles in all (beyond kRayAS in global memory)
   // per-warp shared memory: active records (t_chi hi, t_chi lo, h, c, j | done << 16),
-  // the window / new-particle buffers (two key/value pairs of kNK), the sort
+  // the window / new-particle buffers (two key/value pairs of kRayNK entries), the sort
   // histogram (+ scratch words), the started bits of the waiting slots
-  static constexpr int SMEM = kRayAS * 20 + 4 * kNK * 4 + (256 + 32) * 4 + (WC / 32) * 4;
+  static constexpr int SMEM = kRayAS * 20 + 4 * kRayNK * 4 + (256 + 32) * 4 + (WC / 32) * 4;
   // per-warp global scratch (32-bit words): slot records (float4), slot table
   // entries, free stack, slot -> active index map, two waiting-list buffers
   // (key, slot), the active extension (5 arrays)
@@ -53,6 +67,7 @@ struct RayCaps {
   static_assert(WORDS % 4 == 0, "per-warp scratch keeps float4 alignment");
 };
 static_assert(kRayAS % 32 == 0, "the shared part of the active set is a whole number of lane groups");
+static_assert(kRayNK >= 256 && kRayNK <= 512 && kRayNK % 32 == 0, "the window sort and merge take 256..512 entries");
 constexpr int kRayWords = RayCaps<false>::WORDS;     // per warp of the frame pass
 constexpr int kRayWordsBig = RayCaps<true>::WORDS;   // per warp of the fallback pass and the parity hook
 constexpr int kRayFlagRefit = 32;  // frame flag: a ray overflowed the fallback's capacities too (image wrong)
@@ -113,7 +128,7 @@ __device__ __forceinline__ int warp_excl_scan(int v, int* total) {
 // FB: the fallback pass -- its rays are those the frame pass listed in
 // p.ovf; it and the parity hook (DBG) hold the larger capacities.
 template <int D, int NW, bool DBG, bool BT, bool FB = false>
-__global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(RenderParams p) {
+__global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)) k_ray(RenderParams p) {
   constexpr bool BIG = DBG || FB;
   constexpr int WCX = RayCaps<BIG>::WC, ACTX = RayCaps<BIG>::ACT;
   // capacities in force (the frame pass may be given smaller ones, to test the fallback)
@@ -136,10 +151,10 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
     A.jk = (int*)(A.c + kRayAS);
     float* w = (float*)(A.jk + kRayAS);
     nk0 = w;
-    nv0 = (int*)(w + kNK);
-    nk1 = w + 2 * kNK;
-    nv1 = (int*)(w + 3 * kNK);
-    rh = (int*)(w + 4 * kNK);
+    nv0 = (int*)(w + kRayNK);
+    nk1 = w + 2 * kRayNK;
+    nv1 = (int*)(w + 3 * kRayNK);
+    rh = (int*)(w + 4 * kRayNK);
     stb = (unsigned*)(rh + 256 + 32);
     float* g = p.scratch + (size_t)(blockIdx.x * NW + wid) * RayCaps<BIG>::WORDS;
     s_rec = (float4*)g;
@@ -176,7 +191,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
   const float q = p.q, gam = p.window_h;
   const float kInf = __int_as_float(0x7f800000);
   // aim a window at this many knots from the knot density of the previous one
-  const float kTarget = 0.85f * (float)kRayWcap;
+  constexpr int kWcap = kRayWcap;
+  const float kTarget = SPHDVR_RAY_FILL * (float)kWcap;
 
   for (int it = 0;; ++it) {
     // ------------------------------------------------------------ work item
@@ -276,6 +292,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
     unsigned gmask = 0;
     float g_F = 0.f;
     const float oxh = o[0].hi, oyh = o[1].hi, ozh = o[2].hi, vxh = v[0].hi, vyh = v[1].hi, vzh = v[2].hi;
+    // reciprocal direction for the slab test (a zero component becomes a huge finite one of either sign)
+    const float ivx = 1.f / (fabsf(vxh) > 1e-30f ? vxh : 1e-30f), ivy = 1.f / (fabsf(vyh) > 1e-30f ? vyh : 1e-30f),
+                ivz = 1.f / (fabsf(vzh) > 1e-30f ? vzh : 1e-30f);
     // next chunk of the tile list at or after `from` that can reach this ray
     auto next_hit = [&](int from) -> int {
       for (;;) {
@@ -299,8 +318,19 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
               const float cx = lo.x + hx - oxh, cy = lo.y + hy - oyh, cz = lo.z + hz - ozh;
               const float t = cx * vxh + cy * vyh + cz * vzh;
               const float wx = cx - t * vxh, wy = cy - t * vyh, wz = cz - t * vzh;
-              const float rr = rad + 1e-5f * (fabsf(t) + fabsf(cx) + fabsf(cy) + fabsf(cz) + 1e-2f);
+              const float slack = 1e-5f * (fabsf(t) + fabsf(cx) + fabsf(cy) + fabsf(cz) + 1e-2f);
+              const float rr = rad + slack;
               hit = wx * wx + wy * wy + wz * wz <= rr * rr;
+              if (hit) {
+                // and the box grown by q h_max (plus the slack) must meet the ray's line
+                const float g = q * lo.w + slack;
+                const float ax = (lo.x - g - oxh) * ivx, bx = (hi.x + g - oxh) * ivx;
+                const float ay = (lo.y - g - oyh) * ivy, by = (hi.y + g - oyh) * ivy;
+                const float az = (lo.z - g - ozh) * ivz, bz = (hi.z + g - ozh) * ivz;
+                const float tmin = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fminf(az, bz));
+                const float tmax = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fmaxf(az, bz));
+                hit = tmin <= tmax + slack * (fabsf(tmax) + 1.f);
+              }
             }
           }
           gmask = __ballot_sync(kFull, hit);
@@ -320,7 +350,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
       const float F = last ? kInf : __shfl_sync(kFull, g_F, src & 31);
       if (done) break;  // abandoned (capacity): the fallback pass renders it
       const int room = nfree + (cap_wc - hwm);
-      if (last || nnk + 32 > kNK || room < 32) {
+      if (last || nnk + 32 > kRayNK || room < 32) {
         // ---- sort the new particles by first knot and merge them into the waiting list
         PT_BEGIN
         if (nnk > 0) {
@@ -484,7 +514,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
 #pragma unroll 1
               for (int r = 0; r < ne; ++r) {
                 const int pos = off + r;
-                if (pos < kNK) {
+                if (pos < kRayNK) {
                   nk0[pos] = fmaf(knot_sigma(K, m, th, kd + r), E.z, base);
                   nv0[pos] = (ni << 4) | (kd + r);
                 }
@@ -531,24 +561,24 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
 #pragma unroll 1
               for (int r = 0; r < ne; ++r) {
                 const int pos = off + r;
-                if (pos < kNK) {
+                if (pos < kRayNK) {
                   nk0[pos] = fmaf(knot_sigma(K, m, th, r), E.z, base);
                   nv0[pos] = (e << 4) | 8 | r;
                 }
               }
               T_all += tot;
             }
-            if (T_all <= kNK || gen >= 16) break;
+            if (T_all <= kRayNK || gen >= 16) break;
             // too many knots below U for the buffer: shrink U in proportion
-            // (to about kRayWcap of them at uniform density) and generate again
-            U *= 0.9f * (float)kRayWcap / (float)T_all;
+            // (to about the window capacity at uniform density) and generate again
+            U *= 0.9f * (float)kWcap / (float)T_all;
             capped = false;
             cap2 = kInf;
             __syncwarp();
           }
-          if (T_all > kNK) {
+          if (T_all > kRayNK) {
             rf |= 2;
-            T_all = kNK;
+            T_all = kRayNK;
           }
           PT_END(4)
           PT_BEGIN
@@ -567,9 +597,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
             WHY(3);
           }
           int nc = warp_count_below(GK, 0, T_all, U);
-          if (nc > kRayWcap) {  // full: it ends at the first knot left out
-            nc = kRayWcap;
-            U = GK[kRayWcap];
+          if (nc > kWcap) {  // full: it ends at the first knot left out
+            nc = kWcap;
+            U = GK[kWcap];
             capped = false;
             WHY(4);
           }
@@ -578,88 +608,21 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
             break;  // nothing final below F: wait for more particles
           }
 
-          // ---- the window's first and last knots, and where it ends
-          int nf = 0, nl = 0;
-          float umax = 0.f;
-#pragma unroll 1
-          for (int i = lane; i < nc; i += 32) {
-            const int k = GV[i] & 7;
-            nf += k == 0;
-            nl += k == K;
-            umax = fmaxf(umax, GK[i]);
-          }
-          nf = warp_sum_i(nf);
-          nl = warp_sum_i(nl);
-          umax = warp_max(umax);
-          const int act_after = n_act + nf - nl;
-          // no particle is active after the window's last knot: the field is
-          // identically zero from there on, so the window ends at that knot
-          const bool final_w = nc > 0 && act_after == 0;
-          float Uend = final_w ? fminf(umax, U) : U;
-          if (!(Uend < kInf)) {
-            rf |= 4;
-            Uend = umax;
-          }
-          Uend = fmaxf(Uend, 0.f);
-#ifdef SPHDVR_PHASE_TIMING
-          if (final_w && Uend < U) why = 5;
-          ++why_n[why];
-#endif
+          // (the knots are marked processed in the scan's first pass below: a
+          // starter whose first knot is in the window joins the active set there)
+          if (lane == 0) rh[256] = nal;  // next free index of the active set
+          __syncwarp();
           PT_END(5)
-          PT_BEGIN
-
-          // ---- mark the window's knots processed: starters whose first knot is
-          // in the window join the active set, then every other knot
-          // increments its particle's count
-#pragma unroll 1
-          for (int b0 = 0; b0 < nc; b0 += 32) {
-            const int i = b0 + lane;
-            const int vv = i < nc ? GV[i] : 0;
-            const bool sf = i < nc && (vv & 15) == 8;
-            const unsigned mm = __ballot_sync(kFull, sf);
-            if (sf) {
-              const int e = vv >> 4, ni = nal + __popc(mm & lanemask_lt());
-              const float4 E = s_rec[e];
-              if (ni < cap_act) {
-                act_put(A, ni, E, s_j[e] | (1 << 16));
-                s_map[e] = ni;
-              } else {
-                s_map[e] = -1;
-              }
-              hmin_new = fminf(hmin_new, E.z);
-              atomicOr(stb + (e >> 5), 1u << (e & 31));
-            }
-            nal += __popc(mm);
-          }
-          if (nal > cap_act) {
-            rf |= 1;
-            nal = cap_act;
-          }
-          __syncwarp();
-#pragma unroll 1
-          for (int i = lane; i < nc; i += 32) {
-            const int vv = GV[i];
-            if ((vv & 15) == 8) continue;
-            const int idx = (vv & 8) ? s_map[vv >> 4] : (vv >> 4);
-            if (idx >= 0) atomicAdd(act_jk_ptr(A, idx), 1 << 16);
-          }
-          __syncwarp();
-          n_act = act_after;
-          hmin = warp_min(hmin_new);
-          ray_maxact = max(ray_maxact, n_act);
-          my_knots += nc;
-          ++r_win;
-          ++win_count;
-          if (DBG) ++dbg_win;
-          if (capped) ++r_capped;
-          PT_END(6)
           PT_BEGIN
 
           // ---- segmented scan of the difference coefficients (Sec. 2) and
           // compositing; lane l takes the knots [i0, i1) of the window
+          // (balanced: the lanes' sequential loops below are the critical path)
           const int i0 = (lane * nc) >> 5, i1 = ((lane + 1) * nc) >> 5;
           const bool has = i1 > i0;
-          auto uat = [&](int i) -> float { return fminf(fmaxf(GK[i], 0.f), Uend); };
+          // every window knot lies below U (and below the window end), so only
+          // the start needs clamping
+          auto uat = [&](int i) -> float { return fmaxf(GK[i], 0.f); };
           // difference coefficients of window knot i (Sec. 2, Sec. 3.1)
           auto deltas = [&](int i, float* dl) {
             const int vv = GV[i];
@@ -682,13 +645,15 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
             }
             knot_delta<D>(p, j, h, c, k, dl);
           };
-          const float ufirst = has ? uat(i0) : Uend;
+          const float ufirst = has ? uat(i0) : 0.f;
           float P[D + 1];
+          float Uend;
           {
             float agg[D + 1];
 #pragma unroll
             for (int d = 0; d <= D; ++d) agg[d] = 0.f;
             float ulast = ufirst;
+            int nf = 0, nl = 0;  // the window's first and last knots of particles
 #pragma unroll 1
             for (int i = i0; i < i1; ++i) {
               const float ur = uat(i);
@@ -698,7 +663,60 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
 #pragma unroll
               for (int d = 1; d <= D; ++d) agg[d] += dl[d - 1];
               ulast = ur;
+              // mark the knot processed: a starter's first knot brings the
+              // particle into the active set (its later knots in this window
+              // are counted in the second pass, once every starter is in);
+              // an active particle's knot increments its count
+              const int vv = GV[i], k = vv & 7;
+              nf += k == 0;
+              nl += k == K;
+              if ((vv & 15) == 8) {
+                const int e = vv >> 4;
+                const int ni = atomicAdd(rh + 256, 1);
+                const float4 E = s_rec[e];
+                if (ni < cap_act) {
+                  act_put(A, ni, E, s_j[e] | (1 << 16));
+                  s_map[e] = ni;
+                } else {
+                  s_map[e] = -1;
+                }
+                hmin_new = fminf(hmin_new, E.z);
+                atomicOr(stb + (e >> 5), 1u << (e & 31));
+              } else if (!(vv & 8)) {
+                atomicAdd(act_jk_ptr(A, vv >> 4), 1 << 16);
+              }
             }
+            nf = warp_sum_i(nf);
+            nl = warp_sum_i(nl);
+            const int act_after = n_act + nf - nl;
+            // no particle is active after the window's last knot: the field is
+            // identically zero from there on, so the window ends at that knot
+            const float umax = nc > 0 ? GK[nc - 1] : 0.f;
+            const bool final_w = nc > 0 && act_after == 0;
+            Uend = final_w ? fminf(umax, U) : U;
+            if (!(Uend < kInf)) {
+              rf |= 4;
+              Uend = umax;
+            }
+            Uend = fmaxf(Uend, 0.f);
+#ifdef SPHDVR_PHASE_TIMING
+            if (final_w && Uend < U) why = 5;
+            ++why_n[why];
+#endif
+            __syncwarp();
+            nal = rh[256];
+            if (nal > cap_act) {
+              rf |= 1;
+              nal = cap_act;
+            }
+            n_act = act_after;
+            hmin = warp_min(hmin_new);
+            ray_maxact = max(ray_maxact, n_act);
+            my_knots += nc;
+            ++r_win;
+            ++win_count;
+            if (DBG) ++dbg_win;
+            if (capped) ++r_capped;
             // inclusive warp scan of (agg, ulast, has):
             // (other, oe) (+) (mine, se) = (Shift(other, se - oe) + mine, se)
             float sa[D + 1];
@@ -747,7 +765,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
           // ---- composite: lane 0 first takes the leading piece [0, u_0] of the
           // window (all of it if the window has no knot) with the incoming
           // polynomial, then every lane one piece per knot
-          Acc acc_l{0.f, 0.f, 0.f, 0.f};
+          float tau_l = 0.f, col_l[3] = {0.f, 0.f, 0.f};  // this lane's optical depth and colour
           const df rs = df_add(t_start, df_neg(Ta));
           const float ystart = rs.hi + rs.lo;  // window-relative start of compositing
           long long dbg_base = 0, npieces = 0;
@@ -770,49 +788,51 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
             dbg_base = dbg_np + (xx - tot) + lead;
             npieces = __shfl_sync(kFull, xx, 31);
           }
-          if (lane == 0) {
-            const float ub = nc > 0 ? uat(0) : Uend;
-            const float a0 = fmaxf(0.f, ystart);
-            if (ub > a0) {
-              Poly<D> Pf;
-#pragma unroll
-              for (int d = 0; d <= D; ++d) Pf.c[d] = Aw[d];
-              if (a0 > 0.f) taylor_shift<D, float>(Pf.c, a0);
-              acc_l = composite_piece_v<D>(Pf, ub - a0, tfc, acc_l);
-            }
-            if (DBG && p.dbg_field && ub > 0.f && dbg_np < p.field_cap) {
-              double* fo = p.dbg_field + ((size_t)dbg_row * p.field_cap + dbg_np) * (D + 3);
-              fo[0] = df_to_double(Ta);
-              fo[1] = df_to_double(Ta) + (double)ub;
-              for (int d = 0; d <= D; ++d) fo[2 + d] = (double)Aw[d];
-            }
-          }
           float lastu = ufirst;
+          // lane 0's first iteration (i = -1) is the leading piece [0, u_0] of
+          // the window with the incoming polynomial; the compositing code is
+          // inlined once, here (a call would save the live registers to local
+          // memory around every piece)
 #pragma unroll 1
-          for (int i = i0; i < i1; ++i) {
-            const float ua = uat(i);
-            if (i > i0) taylor_shift<D, float>(P, ua - lastu);
-            float dl[D];
-            deltas(i, dl);
+          for (int i = (lane == 0 ? -1 : i0); i < i1; ++i) {
+            float Pc[D + 1], ua, ub;
+            if (i < 0) {
 #pragma unroll
-            for (int d = 1; d <= D; ++d) P[d] += dl[d - 1];
-            lastu = ua;
-            const float ub = i + 1 < nc ? uat(i + 1) : Uend;
+              for (int d = 0; d <= D; ++d) Pc[d] = Aw[d];
+              ua = 0.f;
+              ub = nc > 0 ? uat(0) : Uend;
+            } else {
+              ua = uat(i);
+              if (i > i0) taylor_shift<D, float>(P, ua - lastu);
+              float dl[D];
+              deltas(i, dl);
+              {
+                // a starter's later knots in this window: count them on its new entry
+                const int vv = GV[i];
+                if ((vv & 8) && (vv & 7)) {
+                  const int idx = s_map[vv >> 4];
+                  if (idx >= 0) atomicAdd(act_jk_ptr(A, idx), 1 << 16);
+                }
+              }
+#pragma unroll
+              for (int d = 1; d <= D; ++d) P[d] += dl[d - 1];
+              lastu = ua;
+#pragma unroll
+              for (int d = 0; d <= D; ++d) Pc[d] = P[d];
+              ub = i + 1 < nc ? uat(i + 1) : Uend;
+            }
             const float a0 = fmaxf(ua, ystart);
             if (ub > a0) {
-              Poly<D> Pf;
-#pragma unroll
-              for (int d = 0; d <= D; ++d) Pf.c[d] = P[d];
-              if (a0 > ua) taylor_shift<D, float>(Pf.c, a0 - ua);
-              acc_l = composite_piece_v<D>(Pf, ub - a0, tfc, acc_l);
+              if (a0 > ua) taylor_shift<D, float>(Pc, a0 - ua);
+              composite_piece_inl<D>(Pc, ub - a0, tfc, tau_l, col_l);
             }
             if (DBG && p.dbg_field && ub > ua) {
-              const long long row = dbg_base++;
+              const long long row = i < 0 ? dbg_np : dbg_base++;
               if (row < p.field_cap) {
                 double* fo = p.dbg_field + ((size_t)dbg_row * p.field_cap + row) * (D + 3);
                 fo[0] = df_to_double(Ta) + (double)ua;
                 fo[1] = df_to_double(Ta) + (double)ub;
-                for (int d = 0; d <= D; ++d) fo[2 + d] = (double)P[d];
+                for (int d = 0; d <= D; ++d) fo[2 + d] = (double)(i < 0 ? Aw[d] : P[d]);
               }
             }
           }
@@ -838,17 +858,17 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
             }
           }
           // combine lanes: transmittance as accumulated optical depth
-          float tx = acc_l.tau;
+          float tx = tau_l;
 #pragma unroll
           for (int o2 = 1; o2 < 32; o2 <<= 1) {
             const float y = __shfl_up_sync(kFull, tx, o2);
             if (lane >= o2) tx += y;
           }
-          const float tex = tx - acc_l.tau;
+          const float tex = tx - tau_l;
           const float w = __expf(-(tau_ray + tex));
-          col[0] += warp_sum(w * acc_l.r);
-          col[1] += warp_sum(w * acc_l.g);
-          col[2] += warp_sum(w * acc_l.b);
+          col[0] += warp_sum(w * col_l[0]);
+          col[1] += warp_sum(w * col_l[1]);
+          col[2] += warp_sum(w * col_l[2]);
           tau_ray += __shfl_sync(kFull, tx, 31);
           dens = (nc > 0 && Uend > 0.f) ? (float)nc / Uend : 0.f;
           Ta = df_add(Ta, df{Uend, 0.f});
@@ -930,7 +950,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? 3 : 1)) k_ray(Rend
             const float x = (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f) * __fdividef(p.lam_scale, h);
             int j = (int)floorf(x + 0.5f);
             const float fr = x - floorf(x);
-            if (fabsf(fr - 0.5f) < 2e-3f) j = nearest_entry_fp64(wv, h, p.n_lambda, q);
+            if (fabsf(fr - 0.5f) < 2e-3f) j = nearest_entry_fp64(wv[0], wv[1], wv[2], h, p.n_lambda, q);
             j = min(max(j, 0), p.n_lambda - 1);
             s_rec[e] = make_float4(tc.hi, tc.lo, h, __fdividef(a, h * h * h));
             s_j[e] = j;

@@ -247,8 +247,13 @@ __device__ __forceinline__ void composite_cell(const float* Q, float L, int c, c
 }
 
 template <int D>
+__device__ __forceinline__ void composite_piece_slow_body(const float* P, float L, float f0, const TfCtx& t,
+                                                          float& tau_l, float* C);
+template <int D>
 __device__ __noinline__ void composite_piece_slow(const float* P, float L, float f0, const TfCtx& t, float& tau_l,
-                                                   float* C);
+                                                   float* C) {
+  composite_piece_slow_body<D>(P, L, f0, t, tau_l, C);
+}
 
 // Composite [0, L] of piece polynomial P (coefficients at the piece start).
 template <int D>
@@ -274,8 +279,8 @@ __device__ __forceinline__ void composite_piece(const float* P, float L, const T
 // Pieces that may cross transfer-function nodes: 8 sub-intervals, node
 // crossings found inside each by a bracketed root search (kept out of line).
 template <int D>
-__device__ __noinline__ void composite_piece_slow(const float* P, float L, float f0, const TfCtx& t, float& tau_l,
-                                                   float* C) {
+__device__ __forceinline__ void composite_piece_slow_body(const float* P, float L, float f0, const TfCtx& t,
+                                                          float& tau_l, float* C) {
   const int NS = 8;
   const float step = L / NS;
   float ya = 0.f, fa = f0;
@@ -349,6 +354,45 @@ __device__ __noinline__ Acc composite_piece_v(Poly<D> P, float L, TfCtx t, Acc a
   float tau = a.tau;
   composite_piece<D>(P.c, L, t, tau, C);
   return Acc{tau, C[0], C[1], C[2]};
+}
+
+// The transfer-function-crossing path with value arguments: a caller's arrays
+// stay in registers (a pointer argument of an out-of-line call would put them
+// in local memory on every use).
+template <int D>
+__device__ __noinline__ Acc composite_piece_slow_v(Poly<D> P, float L, float f0, TfCtx t, Acc a) {
+  float C[3] = {a.r, a.g, a.b};
+  float tau = a.tau;
+  composite_piece_slow_body<D>(P.c, L, f0, t, tau, C);
+  return Acc{tau, C[0], C[1], C[2]};
+}
+
+// Composite [0, L] of piece polynomial P, inline: the common case (the piece
+// stays in one transfer-function cell) here, crossings out of line.
+template <int D>
+__device__ __forceinline__ void composite_piece_inl(const float* P, float L, const TfCtx& t, float& tau_l, float* C) {
+  if (!(L > 0.f)) return;
+  const float f0 = P[0], f1 = horner<D>(P, L);
+  float b2 = 0.f, Lp = 1.f;
+#pragma unroll
+  for (int d = 2; d <= D; ++d) {
+    b2 += d * (d - 1) * fabsf(P[d]) * Lp;
+    Lp *= L;
+  }
+  const float dev = 0.125f * L * L * b2;
+  const int ca = tf_cell(t, fminf(f0, f1) - dev), cb = tf_cell(t, fmaxf(f0, f1) + dev);
+  if (ca == cb) {
+    composite_cell<D>(P, L, ca, t, tau_l, C);
+    return;
+  }
+  Poly<D> pp;
+#pragma unroll
+  for (int d = 0; d <= D; ++d) pp.c[d] = P[d];
+  const Acc r = composite_piece_slow_v<D>(pp, L, f0, t, Acc{tau_l, C[0], C[1], C[2]});
+  tau_l = r.tau;
+  C[0] = r.r;
+  C[1] = r.g;
+  C[2] = r.b;
 }
 // ---------------------------------------------------------------------------
 // the kernel
@@ -693,14 +737,16 @@ __device__ __forceinline__ int warp_bucket_sort(float* k0, int* v0, float* k1, i
     v1[pos] = v0[i];
   }
   __syncwarp();
-  // insertion sort inside this lane's 8 buckets [base, base + s)
+  // insertion sort inside this lane's 8 buckets [base, base + s); after the
+  // scatter rh[b] holds the end of bucket b (read from shared memory, so that
+  // no per-lane array is indexed in the rolled loop)
   {
     int b0 = base;
 #pragma unroll 1
     for (int r = 0; r < 8; ++r) {
-      const int cnt = c[r];
+      const int b1 = rh[lane * 8 + r];
 #pragma unroll 1
-      for (int i = b0 + 1; i < b0 + cnt; ++i) {
+      for (int i = b0 + 1; i < b1; ++i) {
         const float kk = k1[i];
         const int vv = v1[i];
         int j = i - 1;
@@ -712,7 +758,7 @@ __device__ __forceinline__ int warp_bucket_sort(float* k0, int* v0, float* k1, i
         k1[j + 1] = kk;
         v1[j + 1] = vv;
       }
-      b0 += cnt;
+      b0 = b1;
     }
   }
   __syncwarp();
@@ -868,12 +914,10 @@ __device__ __forceinline__ void active_pass(const RenderParams& p, const RayScra
 
 // Nearest Lambda entry decided in FP64 from the double-float components of the
 // ray-to-particle vector (used near a midpoint between entries).
-static __device__ __noinline__ int nearest_entry_fp64(const df* wv, float h, int n_lambda, float q) {
-  double d2d = 0.0;
-  for (int k = 0; k < 3; ++k) {
-    const double wk = (double)wv[k].hi + (double)wv[k].lo;
-    d2d += wk * wk;
-  }
+static __device__ __noinline__ int nearest_entry_fp64(df w0, df w1, df w2, float h, int n_lambda, float q) {
+  const double x0 = (double)w0.hi + (double)w0.lo, x1 = (double)w1.hi + (double)w1.lo,
+               x2 = (double)w2.hi + (double)w2.lo;
+  const double d2d = x0 * x0 + x1 * x1 + x2 * x2;
   const double xd = sqrt(d2d) / (double)h * ((double)(n_lambda - 1) / (double)q);
   return (int)floor(xd + 0.5);
 }
@@ -1738,7 +1782,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
             const float x = (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f) * __fdividef(p.lam_scale, h);
             int j = (int)floorf(x + 0.5f);
             const float fr = x - floorf(x);
-            if (fabsf(fr - 0.5f) < 2e-3f) j = nearest_entry_fp64(wv, h, p.n_lambda, q);
+            if (fabsf(fr - 0.5f) < 2e-3f) j = nearest_entry_fp64(wv[0], wv[1], wv[2], h, p.n_lambda, q);
             j = min(max(j, 0), p.n_lambda - 1);
             T.ent[e] = make_float4(tc.hi, tc.lo, h, __fdividef(a, h * h * h));
             T.jj[e] = j;
