@@ -41,6 +41,14 @@ namespace sphdvr {
 #ifndef SPHDVR_RAY_FILL
 #define SPHDVR_RAY_FILL 0.85f
 #endif
+#ifndef SPHDVR_RAY_U1
+#define SPHDVR_RAY_U1 1
+#endif
+#ifndef SPHDVR_RAY_U2
+#define SPHDVR_RAY_U2 1
+#endif
+constexpr int kRayUnrollScan = SPHDVR_RAY_U1;  // unrolling of the lanes' scan loop
+constexpr int kRayUnrollComp = SPHDVR_RAY_U2;  // unrolling of the lanes' compositing loop
 constexpr int kRayAS = SPHDVR_RAY_AS;    // active particles held in shared memory (per warp)
 constexpr int kRayWarps = 4;             // warps (rays in flight) per CTA
 constexpr int kRayMinBlocks = SPHDVR_RAY_MINB;  // CTAs per SM the register budget is set for
@@ -111,6 +119,22 @@ __device__ __forceinline__ void act_put(const ActSet& A, int i, float4 r, int jk
   }
 }
 __device__ __forceinline__ int* act_jk_ptr(const ActSet& A, int i) { return i < kRayAS ? A.jk + i : A.gjk + (i - kRayAS); }
+
+// Normalised offsets of a particle's knots 0..K in sorted order (Sec. 3.1: the
+// table's positive knots theta_1, theta_2 mirrored, with a middle knot at 0
+// when K is even); entries beyond K are unused.  K is the same on every lane.
+__device__ __forceinline__ void knot_sigmas(int K, float2 th, float (&sg)[5]) {
+  const float a = th.x, b = th.y;
+  if (K == 4) {
+    sg[0] = -b; sg[1] = -a; sg[2] = 0.f; sg[3] = a; sg[4] = b;
+  } else if (K == 3) {
+    sg[0] = -b; sg[1] = -a; sg[2] = a; sg[3] = b; sg[4] = b;
+  } else if (K == 2) {
+    sg[0] = -a; sg[1] = 0.f; sg[2] = a; sg[3] = a; sg[4] = a;
+  } else {
+    sg[0] = -a; sg[1] = a; sg[2] = a; sg[3] = a; sg[4] = a;
+  }
+}
 
 // exclusive prefix sum over the warp; *total gets the sum of all lanes
 __device__ __forceinline__ int warp_excl_scan(int v, int* total) {
@@ -490,8 +514,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
               const int kd = (jk >> 16) & 15, j = jk & 0xffff;
               const bool keep = valid && kd <= K;
               int ne = 0;
-              float base = 0.f;
-              float2 th = make_float2(0.f, 0.f);
+              float uk[5];  // the particle's knots relative to Ta (branch-free, fully unrolled)
               if (keep) {
                 if (gen == 0 && do_anchor) {
                   float Ae[D + 1];
@@ -499,24 +522,25 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
 #pragma unroll
                   for (int d = 0; d <= D; ++d) acc[d] += Ae[d];
                 }
-                th = __ldg(p.theta + j);
-                base = (E.x - Ta.hi) + (E.y - Ta.lo);
-#pragma unroll 1
-                for (int k = kd; k <= K; ++k) {
-                  if (!(fmaf(knot_sigma(K, m, th, k), E.z, base) < U)) break;
-                  ++ne;
+                float sg[5];
+                knot_sigmas(K, __ldg(p.theta + j), sg);
+                const float base = (E.x - Ta.hi) + (E.y - Ta.lo);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                  uk[k] = fmaf(sg[k], E.z, base);
+                  ne += (k >= kd && k <= K && uk[k] < U) ? 1 : 0;  // the knots below U are a prefix
                 }
               }
               const unsigned km = __ballot_sync(kFull, keep);
               const int ni = gen == 0 ? wr + __popc(km & lanemask_lt()) : i;
               int tot;
-              const int off = T_all + warp_excl_scan(ne, &tot);
-#pragma unroll 1
-              for (int r = 0; r < ne; ++r) {
-                const int pos = off + r;
-                if (pos < kRayNK) {
-                  nk0[pos] = fmaf(knot_sigma(K, m, th, kd + r), E.z, base);
-                  nv0[pos] = (ni << 4) | (kd + r);
+              const int off = T_all + warp_excl_scan(ne, &tot) - kd;
+#pragma unroll
+              for (int k = 0; k < 5; ++k) {
+                const int pos = off + k;
+                if (k >= kd && k < kd + ne && pos < kRayNK) {
+                  nk0[pos] = uk[k];
+                  nv0[pos] = (ni << 4) | k;
                 }
               }
               T_all += tot;
@@ -539,31 +563,29 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
               int e = ii < ns ? WV[whead + ii] : -1;
               if (e >= 0 && ((stb[e >> 5] >> (e & 31)) & 1u)) e = -1;  // started already (FP32 ties)
               int ne = 0;
-              float4 E = make_float4(0.f, 0.f, 1.f, 0.f);
-              float base = 0.f;
-              float2 th = make_float2(0.f, 0.f);
+              float uk[5];
               if (e >= 0) {
-                E = s_rec[e];
-                th = __ldg(p.theta + s_j[e]);
-                base = (E.x - Ta.hi) + (E.y - Ta.lo);
-#pragma unroll 1
-                for (int k = 0; k <= K; ++k) {
-                  const float u = fmaf(knot_sigma(K, m, th, k), E.z, base);
-                  if (!(u < U)) break;
-                  // a particle starting inside the window bounds it by its own
-                  // gamma h, or by its first knot when that lies farther
-                  if (k == 0) cap2 = fminf(cap2, fmaxf(u, gam * E.z));
-                  ++ne;
+                const float4 E = s_rec[e];
+                float sg[5];
+                knot_sigmas(K, __ldg(p.theta + s_j[e]), sg);
+                const float base = (E.x - Ta.hi) + (E.y - Ta.lo);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                  uk[k] = fmaf(sg[k], E.z, base);
+                  ne += (k <= K && uk[k] < U) ? 1 : 0;
                 }
+                // a particle starting inside the window bounds it by its own
+                // gamma h, or by its first knot when that lies farther
+                if (ne > 0) cap2 = fminf(cap2, fmaxf(uk[0], gam * E.z));
               }
               int tot;
               const int off = T_all + warp_excl_scan(ne, &tot);
-#pragma unroll 1
-              for (int r = 0; r < ne; ++r) {
-                const int pos = off + r;
-                if (pos < kRayNK) {
-                  nk0[pos] = fmaf(knot_sigma(K, m, th, r), E.z, base);
-                  nv0[pos] = (e << 4) | 8 | r;
+#pragma unroll
+              for (int k = 0; k < 5; ++k) {
+                const int pos = off + k;
+                if (k < ne && pos < kRayNK) {
+                  nk0[pos] = uk[k];
+                  nv0[pos] = (e << 4) | 8 | k;
                 }
               }
               T_all += tot;
@@ -654,7 +676,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
             for (int d = 0; d <= D; ++d) agg[d] = 0.f;
             float ulast = ufirst;
             int nf = 0, nl = 0;  // the window's first and last knots of particles
-#pragma unroll 1
+#pragma unroll kRayUnrollScan
             for (int i = i0; i < i1; ++i) {
               const float ur = uat(i);
               if (i > i0) taylor_shift<D, float>(agg, ur - ulast);
@@ -793,7 +815,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
           // the window with the incoming polynomial; the compositing code is
           // inlined once, here (a call would save the live registers to local
           // memory around every piece)
-#pragma unroll 1
+#pragma unroll kRayUnrollComp
           for (int i = (lane == 0 ? -1 : i0); i < i1; ++i) {
             float Pc[D + 1], ua, ub;
             if (i < 0) {
