@@ -14,7 +14,11 @@ Higher-Order SPH Field Approximation for DVR") computes on the per-ray path:
   overlapping contributions (Sec. 2 localized coefficients; Sec. 4.1 direct
   alternative) -- no recurrence, so no drift;
 * classification and emission-absorption compositing (Sec. 1), evaluated
-  exactly per piece.
+  exactly per piece;
+* gradients (Conclusion: the scheme carries over to additive features): the
+  perpendicular gradient as approximations of G_L = w'(rho)/rho on each table
+  entry's knots, the along-ray gradient as the derivative of the field's pieces,
+  and emission shaded by ka + kd |n . v|.
 * the quantised fixed-point path (Sec. 4.2-4.4, module ``oracle.quant``): the
   quantisation error estimate and optimal quanta, quantised knots in exact
   integers, and the per-ray field of exact integer coefficients.
@@ -30,6 +34,9 @@ from .core import (  # noqa: F401
     kernel_support,
     kernel_w,
     lut_build,
+    lut_build_grad,
+    kernel_dw_r,
+    composite_piece_shaded,
     fixed_knots,
     ray_norm2,
     ray_integral,

@@ -43,6 +43,17 @@ def _load():
             ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_double,  # tf
             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,  # n_rays pix rgba stats
             ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+            ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,  # gpieces ka kd gfield
+        ]
+        lib.orc_kernel_dw_r.restype = ctypes.c_double
+        lib.orc_kernel_dw_r.argtypes = [ctypes.c_int, ctypes.c_double]
+        lib.orc_lut_build_grad.restype = ctypes.c_int
+        lib.orc_lut_build_grad.argtypes = [ctypes.c_int] * 4 + [dp] * 4
+        lib.orc_composite_piece_shaded.restype = None
+        lib.orc_composite_piece_shaded.argtypes = [
+            ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_double,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+            ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
         ]
         lib.orc_composite_piece.restype = None
         lib.orc_composite_piece.argtypes = [
@@ -86,6 +97,29 @@ def kernel_w(kernel, r):
     k = _kid(kernel)
     r = np.asarray(r, dtype=np.float64)
     return np.vectorize(lambda x: lib.orc_kernel_w(k, float(x)))(r) if r.ndim else lib.orc_kernel_w(k, float(r))
+
+
+def kernel_dw_r(kernel, r):
+    """w'(r) / r of the SPH kernel (finite at r = 0), vectorised over r (gradients, oracle part 5)."""
+    lib = _load()
+    k = _kid(kernel)
+    r = np.asarray(r, dtype=np.float64)
+    return np.vectorize(lambda x: lib.orc_kernel_dw_r(k, float(x)))(r) if r.ndim else lib.orc_kernel_dw_r(k, float(r))
+
+
+def lut_build_grad(lut):
+    """Gradient table for a table of lut_build: per entry the optimal approximation of
+    G_L(s) = w'(sqrt(L^2+s^2)) / sqrt(L^2+s^2) on the entry's own knots (the projection of Sec. 3.3).
+    Returns a dict with ``gpieces`` [n][m][D+1], ``gerr`` (||S_G - G_L||) and ``normG`` (||G_L||)."""
+    n, m, D = lut["n_lambda"], (lut["K"] + 1) // 2, lut["D"]
+    th = np.ascontiguousarray(lut["theta"], dtype=np.float64)
+    gp = np.zeros((n, m, D + 1))
+    ge = np.zeros(n)
+    ng = np.zeros(n)
+    rc = _load().orc_lut_build_grad(lut["kernel"], lut["K"], D, n, _dptr(th), _dptr(gp), _dptr(ge), _dptr(ng))
+    if rc:
+        raise ValueError("orc_lut_build_grad rejected the table")
+    return dict(gpieces=gp, gerr=ge, normG=ng)
 
 
 def lut_build(kernel, K, D, n_lambda):
@@ -190,14 +224,17 @@ def particle_amplitude(particles):
     return a
 
 
-def render(particles, lut, camera, tf, pixels, cand_cap=0, field_cap=0):
+def render(particles, lut, camera, tf, pixels, cand_cap=0, field_cap=0, grad=None, shade=(1.0, 0.0)):
     """Render the listed pixels (row-major indices) by direct summation, FP64.
 
     ``particles``: dict with ``pos`` (n,3) float32, ``h`` (n,) float32 and the
     FP32 ``mass``, ``value``, ``density`` (n,) of the C ABI (each optional, 1
     if missing); the amplitude is ``particle_amplitude``.
+    ``grad``: a gradient table of lut_build_grad, or None; with it the emission is
+    shaded by ka + kd |n . v| (``shade`` = (ka, kd)) and ``gfield`` holds per field
+    row the perpendicular gradient's localized coefficients [3][D+1].
     Returns dict(rgba (r,4), stats (r,8) int64, cand_ids (r,cand_cap) or None,
-    field (r, field_cap, D+3) or None, truncated bool).
+    field (r, field_cap, D+3) or None, gfield (r, field_cap, 3, D+1) or None, truncated bool).
     """
     lib = _load()
     pos = np.ascontiguousarray(particles["pos"], dtype=np.float32)
@@ -215,14 +252,17 @@ def render(particles, lut, camera, tf, pixels, cand_cap=0, field_cap=0):
     stats = np.zeros((nr, 8), dtype=np.int64)
     cids = np.full((nr, cand_cap), -1, dtype=np.int64) if cand_cap else None
     fld = np.zeros((nr, field_cap, D + 3)) if field_cap else None
+    gp = np.ascontiguousarray(grad["gpieces"], dtype=np.float64) if grad is not None else None
+    gfld = np.zeros((nr, field_cap, 3, D + 1)) if (field_cap and grad is not None) else None
     rc = lib.orc_render(
         n, _ptr(pos), _ptr(hs), _ptr(amp), lut["kernel"], lut["K"], D, lut["n_lambda"], _ptr(th), _ptr(pc),
         ctypes.byref(cam), int(tf["rgba"].shape[0]), float(tf["lo"]), float(tf["hi"]), _ptr(rgba_tf),
         float(tf["sigma_scale"]), nr, _ptr(pix), _ptr(out), _ptr(stats),
         _ptr(cids) if cids is not None else None, int(cand_cap), _ptr(fld) if fld is not None else None,
-        int(field_cap),
+        int(field_cap), _ptr(gp) if gp is not None else None, float(shade[0]), float(shade[1]),
+        _ptr(gfld) if gfld is not None else None,
     )
-    return dict(rgba=out, stats=stats, cand_ids=cids, field=fld, truncated=bool(rc & 2))
+    return dict(rgba=out, stats=stats, cand_ids=cids, field=fld, gfield=gfld, truncated=bool(rc & 2))
 
 
 def composite_piece(tf, F, ya, yb, rgb=(0.0, 0.0, 0.0), T=1.0):
@@ -234,6 +274,20 @@ def composite_piece(tf, F, ya, yb, rgb=(0.0, 0.0, 0.0), T=1.0):
     t = np.array([T], dtype=np.float64)
     lib.orc_composite_piece(int(rgba_tf.shape[0]), float(tf["lo"]), float(tf["hi"]), _ptr(rgba_tf),
                             float(tf["sigma_scale"]), _ptr(F), len(F) - 1, float(ya), float(yb), _ptr(c), _ptr(t))
+    return c, float(t[0])
+
+
+def composite_piece_shaded(tf, F, GP, ka, kd, ya, yb, rgb=(0.0, 0.0, 0.0), T=1.0):
+    """Composite one piece with shading ka + kd |n . v| (oracle part 5); GP: [3][D+1] perpendicular gradient."""
+    lib = _load()
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    G = np.ascontiguousarray(GP, dtype=np.float64)
+    rgba_tf = np.ascontiguousarray(tf["rgba"], dtype=np.float64)
+    c = np.array(rgb, dtype=np.float64)
+    t = np.array([T], dtype=np.float64)
+    lib.orc_composite_piece_shaded(int(rgba_tf.shape[0]), float(tf["lo"]), float(tf["hi"]), _ptr(rgba_tf),
+                                   float(tf["sigma_scale"]), _ptr(F), _ptr(G), len(F) - 1, float(ka), float(kd),
+                                   float(ya), float(yb), _ptr(c), _ptr(t))
     return c, float(t[0])
 
 

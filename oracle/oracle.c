@@ -26,6 +26,18 @@
  *      exactly: pieces are split at transfer-function node crossings (bisection
  *      on monotone sub-intervals), optical depth is integrated in closed form,
  *      emission by adaptive Gauss-Kronrod.  No early ray termination.
+ *   5. Gradients (Conclusion: the scheme carries over to any feature that is a
+ *      sum of particle contributions).  A particle's gradient at x(t) is
+ *      (c / h^2) (w'(rho) / rho) ((t - t_chi) v - d) with d the vector from the
+ *      ray to the particle (perpendicular to v) and rho = |x - chi| / h: along
+ *      v it is the derivative of its contribution, across the ray it is
+ *      -(c / h^2) d G_L((t - t_chi) / h) with G_L(s) = w'(rho) / rho, which is
+ *      even and compactly supported like B_L.  G_L is approximated by the same
+ *      projection (Sec. 3.3) on the table entry's own knots, so the
+ *      perpendicular gradient of the ray is a piecewise polynomial with the
+ *      same knots; the along-ray part is the derivative of the field's pieces.
+ *      Shading (a reading: the paper names no model): the emitted colour is
+ *      scaled by ka + kd |n . v|, n = grad / |grad| (a light along the ray).
  */
 #include <math.h>
 #include <stdint.h>
@@ -78,6 +90,30 @@ static ld kernel_w(int kernel, ld r) {
 }
 
 double orc_kernel_w(int kernel, double r) { return (double)kernel_w(kernel, r); }
+
+/* w'(r) / r, written in a form that is finite at r = 0 (derivatives of the
+ * four kernels above). */
+static ld kernel_dw_r(int kernel, ld r) {
+  if (r < 0) r = -r;
+  switch (kernel) {
+    case ORC_M4:
+      if (r < 1) return (-12 + 9 * r) / (4 * ORC_PI);
+      if (r < 2) return -3 * (2 - r) * (2 - r) / (4 * ORC_PI * r);
+      return 0;
+    case ORC_WENDLAND_C2:
+      if (r < 2) { ld a = 1 - r / 2; return -105.0L / (16 * ORC_PI) * a * a * a; }
+      return 0;
+    case ORC_WENDLAND_C4:
+      if (r < 2) { ld a = 1 - r / 2, a2 = a * a; return -1155.0L / (256 * ORC_PI) * (5 * r + 2) * a2 * a2 * a; }
+      return 0;
+    case ORC_POLY6:
+      if (r < 1) { ld a = 1 - r * r; return -945.0L / (32 * ORC_PI) * a * a; }
+      return 0;
+  }
+  return 0;
+}
+
+double orc_kernel_dw_r(int kernel, double r) { return (double)kernel_dw_r(kernel, r); }
 
 /* Radii inside (0, q) where w changes its polynomial piece. */
 static int kernel_breaks(int kernel, ld* br) {
@@ -133,6 +169,7 @@ static const double gk_wg[4] = {0.129484966168869693270611432679082, 0.279705391
 
 typedef struct {
   int kernel, K, D, m, middle;
+  int target;             /* approximated function: 0 B_L(t) = w(rho), 1 G_L(t) = w'(rho) / rho */
   ld q, lam, T;           /* L and the half-length T = sqrt(q^2 - L^2) of supp B_L */
   int nsp;
   ld sp[96];              /* split points in (0, T]: grading near 0 + kernel breaks + T */
@@ -141,7 +178,10 @@ typedef struct {
   int bk[ORC_MAXB], bd[ORC_MAXB];  /* index set J in lexicographic order */
 } lam_ctx;
 
-static ld B_of(const lam_ctx* c, ld t) { return kernel_w(c->kernel, sqrtl(c->lam * c->lam + t * t)); }
+static ld B_of(const lam_ctx* c, ld t) {
+  const ld rho = sqrtl(c->lam * c->lam + t * t);
+  return c->target ? kernel_dw_r(c->kernel, rho) : kernel_w(c->kernel, rho);
+}
 
 static int cmp_ld(const void* a, const void* b) {
   ld x = *(const ld*)a, y = *(const ld*)b;
@@ -642,6 +682,47 @@ int orc_lut_build(int kernel, int K, int D, int n_lambda, double* theta, double*
   return 0;
 }
 
+/*
+ * Gradient table (part 5): for every entry of a table built above, the optimal
+ * approximation of G_L(s) = w'(sqrt(L^2 + s^2)) / sqrt(L^2 + s^2) for the
+ * entry's own knots theta (the projection of Sec. 3.3 with G_L in place of
+ * B_L).  Outputs gpieces[n_lambda][m][D+1] (local coefficients as pieces),
+ * gerr[n_lambda] = ||S_G - G_L||_2 and normG[n_lambda] = ||G_L||_2.  Entries
+ * with all knots at 0 get the zero function.  Returns 0 on success.
+ */
+int orc_lut_build_grad(int kernel, int K, int D, int n_lambda, const double* theta, double* gpieces, double* gerr,
+                       double* normG) {
+  if (K < 1 || K > 2 * ORC_MAXM || D < 1 || D > ORC_MAXD || n_lambda < 2) return 1;
+  gl_init();
+  int m = (K + 1) / 2;
+  double q = orc_kernel_support(kernel);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int j = 0; j < n_lambda; j++) {
+    lam_ctx c;
+    lam_ctx_init(&c, kernel, K, D, (ld)j * q / (n_lambda - 1));
+    c.target = 1;
+    double* p_o = gpieces + (size_t)j * m * (D + 1);
+    for (int k = 0; k < m * (D + 1); k++) p_o[k] = 0;
+    gerr[j] = 0; normG[j] = 0;
+    const double* th_i = theta + (size_t)j * m;
+    if (!(c.T > 0) || j == n_lambda - 1 || !(th_i[0] > 0)) continue;
+    bb_acc ba; ba.c = &c; ba.sum = 0;
+    quad_nodes(&c, 0, c.T, acc_bb, &ba);
+    normG[j] = (double)sqrtl(2 * ba.sum);
+    if (c.nb == 0) { gerr[j] = normG[j]; continue; }
+    ld th[ORC_MAXM];
+    for (int k = 0; k < m; k++) th[k] = th_i[k];
+    fixed_sol sol = solve_fixed(&c, th);
+    if (!sol.ok) { gerr[j] = normG[j]; continue; }
+    ld pp[ORC_MAXM][ORC_MAXD + 1];
+    pieces_from_coef(&c, th, sol.coef, pp);
+    for (int k = 0; k < m; k++)
+      for (int d = 0; d <= D; d++) p_o[k * (D + 1) + d] = (double)pp[k][d];
+    gerr[j] = (double)sqrtl(sol.err2);
+  }
+  return 0;
+}
+
 /* Error of the optimal approximation for GIVEN knots (for tests of Sec. 3.3):
  * writes the pieces and returns ||S - B_L||_2, or -1 on invalid knots. */
 double orc_fixed_knots(int kernel, int K, int D, double lam, const double* theta, double* pieces) {
@@ -753,6 +834,7 @@ typedef struct {
   double tc, h, c;   /* t_chi, smoothing length, amplitude a / h^3 */
   int j;             /* table entry */
   int passed;        /* knots already passed */
+  double dp[3];      /* vector from the ray's closest point to the particle (perpendicular to v) */
 } cand_t;
 
 static double binom(int n, int k) {
@@ -762,11 +844,13 @@ static double binom(int n, int k) {
 }
 
 /* Localized coefficients (Sec. 2) at ray parameter ta of one candidate's
- * piece polynomial (pc = piece index between its knots pc and pc+1). */
-static void cand_piece_coef(const orc_lut* L, const cand_t* cd, int pc, double ta, double* A) {
+ * piece polynomial (pc = piece index between its knots pc and pc+1), of the
+ * approximation in table `tab` (the field's pieces, or the gradient's),
+ * times the candidate's amplitude c. */
+static void cand_piece_coef_tab(const orc_lut* L, const double* tab, const cand_t* cd, int pc, double ta, double* A) {
   int K = L->K, D = L->D, m = (K + 1) / 2;
   const double* th = L->theta + (size_t)cd->j * m;
-  const double* P = L->pieces + (size_t)cd->j * m * (D + 1);
+  const double* P = tab + (size_t)cd->j * m * (D + 1);
   int k, sg;
   if (K % 2 == 0) {
     if (pc < m) { k = m - pc; sg = -1; } else { k = pc - m + 1; sg = 1; }
@@ -785,6 +869,10 @@ static void cand_piece_coef(const orc_lut* L, const cand_t* cd, int pc, double t
     A[e] = cd->c * se * acc;
     se *= s;
   }
+}
+
+static void cand_piece_coef(const orc_lut* L, const cand_t* cd, int pc, double ta, double* A) {
+  cand_piece_coef_tab(L, L->pieces, cd, pc, ta, A);
 }
 
 /* Sorted knot offsets (normalised s) of one table entry. */
@@ -849,12 +937,28 @@ typedef struct {
   double a0, a1;     /* sigma = a0 + a1 F  on this sub-interval */
   double c0[3], c1[3];
   double ya, Gya;
+  const double* GP;  /* perpendicular gradient polynomials [3][D+1] (part 5), NULL: no shading */
+  double ka, kd;
 } emis_ctx;
+
+/* Shading factor ka + kd |n . v| at y: n . v = F'(y) / |grad|, |grad|^2 = F'^2 + |GP(y)|^2
+ * (the perpendicular part is orthogonal to v); where the gradient vanishes, ka + kd. */
+static double shade_at(const emis_ctx* e, double y) {
+  double dF = 0, yp = 1;
+  for (int i = 1; i <= e->D; i++) { dF += i * e->F[i] * yp; yp *= y; }
+  double n2 = dF * dF;
+  for (int comp = 0; comp < 3; comp++) {
+    double g = poly_eval(e->GP + comp * (e->D + 1), e->D, y);
+    n2 += g * g;
+  }
+  return n2 > 0 ? e->ka + e->kd * fabs(dF) / sqrt(n2) : e->ka + e->kd;
+}
 
 static void emis_eval(const emis_ctx* e, double y, double* out) {
   double f = poly_eval(e->F, e->D, y);
   double tau = e->a0 * (y - e->ya) + e->a1 * (poly_eval(e->G, e->D + 1, y) - e->Gya);
   double sg = e->a0 + e->a1 * f, w = sg * exp(-tau);
+  if (e->GP) w *= shade_at(e, y);
   for (int ch = 0; ch < 3; ch++) out[ch] = (e->c0[ch] + e->c1[ch] * f) * w;
 }
 
@@ -925,8 +1029,10 @@ static int cmp_d(const void* a, const void* b) {
   return x < y ? -1 : x > y;
 }
 
-/* Composite one field piece F(y), y in [ya, yb] (local to the piece start). */
-static void composite_piece(const orc_tf* tf, const double* F, int D, double ya, double yb, double* rgb, double* Tacc) {
+/* Composite one field piece F(y), y in [ya, yb] (local to the piece start);
+ * with GP (perpendicular gradient polynomials, part 5) the emission is shaded. */
+static void composite_piece(const orc_tf* tf, const double* F, int D, double ya, double yb, double* rgb, double* Tacc,
+                            const double* GP, double ka, double kd) {
   if (!(yb > ya)) return;
   /* monotone sub-intervals: critical points of F */
   double dF[ORC_MAXD + 1], crit[ORC_MAXD + 2];
@@ -965,6 +1071,7 @@ static void composite_piece(const orc_tf* tf, const double* F, int D, double ya,
   qsort(cuts, ncut, sizeof(double), cmp_d);
   emis_ctx e;
   e.F = F; e.D = D;
+  e.GP = GP; e.ka = ka; e.kd = kd;
   e.G[0] = 0;
   for (int i = 0; i <= D; i++) e.G[i + 1] = F[i] / (i + 1);
   double lo = ya;
@@ -995,13 +1102,16 @@ static void composite_piece(const orc_tf* tf, const double* F, int D, double ya,
  *                   a table midpoint, [5] field pieces written, [6] 0, [7] 0
  *   cand_ids        if non-NULL: candidate particle indices, cand_cap per ray
  *   field           if non-NULL: per piece (t_a, t_b, A_0..A_D), field_cap per ray
+ * With gpieces (the gradient table of orc_lut_build_grad, part 5) non-NULL the
+ * emission is shaded with ka, kd, and gfield (if non-NULL) gets per field row
+ * the perpendicular gradient's localized coefficients [3][D+1].
  * Returns 0, or 2 when a buffer capacity was too small (data truncated).
  */
 int orc_render(int64_t n, const float* pos, const float* hs, const double* amp, int kernel, int K, int D,
                int n_lambda, const double* theta, const double* pieces, const orc_camera* cam, int tf_n,
                double tf_lo, double tf_hi, const double* tf_rgba, double sigma_scale, int n_rays,
                const int* pix, double* rgba, int64_t* stats, int64_t* cand_ids, int cand_cap, double* field,
-               int field_cap) {
+               int field_cap, const double* gpieces, double shade_ka, double shade_kd, double* gfield) {
   orc_lut L = {K, D, n_lambda, kernel, theta, pieces};
   orc_tf tf = {tf_n, tf_lo, tf_hi, tf_rgba, sigma_scale};
   double q = orc_kernel_support(kernel);
@@ -1031,7 +1141,7 @@ int orc_render(int64_t n, const float* pos, const float* hs, const double* amp, 
       if (j > n_lambda - 1) j = n_lambda - 1;
       if (fabs(x - floor(x) - 0.5) <= 1e-9) st[4]++;
       if (fabs(d - R) <= 1e-6 * h) st[2]++;
-      cand_t cd = {i, tc, h, amp[i] / (h * h * h), j, 0};
+      cand_t cd = {i, tc, h, amp[i] / (h * h * h), j, 0, {p[0] - tc * v[0], p[1] - tc * v[1], p[2] - tc * v[2]}};
       cands[nc++] = cd;
     }
     st[0] = (int64_t)nc;
@@ -1078,17 +1188,34 @@ int orc_render(int64_t n, const float* pos, const float* hs, const double* amp, 
         cand_piece_coef(&L, c2, c2->passed - 1, ta, Ai);
         for (int e = 0; e <= D; e++) A[e] += Ai[e];
       }
+      /* part 5: the perpendicular gradient's localized coefficients, summed
+       * the same way: -(c / h^2) d times each candidate's G approximation */
+      double GP[3 * (ORC_MAXD + 1)];
+      if (gpieces) {
+        for (int e = 0; e < 3 * (D + 1); e++) GP[e] = 0;
+        for (int a = 0; a < na; a++) {
+          cand_t* c2 = &cands[act[a]];
+          cand_piece_coef_tab(&L, gpieces, c2, c2->passed - 1, ta, Ai);
+          const double sc = -1.0 / (c2->h * c2->h);
+          for (int comp = 0; comp < 3; comp++)
+            for (int e = 0; e <= D; e++) GP[comp * (D + 1) + e] += sc * c2->dp[comp] * Ai[e];
+        }
+      }
       if (field) {
         if (nf < field_cap) {
           double* fo = field + ((size_t)r * field_cap + nf) * (D + 3);
           fo[0] = ta; fo[1] = tb;
           for (int e = 0; e <= D; e++) fo[2 + e] = A[e];
+          if (gpieces && gfield) {
+            double* go = gfield + ((size_t)r * field_cap + nf) * 3 * (D + 1);
+            for (int e = 0; e < 3 * (D + 1); e++) go[e] = GP[e];
+          }
         } else trunc |= 2;
       }
       nf++;
       /* composite the part of the piece inside [t0, t1] */
       double ya = t0 > ta ? t0 - ta : 0, yb = (tb < t1 ? tb : t1) - ta;
-      composite_piece(&tf, A, D, ya, yb, rgb, &Tacc);
+      composite_piece(&tf, A, D, ya, yb, rgb, &Tacc, gpieces ? GP : NULL, shade_ka, shade_kd);
     }
     st[5] = nf;
     out[0] = rgb[0]; out[1] = rgb[1]; out[2] = rgb[2]; out[3] = 1 - Tacc;
@@ -1102,7 +1229,15 @@ int orc_render(int64_t n, const float* pos, const float* hs, const double* amp, 
 void orc_composite_piece(int tf_n, double tf_lo, double tf_hi, const double* tf_rgba, double sigma_scale,
                          const double* F, int D, double ya, double yb, double* rgb_inout, double* T_inout) {
   orc_tf tf = {tf_n, tf_lo, tf_hi, tf_rgba, sigma_scale};
-  composite_piece(&tf, F, D, ya, yb, rgb_inout, T_inout);
+  composite_piece(&tf, F, D, ya, yb, rgb_inout, T_inout, NULL, 1.0, 0.0);
+}
+
+/* The same with shading (part 5): GP are the three perpendicular gradient polynomials [3][D+1]. */
+void orc_composite_piece_shaded(int tf_n, double tf_lo, double tf_hi, const double* tf_rgba, double sigma_scale,
+                                const double* F, const double* GP, int D, double ka, double kd, double ya, double yb,
+                                double* rgb_inout, double* T_inout) {
+  orc_tf tf = {tf_n, tf_lo, tf_hi, tf_rgba, sigma_scale};
+  composite_piece(&tf, F, D, ya, yb, rgb_inout, T_inout, GP, ka, kd);
 }
 
 int orc_num_threads(void) {
