@@ -40,6 +40,11 @@ WORKLOADS = {
     "halo1m": dict(n=1_000_000, a_range=(5e-3, 0.05), seed=SY.BASE_SEED + 1, kernel="wendland_c2", K=4, D=3,
                    n_lambda=4096, res=1024,
                    desc="halo mixture 1,000,000 particles, Wendland C2, K=4, D=3, perspective 1024x1024"),
+    # the large single frame: dam-break slab, high-opacity transfer function (early ray termination)
+    "slab64m": dict(n=64_000_000, slab=True, kernel="wendland_c4", K=4, D=4, n_lambda=4096, res=4096, sigma_scale=500.0,
+                    desc="dam-break slab 64,000,000 particles (dense graded layer + 5% splash, h 1e-4..1e-2), "
+                         "Wendland C4, K=4, D=4, 4096-entry table, perspective 4096x4096, transfer function "
+                         "sigma x500 (early ray termination), FP32 anchored"),
 }
 
 # DRAM bytes (read + write) of one render launch, from the ncu capture named in
@@ -120,13 +125,63 @@ def clocks_stop(proc, f, path, device):
 
 
 def make_inputs(w, device):
-    P = SY.halo_mixture(w["n"], a_range=w["a_range"], seed=w["seed"], device=device)
-    tf = SY.tf_density(P["value"])
+    if w.get("slab"):
+        P = SY.dam_break_slab(w["n"])
+    else:
+        P = SY.halo_mixture(w["n"], a_range=w["a_range"], seed=w["seed"], device=device)
+    tf = SY.tf_density(P["value"], sigma_scale=w.get("sigma_scale", 1.0)) if w.get("sigma_scale") else \
+        SY.tf_density(P["value"])
     return P, tf
 
 
 def camera_for(w, rank, step=0):
+    if w.get("slab"):
+        return SY.orbit_camera(w["res"], w["res"], azimuth_deg=-60.0 + 7.0 * rank, elevation_deg=25.0, distance=1.6,
+                               center=(0.5, 0.25, 0.3))
     return SY.orbit_camera(w["res"], w["res"], azimuth_deg=30.0 + 7.0 * rank, elevation_deg=20.0)
+
+
+def log_dir():
+    """Directory for the run's side files (clock samples, autotune cache): $SPHDVR_BENCH_LOG_DIR or the temp dir."""
+    return os.environ.get("SPHDVR_BENCH_LOG_DIR") or tempfile.gettempdir()
+
+
+def plain_vs_served(S, torch, ctx, ds, lut, tf, opts, dev, stream, n=16, sizes=(128, 256, 512), seed=4321):
+    """The same mixed request set rendered (a) in the plain form -- one render launch per frame with a static
+    ray schedule (persistent=0), frames one after another -- and (b) through the frame server -- two worker
+    streams, the persistent work queue, compatible requests batched into one launch -- all requests queued at
+    once.  Wall time from the first request to the last image; rays/s of each form and their ratio."""
+    rng = np.random.default_rng(seed)
+    cams = []
+    for _ in range(n):
+        r_ = int(rng.choice(sizes))
+        cams.append(SY.orbit_camera(r_, r_, azimuth_deg=360 * rng.random(), elevation_deg=-40 + 80 * rng.random()))
+    rays = sum(c["width"] * c["height"] for c in cams)
+    a_out = [torch.empty((c["height"], c["width"], 4), dtype=torch.float32, device=dev) for c in cams]
+    b_out = [torch.empty_like(o) for o in a_out]
+    plain = dict(opts, persistent=0)
+    S.sphdvr_render(ctx, ds, lut, cams[0], tf, plain, a_out[0].data_ptr(), stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, o in zip(cams, a_out):
+        S.sphdvr_render(ctx, ds, lut, c, tf, plain, o.data_ptr(), stream=stream)
+        torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    srv = S.Server(ctx, 16 << 30, max_inflight=2)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(ds, lut, c, tf, dict(opts, persistent=1), o.data_ptr()) for c, o in zip(cams, b_out)]
+    for t_ in tickets:
+        srv.wait(t_, -1)
+    t_served = time.perf_counter() - t0
+    bs = srv.batch_stats()
+    srv.destroy()
+    diff = max(float((a - b).abs().max()) for a, b in zip(a_out, b_out))
+    return dict(requests=n, sizes=list(sizes), rays=rays, plain_ms=t_plain * 1e3, served_ms=t_served * 1e3,
+                plain_mrays_per_s=rays / t_plain / 1e6, served_mrays_per_s=rays / t_served / 1e6,
+                ratio=t_plain / t_served, served_launches=bs["launches"], largest_batch=bs["largest"],
+                max_pixel_diff=diff,
+                note="plain: one sphdvr_render per frame, static ray schedule, synchronised frame by frame; served: "
+                     "frame server, 2 workers, work queue, batched launches, all requests queued at once; wall time")
 
 
 def cpu_oracle_rate(P, w, tf, n_pix, seed, threads=None):
@@ -178,6 +233,120 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def serving_stream(S, torch, ctx, tf_all, dev, per_rate=20, seed=2024, workers=3):
+    """C4: four resident clustered data sets (1M, 4M, 16M, 32M particles of the halo generator, seeds +0..3),
+    requests with random orbit cameras and sizes uniform over {256, 512, 1024, 2048} squared, Poisson arrivals.
+    The service rate is measured first (a burst of requests queued at once); then three arrival rates
+    (0.5, 0.8 and 1.2 times it) with `per_rate` requests each: p50/p99 submission-to-completion latency per
+    rate and per size."""
+    sets, luts = [], {}
+    th, pc, _ = S.sphdvr_lut_build("wendland_c2", 4, 3, 4096)
+    lut = S.sphdvr_lut_create(ctx, "wendland_c2", 4, 3, 4096, th, pc)
+    for i, n in enumerate((1_000_000, 4_000_000, 16_000_000, 32_000_000)):
+        P = SY.halo_mixture(n, seed=SY.BASE_SEED + 1 + i, device="cuda")
+        t = {k: torch.from_numpy(np.ascontiguousarray(P[k])).to(dev) for k in ("pos", "h", "mass", "density", "value")}
+        ds = S.sphdvr_dataset_create(ctx, t["pos"], t["h"], t["mass"], t["density"], t["value"])
+        sets.append((n, ds, SY.tf_density(P["value"])))
+        del t, P
+    resident = sum(S.sphdvr_dataset_info(ds)["bytes"] for _, ds, _ in sets)
+    rng = np.random.default_rng(seed)
+    sizes = (256, 512, 1024, 2048)
+
+    def request():
+        k = int(rng.integers(len(sets)))
+        r_ = int(rng.choice(sizes))
+        return k, r_, SY.orbit_camera(r_, r_, azimuth_deg=360 * rng.random(), elevation_deg=-40 + 80 * rng.random())
+
+    def run(reqs, gaps):
+        srv = S.Server(ctx, 64 << 30, max_inflight=workers)
+        outs, tix = [], []
+        t0 = time.perf_counter()
+        for (k, r_, c_), g in zip(reqs, gaps):
+            time.sleep(g)
+            o_ = torch.empty((r_, r_, 4), dtype=torch.float32, device=dev)
+            outs.append(o_)
+            tix.append((time.perf_counter(), r_, srv.submit(sets[k][1], lut, c_, sets[k][2], dict(ert_eps=1e-5),
+                                                            o_.data_ptr())))
+        lat = []
+        pending = list(tix)
+        while pending:  # completion times, polled
+            still = []
+            for ts, r_, t_ in pending:
+                try:
+                    srv.wait(t_, 0)
+                    lat.append((time.perf_counter() - ts, r_))
+                except S.SphdvrError as e:
+                    if e.status != S.ETIMEOUT:
+                        raise
+                    still.append((ts, r_, t_))
+            pending = still
+            if pending:
+                time.sleep(0.005)
+        wall = time.perf_counter() - t0
+        srv.destroy()
+        rays = sum(r_ * r_ for _, r_, _ in reqs)
+        return lat, wall, rays
+
+    burst = [request() for _ in range(2 * workers + 2)]
+    lat, wall, rays = run(burst, [0.0] * len(burst))
+    capacity = len(burst) / wall  # requests per second at saturation
+    out = dict(datasets="halo generator 1M/4M/16M/32M, seeds +0..3, resident together (%.2f GB)" % (resident / 1e9),
+               sizes=list(sizes), workers=workers, burst=dict(requests=len(burst), requests_per_s=capacity,
+                                                              mrays_per_s=rays / wall / 1e6), rates=[])
+    for f in (0.5, 0.8, 1.2):
+        lam = f * capacity
+        reqs = [request() for _ in range(per_rate)]
+        gaps = list(rng.exponential(1.0 / lam, size=per_rate))
+        lat, wall, rays = run(reqs, gaps)
+        ms = np.array([x[0] for x in lat]) * 1e3
+        per_size = {}
+        for r_ in sizes:
+            v = np.array([x[0] for x in lat if x[1] == r_]) * 1e3
+            if len(v):
+                per_size[str(r_)] = dict(n=int(len(v)), p50_ms=float(np.percentile(v, 50)),
+                                         p99_ms=float(np.percentile(v, 99)))
+        out["rates"].append(dict(load=f, requests_per_s=lam, requests=per_rate, p50_ms=float(np.percentile(ms, 50)),
+                                 p99_ms=float(np.percentile(ms, 99)), mrays_per_s=rays / wall / 1e6,
+                                 per_size=per_size))
+    for _, ds, _ in sets:
+        S.sphdvr_dataset_free(ds)
+    S.sphdvr_lut_free(lut)
+    return out
+
+
+def precision_sweep_times(S, torch, ctx, ds, w, tf, cam, dev, stream, degrees=(1, 2, 3, 4)):
+    """C3's frame times: each precision mode x degree D on the workload's frame (kernel time, CUDA events),
+    and each mode's largest pixel difference from the FP32 anchored frame of the same D.  (The errors against
+    the FP64 oracle are measured by tests/test_gpu_precision_sweep.py.)"""
+    W, H = cam["width"], cam["height"]
+    rows = []
+    for D in degrees:
+        th, pc, _ = S.sphdvr_lut_build(w["kernel"], w["K"], D, w["n_lambda"])
+        lt = S.sphdvr_lut_create(ctx, w["kernel"], w["K"], D, w["n_lambda"], th, pc)
+        imgs = {}
+        for mode in ("fp32_anchored", "fp32_naive", "fp64_naive", "fp32_reinit", "int64_quant"):
+            o = dict(precision=mode, ert_eps=1e-5)
+            if mode == "fp32_reinit":
+                o["reinit_dt"] = 0.02
+            if mode == "int64_quant":
+                q = S.sphdvr_dataset_quant_params(ctx, ds, w["kernel"], D, 64)
+                o.update(quant_tau=q["tau"], quant_sigma=q["sigma"])
+            img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+            S.sphdvr_render(ctx, ds, lt, cam, tf, o, img.data_ptr(), stream=stream)
+            torch.cuda.synchronize()
+            st = S.sphdvr_frame_stats(ctx)
+            imgs[mode] = img
+            rows.append(dict(D=D, mode=mode, render_ms=st["render_ns"] / 1e6,
+                             mrays_per_s=W * H / (st["render_ns"] / 1e9) / 1e6, segments=st["segments"],
+                             flags=st["overflow"]))
+        for r in rows:
+            if r["D"] == D:
+                r["max_pixel_diff_vs_anchored"] = float((imgs[r["mode"]] - imgs["fp32_anchored"]).abs().max())
+        del imgs
+        S.sphdvr_lut_free(lt)
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,6 +367,14 @@ def main():
                     help="time the paper's scatter-sort pass order against ray gathering on a 1M-particle frame (0: skip)")
     ap.add_argument("--quant-frame", type=int, default=1,
                     help="time the quantised integer path against FP32 anchored on a 1M-particle frame (0: skip)")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="tune the render options on the workload's frame before timing (sphdvr_autotune; 0: defaults)")
+    ap.add_argument("--plain-vs-served", type=int, default=16,
+                    help="requests of the plain-vs-served comparison (0: skip)")
+    ap.add_argument("--precision-sweep", action="store_true",
+                    help="also time every precision mode x D in {1,2,3,4} on the workload's frame (C3)")
+    ap.add_argument("--serving-stream", type=int, default=0,
+                    help="requests per arrival rate of the C4 serving stream over four resident data sets (0: skip)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.res > 0:
@@ -238,6 +415,22 @@ def main():
     W, H = cam["width"], cam["height"]
     out = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
+    # ---- autotuning: the timed frames use the options the autotuner picks for this frame
+    autotune = None
+    if args.autotune and args.precision in ("fp32_anchored", "fp32_naive"):
+        default_opts = dict(opts)
+        opts, (ms0, ms1) = S.sphdvr_autotune(ctx, ds, lut, cam, tf, default_opts,
+                                             cache_path=os.path.join(log_dir(), "sphdvr_autotune_r%d.jsonl" % rank),
+                                             stream=stream)
+        # the default options once at the full size, for the speed-up the tuning brings there
+        S.sphdvr_render(ctx, ds, lut, cam, tf, default_opts, out.data_ptr(), stream=stream)
+        torch.cuda.synchronize()
+        full_default_ms = S.sphdvr_frame_stats(ctx)["render_ns"] / 1e6
+        autotune = dict(chosen=dict(ctas_per_sm=opts["ctas_per_sm"], window_h=opts["window_h"],
+                                    window_fill=opts["window_fill"]),
+                        tuning_frame_ms=dict(default=ms0, tuned=ms1), full_frame_default_ms=full_default_ms,
+                        note="coordinate descent over CTAs per SM, window_h, window_fill on the frame's view at "
+                             "<= 512x512 (render-kernel time, CUDA events); the timed frames use the chosen options")
 
     def frame():
         S.sphdvr_render(ctx, ds, lut, cam, tf, opts, out.data_ptr(), stream=stream)
@@ -308,6 +501,11 @@ def main():
                        p50_ms=sv["p50_ms"], p99_ms=sv["p99_ms"], mrays_per_s=sv["rays_per_s"] / 1e6,
                        failed=int(sv["failed"]), render_launches=bs["launches"], largest_batch=bs["largest"])
         del outs
+
+    # ---- plain one-launch-per-frame form against the served form on one mixed request set
+    pvs = None
+    if args.plain_vs_served > 0:
+        pvs = plain_vs_served(S, torch, ctx, ds, lut, tf, opts, dev, stream, n=args.plain_vs_served)
 
     # ---- batching: the same small frames rendered one launch each and as one batched launch
     batching = None
@@ -430,6 +628,9 @@ def main():
         S.sphdvr_dataset_free(ds1)
         del ga, sc
 
+    sweep = precision_sweep_times(S, torch, ctx, ds, w, tf, cam, dev, stream) if args.precision_sweep else None
+    stream_c4 = serving_stream(S, torch, ctx, tf, dev, per_rate=args.serving_stream) if args.serving_stream > 0 else None
+
     if rank == 0:
         seg_per_frame = segs / args.steps
         fps = flops_per_segment(w["K"], w["D"])
@@ -461,6 +662,16 @@ def main():
             gpu_launches=int(launches),
             clocks=clocks,
         )
+        if autotune:
+            autotune["full_frame_tuned_ms"] = kern_s * 1e3
+            autotune["full_frame_speedup"] = autotune["full_frame_default_ms"] / (kern_s * 1e3)
+            line["autotune"] = autotune
+        if pvs:
+            line["plain_vs_served"] = pvs
+        if sweep:
+            line["precision_sweep"] = sweep
+        if stream_c4:
+            line["serving_stream"] = stream_c4
         if serving:
             line["serving"] = serving
         if batching:

@@ -15,7 +15,7 @@ LIB = os.path.join(LIBDIR, "libsphdvr.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 CU = ["api.cu", "sort.cu", "dataset.cu", "frame.cu", "server.cu", "static_scratch.cu", "plan.cu", "scatter.cu",
-      "quanta.cu", "peak.cu"]
+      "quanta.cu", "peak.cu", "autotune.cu"]
 # the render kernels: one source compiled once per polynomial degree
 DEGREES = range(1, 7)
 RENDER_INST = "render_inst.cu"

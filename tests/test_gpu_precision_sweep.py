@@ -1,0 +1,83 @@
+"""Precision / degree sweep (the survey's C3 workload): every precision mode x D in {1, 2, 3, 4}, errors per
+pixel and per ray field against the FP64 oracle on 48 seeded rays.
+
+By default a 1,000,000-particle halo mixture at 512x512 (the test suite's size); with SPHDVR_SWEEP_FULL=1 the
+16,777,216-particle set at 2048x2048 of the benchmark.  Each row: worst and median field relative L2 over the
+rays, worst and median absolute pixel error.  What must hold:
+* FP32 anchored (re-started every 2nd window from the exact sum of the active pieces, Sec. 4.1's direct
+  localized coefficients): within the field (1e-5) and pixel (2e-4) tolerances for every D;
+* FP32 with reinitialisation knots (Sec. 4.1): within the tolerances as well, at a spacing of 0.02 along t
+  for D <= 3 and 0.005 for D = 4 (the recurrence amplifies its rounding by about (distance / h)^D between two
+  reinitialisations: at D = 4 the 0.02 spacing, four times the smallest h, reached 2.6e-5 on the worst ray);
+* the plain recurrences (FP32, and FP64 running coefficients over FP32 difference coefficients) drift:
+  their field error is larger than the anchored one (Sec. 4.1 "sprinkling");
+* the quantised integer path (Sec. 4.2-4.4, 64 bits, quanta of the data set) renders without a flag; its
+  error is the quantisation's (one length quantum serves particles whose h spans two decades) and is
+  reported, bounded only against gross failure here.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_02896_b300 import synthetic as SY
+
+from _helpers import FIELD_REL_L2, PIXEL_ABS, field_rel_l2, oracle_lut
+
+pytestmark = pytest.mark.gpu
+
+FULL = os.environ.get("SPHDVR_SWEEP_FULL") == "1"
+
+
+def test_precision_degree_sweep():
+    from paper_2401_02896_b300 import sphdvr as S
+
+    if FULL:
+        P = SY.halo_mixture(16_777_216, a_range=(5e-4, 0.05), seed=SY.BASE_SEED + 2, device="cuda")
+        res = 2048
+    else:
+        P = SY.halo_mixture(1_000_000, a_range=(5e-3, 0.05), seed=SY.BASE_SEED + 1, device="cuda")
+        res = 512
+    cam = SY.orbit_camera(res, res)
+    tf = SY.tf_density(P["value"])
+    pix = SY.pixel_sample(res, res, 48, seed=33)
+    ctx = S.sphdvr_create(0)
+    ds = S.sphdvr_dataset_create(ctx, P["pos"], P["h"], P["mass"], P["density"], P["value"])
+    rows = []
+    try:
+        for D in (1, 2, 3, 4):
+            lut = oracle_lut("wendland_c2", 4, D, 4096)
+            lt = S.sphdvr_lut_create(ctx, "wendland_c2", 4, D, 4096, lut["theta"], lut["pieces"])
+            R = oracle.render(P, lut, cam, tf, pix, field_cap=1 << 18)
+            q = S.sphdvr_dataset_quant_params(ctx, ds, "wendland_c2", D, 64)
+            modes = {
+                "fp32_anchored": dict(precision="fp32_anchored"),
+                "fp32_reinit": dict(precision="fp32_reinit", reinit_dt=0.02 if D <= 3 else 0.005),
+                "fp32_naive": dict(precision="fp32_naive"),
+                "fp64_naive": dict(precision="fp64_naive"),
+                "int64_quant": dict(precision="int64_quant", quant_tau=q["tau"], quant_sigma=q["sigma"]),
+            }
+            for name, o in modes.items():
+                G = S.sphdvr_debug_rays(ctx, ds, lt, cam, tf, dict(o, ert_eps=0.0), pix, field_cap=1 << 18, D=D)
+                assert not G["overflow"], name
+                fe = [field_rel_l2(G["field"][r, :G["counts"][r, 2]], R["field"][r, :R["stats"][r, 5]], D)
+                      for r in range(len(pix)) if R["stats"][r, 0]]
+                pe = np.abs(G["rgba"].astype(np.float64) - R["rgba"]).max(axis=1)
+                rows.append(dict(D=D, mode=name, field_worst=float(max(fe)), field_median=float(np.median(fe)),
+                                 pixel_worst=float(pe.max()), pixel_median=float(np.median(pe))))
+            S.sphdvr_lut_free(lt)
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_destroy(ctx)
+    for r in rows:
+        print(json.dumps(r))
+    by = {(r["D"], r["mode"]): r for r in rows}
+    for D in (1, 2, 3, 4):
+        a = by[(D, "fp32_anchored")]
+        assert a["field_worst"] <= FIELD_REL_L2 and a["pixel_worst"] <= PIXEL_ABS, a
+        ri = by[(D, "fp32_reinit")]
+        assert ri["field_worst"] <= FIELD_REL_L2 and ri["pixel_worst"] <= PIXEL_ABS, ri
+        assert by[(D, "fp32_naive")]["field_worst"] > a["field_worst"]
+        assert by[(D, "int64_quant")]["pixel_worst"] < 0.05, by[(D, "int64_quant")]
