@@ -138,11 +138,25 @@ typedef struct {
                         active in the frame pass; 0 selects 4096, else in [64, 4096].  A
                         ray that needs more is abandoned by the frame pass and rendered
                         again by a fallback pass with 16384 of each (same image); only a
-                        ray beyond that too is wrong, and sets frame flag bit 5.  Smaller
-                        values exist to exercise the fallback. */
+                        ray beyond that too, or beyond the fallback's list of 65,536 rays
+                        per frame, is wrong (left unwritten when the list is full), and
+                        sets frame flag bit 5.  Smaller values exist to exercise the
+                        fallback. */
   int reserved;      /* must be 0 */
   double quant_tau;   /* INT64_QUANT: length quantum (ray-parameter units, > 0) */
   double quant_sigma; /* INT64_QUANT: field value quantum (> 0) */
+  float window_fill;  /* FP32_ANCHORED / FP32_NAIVE: a window also ends where the knot density
+                         of the previous window puts window_fill times its capacity of knots
+                         (0 selects 0.85; values >= 1 turn the rule off) */
+  int ctas_per_sm;    /* render-grid CTAs per SM (0: as many as fit; else 1 .. that) */
+  int shading;        /* 1: shaded rendering -- the emission of every point is scaled by
+                           ka + kd |n . v|, n the direction of the field's gradient and v the
+                           ray's (a light at the eye); the gradient is reconstructed along the
+                           ray like the field (see sphdvr_lut_set_gradient), which the table
+                           must carry.  FP32_ANCHORED / FP32_NAIVE, through sphdvr_render and
+                           sphdvr_debug_rays only.  0: off (shade_ka / shade_kd ignored) */
+  float shade_ka;     /* shading: ambient weight, finite and >= 0 */
+  float shade_kd;     /* shading: diffuse weight, finite and >= 0 */
 } sphdvr_render_opts;
 
 typedef struct sphdvr_ctx sphdvr_ctx;
@@ -234,6 +248,27 @@ sphdvr_status sphdvr_dataset_quant_params(sphdvr_ctx* ctx, const sphdvr_dataset*
 sphdvr_status sphdvr_lut_create(sphdvr_ctx* ctx, int kernel, int K, int D, int n_lambda, const double* theta,
                                 const double* pieces, sphdvr_lut** out);
 sphdvr_status sphdvr_lut_free(sphdvr_lut* lut);
+
+/* Gradient table (the Conclusion: quantities generated additively from the
+ * particles' contributions, gradients among them, are approximated the same
+ * way as the field).  A particle's field contribution c w(|x - chi| / h) has
+ * the gradient c (x - chi) w'(r) / (r h^2): its part across a ray is, at ray
+ * parameter s from the closest point, (closest point - chi) c / h^2 times
+ * G_L(s) = w'(rho) / rho with rho = sqrt(L^2 + s^2) (along the ray it is the
+ * derivative of the field piece itself).  For every entry j of a table with
+ * knots theta (layout of sphdvr_lut_build) this computes in FP64 the optimal
+ * even piecewise polynomial approximation of G_{L_j} on the entry's OWN
+ * knots (the projection of Sec. 3.3 with G in place of B): gpieces in the
+ * layout of `pieces`, [n_lambda * m * (D+1)], and gerr[j] its L2 error (gerr
+ * may be NULL).  Host arrays, caller-allocated.  EINVAL on bad arguments. */
+sphdvr_status sphdvr_lut_build_grad(int kernel, int K, int D, int n_lambda, const double* theta, double* gpieces,
+                                    double* gerr);
+
+/* Attach a gradient table (from sphdvr_lut_build_grad with this table's
+ * knots) to a device table, replacing any earlier one; shaded rendering needs
+ * it.  `theta` must be the knots the table was created with (compared in
+ * FP32; EINVAL otherwise).  Host arrays; synchronous upload. */
+sphdvr_status sphdvr_lut_set_gradient(sphdvr_lut* lut, const double* theta, const double* gpieces);
 
 /* Table files (the table is built once, offline, Sec. 3.1).  Layout, little
  * endian: 8 bytes "SPHDVRLT", uint32 version 1, int32 kernel, K, D, n_lambda,
@@ -391,6 +426,27 @@ sphdvr_status sphdvr_render_static_scratch(sphdvr_ctx* ctx, const sphdvr_dataset
                                            const sphdvr_camera* cam, const sphdvr_tf* tf,
                                            const sphdvr_render_opts* opts, float* rgba_out, void* stream);
 
+/* Autotuner (no counterpart in the paper: a serving service).  Picks the
+ * runtime parameters of the FP32 window kernel -- ctas_per_sm (render-grid
+ * occupancy, 1..3), window_h (1, 1.5, 2) and window_fill (0.6, 0.85, off) --
+ * for this data set, table, transfer function and camera by timing real frames
+ * (CUDA events around the render kernels on `stream`, best of two after a
+ * warm-up), one parameter at a time from `base` (NULL: the defaults), on the
+ * camera's view at no more than 512 x 512 pixels; a change is kept only for a
+ * gain above 1 %.  None of the parameters changes what is computed beyond
+ * FP32 rounding (window_h <= 2 keeps the field within its tolerance).
+ * *tuned gets `base` with the chosen values; ms (may be NULL) the frame times
+ * before and after, in ms.  cache_path (may be NULL): a JSON-lines file keyed
+ * by device name, kernel, K, D, table size, log2 of the particle, chunk and
+ * pixel counts, the data set's smoothing-length levels, precision and
+ * anchor_every -- a hit returns the cached choice without timing, a miss
+ * appends its result.  Allocates one frame image for the duration of the call;
+ * changes no device setting.  EINVAL for bad arguments or a precision other
+ * than FP32_ANCHORED / FP32_NAIVE. */
+sphdvr_status sphdvr_autotune(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+                              const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* base,
+                              const char* cache_path, void* stream, sphdvr_render_opts* tuned, double ms[2]);
+
 /* FP32 FMA throughput of the context's device in TFLOP/s (no counterpart in
  * the paper: the roofline denominator of the render kernel, which is bound by
  * FP32/ALU issue).  Eight independent FMA chains per thread on every resident
@@ -496,6 +552,17 @@ sphdvr_status sphdvr_debug_rays(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const
                                 const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
                                 int n_pix, const int* pix, float* rgba, int64_t* counts, int64_t* cand_ids,
                                 int cand_cap, double* field, int field_cap);
+
+/* As sphdvr_debug_rays with opts->shading = 1 (required), and beside every
+ * field row i of pixel r the across-ray gradient of the field on that piece:
+ *   grad[((r*field_cap + i)*3 + c)*(D+1) + d], c = x, y, z: its localized
+ * coefficients at t_a (the gradient there is sum_d grad[..d] (t - t_a)^d; the
+ * along-ray part is the derivative of the field row).  grad (HOST, may be NULL)
+ * holds n_pix * field_cap * 3 * (D+1) doubles. */
+sphdvr_status sphdvr_debug_rays_grad(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+                                     const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
+                                     int n_pix, const int* pix, float* rgba, int64_t* counts, double* field,
+                                     double* grad, int field_cap);
 
 #ifdef __cplusplus
 }

@@ -139,6 +139,21 @@ sphdvr_status check_opts(sphdvr_ctx* ctx, const sphdvr_render_opts* o) {
   if (o->ray_capacity != 0 && (o->ray_capacity < 64 || o->ray_capacity > 4096))
     return set_err(ctx, SPHDVR_EINVAL, "opts: ray_capacity must be 0 or in [64, 4096]");
   if (o->reserved) return set_err(ctx, SPHDVR_EINVAL, "opts: reserved field must be 0");
+  if (!(o->window_fill >= 0.f) || !std::isfinite(o->window_fill))
+    return set_err(ctx, SPHDVR_EINVAL, "opts: window_fill must be finite and >= 0");
+  if (o->ctas_per_sm < 0 || o->ctas_per_sm > 32) return set_err(ctx, SPHDVR_EINVAL, "opts: ctas_per_sm out of [0, 32]");
+  if (o->shading != 0 && o->shading != 1) return set_err(ctx, SPHDVR_EINVAL, "opts: shading must be 0 or 1");
+  if (o->shading) {
+    if (o->precision != SPHDVR_PREC_FP32_ANCHORED && o->precision != SPHDVR_PREC_FP32_NAIVE)
+      return set_err(ctx, SPHDVR_EINVAL, "opts: shading needs FP32_ANCHORED or FP32_NAIVE");
+    if (!(o->shade_ka >= 0.f) || !std::isfinite(o->shade_ka) || !(o->shade_kd >= 0.f) || !std::isfinite(o->shade_kd))
+      return set_err(ctx, SPHDVR_EINVAL, "opts: shade_ka and shade_kd must be finite and >= 0");
+  }
+  return SPHDVR_OK;
+}
+
+sphdvr_status reject_shading(sphdvr_ctx* ctx, const sphdvr_render_opts* o, const char* where) {
+  if (o && o->shading) return set_err(ctx, SPHDVR_EINVAL, std::string(where) + ": shading is available through sphdvr_render and sphdvr_debug_rays only");
   return SPHDVR_OK;
 }
 
@@ -158,7 +173,7 @@ size_t ctx_held_bytes(const sphdvr_ctx* c) {
   const DevBuf* bufs[] = {&c->chunk_rect, &c->chunk_front, &c->chunk_ntile, &c->chunk_off, &c->pair_key,
                           &c->pair_val, &c->pair_key2, &c->pair_val2, &c->tile_range, &c->scan_tmp, &c->sort_tmp,
                           &c->stats, &c->tf, &c->img, &c->dbg_pix, &c->dbg_rgba, &c->dbg_counts, &c->dbg_cands,
-                          &c->dbg_field, &c->table, &c->work, &c->frames, &c->fb_table, &c->fb_list};
+                          &c->dbg_field, &c->dbg_grad, &c->table, &c->work, &c->frames, &c->fb_table, &c->fb_list};
   size_t t = 0;
   for (const DevBuf* b : bufs) t += b->bytes;
   return t;
@@ -168,7 +183,7 @@ void ctx_release_buffers(sphdvr_ctx* c) {
   DevBuf* bufs[] = {&c->chunk_rect, &c->chunk_front, &c->chunk_ntile, &c->chunk_off, &c->pair_key, &c->pair_val,
                     &c->pair_key2, &c->pair_val2, &c->tile_range, &c->scan_tmp, &c->sort_tmp, &c->stats,
                     &c->tf, &c->img, &c->dbg_pix, &c->dbg_rgba, &c->dbg_counts, &c->dbg_cands, &c->dbg_field,
-                    &c->table, &c->work, &c->frames, &c->fb_table, &c->fb_list};
+                    &c->dbg_grad, &c->table, &c->work, &c->frames, &c->fb_table, &c->fb_list};
   for (DevBuf* b : bufs) free_buf(*b);
   c->stats_pending = false;
 }
@@ -361,29 +376,22 @@ sphdvr_status sphdvr_lut_build(int kernel, int K, int D, int n_lambda, double* t
   return build_lut_host(kernel, K, D, n_lambda, theta, pieces, err) ? SPHDVR_EINVAL : SPHDVR_OK;
 }
 
-sphdvr_status sphdvr_lut_create(sphdvr_ctx* ctx, int kernel, int K, int D, int n_lambda, const double* theta,
-                                const double* pieces, sphdvr_lut** out) {
-  if (!ctx || !out) return SPHDVR_EINVAL;
-  *out = nullptr;
-  if (kernel < 0 || kernel > 3 || K < 1 || K > 4 || D < 1 || D > 6 || n_lambda < 2 || n_lambda > 65536 || !theta ||
-      !pieces)
-    return set_err(ctx, SPHDVR_EINVAL, "lut_create: bad arguments (K in [1,4], D in [1,6], n_lambda in [2,65536])");
-  cudaError_t e = cudaSetDevice(ctx->device);
-  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+// Device layouts of one table's pieces (for the field, or for the gradient's
+// G_L on the same knots): per entry the localized difference coefficients
+// (Sec. 2) at the knot slots -- jump[j*3*D + s*D + d-1], slot 0 the middle knot
+// (even K), slot s >= 1 the knot +theta_s -- and the pieces' local
+// coefficients piece[j*2*(D+1) + (k-1)*(D+1) + d].  False on a non-finite
+// coefficient.
+static bool difference_tables(int K, int D, int n_lambda, const double* theta, const double* pieces,
+                              std::vector<float>& jump, std::vector<float>& pc) {
   const int m = (K + 1) / 2;
-  std::vector<float> th(2 * (size_t)n_lambda, 0.f), jump((size_t)n_lambda * 3 * D, 0.f),
-      pc((size_t)n_lambda * 2 * (D + 1), 0.f);
+  jump.assign((size_t)n_lambda * 3 * D, 0.f);
+  pc.assign((size_t)n_lambda * 2 * (D + 1), 0.f);
   for (int j = 0; j < n_lambda; ++j) {
     const double* T = theta + (size_t)j * m;
     const double* P = pieces + (size_t)j * m * (D + 1);
-    for (int k = 0; k < m; ++k) {
-      if (!std::isfinite(T[k]) || T[k] < 0 || (k && T[k] < T[k - 1]))
-        return set_err(ctx, SPHDVR_EINVAL, "lut_create: knots must be finite, >= 0 and non-decreasing");
-    }
     for (int i = 0; i < m * (D + 1); ++i)
-      if (!std::isfinite(P[i])) return set_err(ctx, SPHDVR_EINVAL, "lut_create: non-finite piece coefficient");
-    th[2 * j] = (float)T[0];
-    th[2 * j + 1] = (float)(m > 1 ? T[1] : T[0]);
+      if (!std::isfinite(P[i])) return false;
     for (int k = 0; k < m; ++k)
       for (int d = 0; d <= D; ++d) pc[(size_t)j * 2 * (D + 1) + k * (D + 1) + d] = (float)P[k * (D + 1) + d];
     // localized difference coefficients (Sec. 2) at +theta_r: P_{r+1} - P_r expanded at theta_r
@@ -402,6 +410,31 @@ sphdvr_status sphdvr_lut_create(sphdvr_ctx* ctx, int kernel, int K, int D, int n
     if (!(K & 1))
       for (int d = 1; d <= D; d += 2) jump[(size_t)j * 3 * D + 0 * D + d - 1] = (float)(2.0 * P[d]);
   }
+  return true;
+}
+
+sphdvr_status sphdvr_lut_create(sphdvr_ctx* ctx, int kernel, int K, int D, int n_lambda, const double* theta,
+                                const double* pieces, sphdvr_lut** out) {
+  if (!ctx || !out) return SPHDVR_EINVAL;
+  *out = nullptr;
+  if (kernel < 0 || kernel > 3 || K < 1 || K > 4 || D < 1 || D > 6 || n_lambda < 2 || n_lambda > 65536 || !theta ||
+      !pieces)
+    return set_err(ctx, SPHDVR_EINVAL, "lut_create: bad arguments (K in [1,4], D in [1,6], n_lambda in [2,65536])");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  const int m = (K + 1) / 2;
+  std::vector<float> th(2 * (size_t)n_lambda, 0.f), jump, pc;
+  for (int j = 0; j < n_lambda; ++j) {
+    const double* T = theta + (size_t)j * m;
+    for (int k = 0; k < m; ++k) {
+      if (!std::isfinite(T[k]) || T[k] < 0 || (k && T[k] < T[k - 1]))
+        return set_err(ctx, SPHDVR_EINVAL, "lut_create: knots must be finite, >= 0 and non-decreasing");
+    }
+    th[2 * j] = (float)T[0];
+    th[2 * j + 1] = (float)(m > 1 ? T[1] : T[0]);
+  }
+  if (!difference_tables(K, D, n_lambda, theta, pieces, jump, pc))
+    return set_err(ctx, SPHDVR_EINVAL, "lut_create: non-finite piece coefficient");
   sphdvr_lut* L = new (std::nothrow) sphdvr_lut();
   if (!L) return set_err(ctx, SPHDVR_ENOMEM, "lut_create: host allocation");
   L->ctx = ctx;
@@ -435,12 +468,61 @@ sphdvr_status sphdvr_lut_create(sphdvr_ctx* ctx, int kernel, int K, int D, int n
   return SPHDVR_OK;
 }
 
+sphdvr_status sphdvr_lut_build_grad(int kernel, int K, int D, int n_lambda, const double* theta, double* gpieces,
+                                    double* gerr) {
+  if (kernel < 0 || kernel > 3 || K < 1 || K > 4 || D < 1 || D > 6 || n_lambda < 2 || n_lambda > 65536 || !theta ||
+      !gpieces)
+    return SPHDVR_EINVAL;
+  const int m = (K + 1) / 2;
+  for (int64_t i = 0; i < (int64_t)n_lambda * m; ++i)
+    if (!std::isfinite(theta[i]) || theta[i] < 0) return SPHDVR_EINVAL;
+  return build_grad_host(kernel, K, D, n_lambda, theta, gpieces, gerr) == 0 ? SPHDVR_OK : SPHDVR_EINVAL;
+}
+
+sphdvr_status sphdvr_lut_set_gradient(sphdvr_lut* L, const double* theta, const double* gpieces) {
+  if (!L || !theta || !gpieces) return SPHDVR_EINVAL;
+  sphdvr_ctx* ctx = L->ctx;
+  const DevLut& d = L->d;
+  std::vector<float> jump, pc;
+  if (!difference_tables(d.K, d.D, d.n_lambda, theta, gpieces, jump, pc))
+    return set_err(ctx, SPHDVR_EINVAL, "lut_set_gradient: non-finite piece coefficient");
+  // the knots must be the table's own (the gradient shares them)
+  std::vector<float> th(2 * (size_t)d.n_lambda);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaMemcpy(th.data(), d.theta, th.size() * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "lut_set_gradient: table knots");
+  const int m = d.m;
+  for (int j = 0; j < d.n_lambda; ++j)
+    if (th[2 * j] != (float)theta[(size_t)j * m] || (m > 1 && th[2 * j + 1] != (float)theta[(size_t)j * m + 1]))
+      return set_err(ctx, SPHDVR_EINVAL, "lut_set_gradient: knots differ from the table's");
+  float *gj = nullptr, *gp = nullptr;
+  sphdvr_status s;
+  if ((s = dev_alloc(ctx, (void**)&gj, jump.size() * sizeof(float))) != SPHDVR_OK) return s;
+  if ((s = dev_alloc(ctx, (void**)&gp, pc.size() * sizeof(float))) != SPHDVR_OK) {
+    cudaFree(gj);
+    return s;
+  }
+  if ((e = cudaMemcpy(gj, jump.data(), jump.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(gp, pc.data(), pc.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(gj);
+    cudaFree(gp);
+    return cuda_err(ctx, e, "lut_set_gradient: upload");
+  }
+  cudaFree(L->d.gjump);
+  cudaFree(L->d.gpiece);
+  L->d.gjump = gj;
+  L->d.gpiece = gp;
+  return SPHDVR_OK;
+}
+
 sphdvr_status sphdvr_lut_free(sphdvr_lut* L) {
   if (!L) return SPHDVR_EINVAL;
   if (L->ctx) cudaSetDevice(L->ctx->device);
   cudaFree(L->d.theta);
   cudaFree(L->d.jump);
   cudaFree(L->d.piece);
+  cudaFree(L->d.gjump);
+  cudaFree(L->d.gpiece);
   delete L;
   return SPHDVR_OK;
 }
@@ -531,6 +613,8 @@ static sphdvr_status do_render(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const 
   sphdvr_status s = check_common(ctx, ds, lut);
   if (s != SPHDVR_OK) return s;
   if ((s = check_opts(ctx, opts)) != SPHDVR_OK) return s;
+  if (opts && opts->shading && !(lut->d.gjump && lut->d.gpiece))
+    return set_err(ctx, SPHDVR_EINVAL, "render: shading needs a table with a gradient (sphdvr_lut_set_gradient)");
   RenderArgs a = base ? *base : RenderArgs();
   a.ds = ds;
   a.lut = &lut->d;
@@ -569,7 +653,8 @@ sphdvr_status sphdvr_render_batch(sphdvr_ctx* ctx, const sphdvr_dataset* ds, con
   if (!cams || !rgba_out) return set_err(ctx, SPHDVR_EINVAL, "render_batch: NULL argument");
   sphdvr_status s = check_common(ctx, ds, lut);
   if (s != SPHDVR_OK) return s;
-  if ((s = check_opts(ctx, opts)) != SPHDVR_OK) return s;
+  if ((s = check_opts(ctx, opts)) != SPHDVR_OK || (s = reject_shading(ctx, opts, "render_batch")) != SPHDVR_OK)
+    return s;
   std::vector<float4> tfh;
   if ((s = pack_tf(ctx, tf, tfh)) != SPHDVR_OK) return s;
   RenderArgs a[SPHDVR_MAX_BATCH];
@@ -602,7 +687,8 @@ sphdvr_status sphdvr_render_scatter(sphdvr_ctx* ctx, const sphdvr_dataset* ds, c
   if (!rgba_out) return set_err(ctx, SPHDVR_EINVAL, "render_scatter: rgba_out is NULL");
   sphdvr_status s = check_common(ctx, ds, lut);
   if (s != SPHDVR_OK) return s;
-  if ((s = check_opts(ctx, opts)) != SPHDVR_OK) return s;
+  if ((s = check_opts(ctx, opts)) != SPHDVR_OK || (s = reject_shading(ctx, opts, "render_scatter")) != SPHDVR_OK)
+    return s;
   RenderArgs a{};
   a.ds = ds;
   a.lut = &lut->d;
@@ -683,10 +769,10 @@ sphdvr_status sphdvr_phase_times(sphdvr_ctx* ctx, int64_t out[16]) {
 }
 #endif
 
-sphdvr_status sphdvr_debug_rays(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+static sphdvr_status debug_rays(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
                                 const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
                                 int n_pix, const int* pix, float* rgba, int64_t* counts, int64_t* cand_ids,
-                                int cand_cap, double* field, int field_cap) {
+                                int cand_cap, double* field, double* grad, int field_cap) {
   if (!ctx) return SPHDVR_EINVAL;
   if (n_pix < 1 || !pix || !rgba || !counts || !cam) return set_err(ctx, SPHDVR_EINVAL, "debug_rays: bad arguments");
   if ((cand_ids && cand_cap < 1) || (field && field_cap < 1)) return set_err(ctx, SPHDVR_EINVAL, "debug_rays: capacity < 1");
@@ -703,6 +789,8 @@ sphdvr_status sphdvr_debug_rays(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const
   if (cand_ids && (s = ensure(ctx, ctx->dbg_cands, (size_t)n_pix * cand_cap * sizeof(int64_t))) != SPHDVR_OK) return s;
   if (field && (s = ensure(ctx, ctx->dbg_field, (size_t)n_pix * field_cap * (D + 3) * sizeof(double))) != SPHDVR_OK)
     return s;
+  const size_t grad_doubles = (size_t)n_pix * field_cap * 3 * (D + 1);
+  if (grad && (s = ensure(ctx, ctx->dbg_grad, grad_doubles * sizeof(double))) != SPHDVR_OK) return s;
   cudaStream_t st = nullptr;
   cudaError_t e = cudaMemcpy(ctx->dbg_pix.p, pix, n_pix * sizeof(int), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_err(ctx, e, "debug upload");
@@ -714,7 +802,12 @@ sphdvr_status sphdvr_debug_rays(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const
   a.dbg_cands = cand_ids ? (long long*)ctx->dbg_cands.p : nullptr;
   a.cand_cap = cand_ids ? cand_cap : 0;
   a.dbg_field = field ? (double*)ctx->dbg_field.p : nullptr;
-  a.field_cap = field ? field_cap : 0;
+  a.field_cap = (field || grad) ? field_cap : 0;
+  a.dbg_grad = grad ? (double*)ctx->dbg_grad.p : nullptr;
+  if (grad && !field) {  // the kernel writes gradient rows beside field rows
+    if ((s = ensure(ctx, ctx->dbg_field, (size_t)n_pix * field_cap * (D + 3) * sizeof(double))) != SPHDVR_OK) return s;
+    a.dbg_field = (double*)ctx->dbg_field.p;
+  }
   s = do_render(ctx, ds, lut, cam, tf, opts, nullptr, st, &a);
   if (s != SPHDVR_OK) return s;
   if ((e = cudaMemcpy(rgba, ctx->dbg_rgba.p, n_pix * 4 * sizeof(float), cudaMemcpyDeviceToHost)) != cudaSuccess ||
@@ -727,13 +820,33 @@ sphdvr_status sphdvr_debug_rays(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const
   if (field && (e = cudaMemcpy(field, ctx->dbg_field.p, (size_t)n_pix * field_cap * (D + 3) * sizeof(double),
                                cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_err(ctx, e, "debug download");
+  if (grad && (e = cudaMemcpy(grad, ctx->dbg_grad.p, grad_doubles * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_err(ctx, e, "debug download");
   bool over = false;
   for (int i = 0; i < n_pix; ++i) {
     if (cand_ids && counts[8 * i] > cand_cap) over = true;
-    if (field && counts[8 * i + 2] > field_cap) over = true;
+    if ((field || grad) && counts[8 * i + 2] > field_cap) over = true;
     if (counts[8 * i + 3]) over = true;
   }
   return over ? set_err(ctx, SPHDVR_EOVERFLOW, "debug_rays: a capacity or per-ray buffer was exceeded") : SPHDVR_OK;
+}
+
+sphdvr_status sphdvr_debug_rays(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+                                const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
+                                int n_pix, const int* pix, float* rgba, int64_t* counts, int64_t* cand_ids,
+                                int cand_cap, double* field, int field_cap) {
+  return debug_rays(ctx, ds, lut, cam, tf, opts, n_pix, pix, rgba, counts, cand_ids, cand_cap, field, nullptr,
+                    field_cap);
+}
+
+sphdvr_status sphdvr_debug_rays_grad(sphdvr_ctx* ctx, const sphdvr_dataset* ds, const sphdvr_lut* lut,
+                                     const sphdvr_camera* cam, const sphdvr_tf* tf, const sphdvr_render_opts* opts,
+                                     int n_pix, const int* pix, float* rgba, int64_t* counts, double* field,
+                                     double* grad, int field_cap) {
+  if (!ctx) return SPHDVR_EINVAL;
+  if (!opts || !opts->shading) return set_err(ctx, SPHDVR_EINVAL, "debug_rays_grad: opts->shading must be 1");
+  if (grad && field_cap < 1) return set_err(ctx, SPHDVR_EINVAL, "debug_rays: capacity < 1");
+  return debug_rays(ctx, ds, lut, cam, tf, opts, n_pix, pix, rgba, counts, nullptr, 0, field, grad, field_cap);
 }
 
 }  // extern "C"

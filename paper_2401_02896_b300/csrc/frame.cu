@@ -175,8 +175,9 @@ SPHDVR_DECL(5)
 SPHDVR_DECL(6)
 #undef SPHDVR_DECL
 
-// The render kernel of a precision mode.
+// The render kernel of a precision mode (and of shaded rendering).
 static int kernel_kind(const sphdvr_render_opts* o) {
+  if (o && o->shading) return kKernRaySh;
   switch (o ? o->precision : SPHDVR_PREC_FP32_ANCHORED) {
     case SPHDVR_PREC_FP64_NAIVE: return kKernF64;
     case SPHDVR_PREC_FP32_REINIT: return kKernReinit;
@@ -187,9 +188,10 @@ static int kernel_kind(const sphdvr_render_opts* o) {
 
 // Dynamic shared memory of a render launch.
 static size_t kernel_smem(int kind, int tf_n, bool dbg) {
-  if (kind == kKernRayFB) return ray_smem_bytes(tf_n, 1, true);
-  const int nw = dbg ? 1 : (kind == kKernRay ? kRayWarps : kRenderWarps);
-  return kind == kKernRay ? ray_smem_bytes(tf_n, nw, dbg) : render_smem_bytes(tf_n, nw);
+  if (kind == kKernRayFB || kind == kKernRayShFB) return ray_smem_bytes(tf_n, 1, true, kind == kKernRayShFB);
+  const bool ray = kind == kKernRay || kind == kKernRaySh;
+  const int nw = dbg ? 1 : (ray ? kRayWarps : kRenderWarps);
+  return ray ? ray_smem_bytes(tf_n, nw, dbg, kind == kKernRaySh) : render_smem_bytes(tf_n, nw);
 }
 
 static sphdvr_status dispatch_render(sphdvr_ctx* ctx, int D, int kind, bool dbg, bool batch, const RenderParams& p,
@@ -225,6 +227,7 @@ static int grid_for_items(sphdvr_ctx* ctx, const RenderArgs& a, int64_t items) {
   const int kind = kernel_kind(a.opts);
   const size_t smem = kernel_smem(kind, a.tf_n, dbg);
   int nb = render_occupancy(a.lut->D, kind, dbg, smem);
+  if (!dbg && a.opts && a.opts->ctas_per_sm > 0) nb = std::min(nb, a.opts->ctas_per_sm);
   if (ctx->num_sms <= 0) {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -246,13 +249,14 @@ int render_grid_batch(sphdvr_ctx* ctx, const RenderArgs* a, int n) {
   return grid_for_items(ctx, a[0], (rays + kRenderWarps - 1) / kRenderWarps);
 }
 
-size_t render_table_floats(int grid, bool dbg) {
+size_t render_table_floats(int grid, bool dbg, bool shaded) {
   static_assert(kRayWarps == kRenderWarps, "both render kernels run the same warps per CTA");
   // the parity hook runs k_ray with the fallback's larger per-ray capacities
-  return (size_t)grid * (dbg ? 1 : kRenderWarps) * (size_t)std::max(kTableWords, dbg ? kRayWordsBig : kRayWords);
+  const int ray = shaded ? (dbg ? kRayWordsBigGR : kRayWordsGR) : (dbg ? kRayWordsBig : kRayWords);
+  return (size_t)grid * (dbg ? 1 : kRenderWarps) * (size_t)std::max(kTableWords, ray);
 }
 
-size_t fallback_floats(int warps) { return (size_t)warps * kRayWordsBig; }
+size_t fallback_floats(int warps, bool shaded) { return (size_t)warps * (shaded ? kRayWordsBigGR : kRayWordsBig); }
 
 // warps of the fallback pass (one per SM)
 static int fallback_warps(sphdvr_ctx* ctx) {
@@ -308,9 +312,9 @@ static size_t shared_fixed_bytes(const RenderArgs& a, int grid, int n, int ctx_f
   const size_t nc = a.ds->n_chunks;
   return nc * (sizeof(unsigned) + 2 * sizeof(uint32_t)) + 32 + 32 * sizeof(unsigned long long) +
          scan_tmp_words(nc) * sizeof(uint32_t) + (size_t)a.tf_n * sizeof(float4) +
-         render_table_floats(grid, a.n_dbg > 0) * sizeof(float) + 4 * sizeof(unsigned) +
+         render_table_floats(grid, a.n_dbg > 0, a.opts && a.opts->shading) * sizeof(float) + 4 * sizeof(unsigned) +
          (n > 1 ? (size_t)n * sizeof(RenderFrame) : 0) + (size_t)(kFallbackList + 1) * sizeof(unsigned) +
-         fallback_floats(ctx_fallback_warps) * sizeof(float);
+         fallback_floats(ctx_fallback_warps, a.opts && a.opts->shading) * sizeof(float);
 }
 
 size_t frame_fixed_bytes(sphdvr_ctx* ctx, const RenderArgs& a) {
@@ -339,9 +343,9 @@ static sphdvr_status shared_work(sphdvr_ctx* ctx, const RenderArgs& a, int grid,
       (s = ensure(ctx, ctx->stats, 32 * sizeof(unsigned long long))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->scan_tmp, scan_tmp_words(nc) * sizeof(uint32_t))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->tf, (size_t)a.tf_n * sizeof(float4))) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->table, render_table_floats(grid, a.n_dbg > 0) * sizeof(float))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->table, render_table_floats(grid, a.n_dbg > 0, a.opts && a.opts->shading) * sizeof(float))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->work, 4 * sizeof(unsigned))) != SPHDVR_OK ||
-      (s = ensure(ctx, ctx->fb_table, fallback_floats(fallback_warps(ctx)) * sizeof(float))) != SPHDVR_OK ||
+      (s = ensure(ctx, ctx->fb_table, fallback_floats(fallback_warps(ctx), a.opts && a.opts->shading) * sizeof(float))) != SPHDVR_OK ||
       (s = ensure(ctx, ctx->fb_list, (size_t)(kFallbackList + 1) * sizeof(unsigned))) != SPHDVR_OK)
     return s;
   w.fb_table = (float*)ctx->fb_table.p;
@@ -455,6 +459,10 @@ static void common_params(const RenderArgs& a, const FrameWork& w, RenderParams&
   p.theta = L->theta;
   p.jump = L->jump;
   p.piece = L->piece;
+  p.gjump = L->gjump;
+  p.gpiece = L->gpiece;
+  p.shade_ka = (a.opts && a.opts->shading) ? a.opts->shade_ka : 1.f;
+  p.shade_kd = (a.opts && a.opts->shading) ? a.opts->shade_kd : 0.f;
   p.tf_n = a.tf_n;
   p.tf_lo = a.tf_lo;
   p.tf_dv = (a.tf_hi - a.tf_lo) / (a.tf_n - 1);
@@ -464,6 +472,7 @@ static void common_params(const RenderArgs& a, const FrameWork& w, RenderParams&
   int prec = o ? o->precision : SPHDVR_PREC_FP32_ANCHORED;
   p.anchor_every = (prec == SPHDVR_PREC_FP32_ANCHORED) ? std::max(1, o ? o->anchor_every : 2) : 0;
   p.window_h = (o && o->window_h > 0.f) ? o->window_h : 1.0f;
+  p.window_fill = (o && o->window_fill > 0.f) ? o->window_fill : 0.85f;
   p.reinit_dt = (prec == SPHDVR_PREC_FP32_REINIT) ? o->reinit_dt : 0.f;
   const bool qt = prec == SPHDVR_PREC_INT64_QUANT;
   p.q_tau = qt ? o->quant_tau : 1.0;
@@ -496,7 +505,7 @@ static sphdvr_status clear_counters(sphdvr_ctx* ctx, const FrameWork& w, cudaStr
 static sphdvr_status launch_frame(sphdvr_ctx* ctx, const RenderArgs& a, const FrameWork& w, RenderParams p,
                                   bool batch, int grid, cudaStream_t st) {
   const int kind = kernel_kind(a.opts);
-  const bool fb = kind == kKernRay && w.fb_table && w.fb_list && w.fb_warps > 0;
+  const bool fb = (kind == kKernRay || kind == kKernRaySh) && w.fb_table && w.fb_list && w.fb_warps > 0;
   p.ray_cap = a.opts ? a.opts->ray_capacity : 0;
   p.ovf = fb ? w.fb_list : nullptr;
   p.ovf_cap = fb ? w.fb_cap : 0;
@@ -504,8 +513,8 @@ static sphdvr_status launch_frame(sphdvr_ctx* ctx, const RenderArgs& a, const Fr
       dispatch_render(ctx, a.lut->D, kind, false, batch, p, grid, kernel_smem(kind, a.tf_n, false), st);
   if (s != SPHDVR_OK || !fb) return s;
   p.scratch = w.fb_table;
-  return dispatch_render(ctx, a.lut->D, kKernRayFB, false, batch, p, w.fb_warps,
-                         kernel_smem(kKernRayFB, a.tf_n, false), st);
+  const int fk = kind == kKernRaySh ? kKernRayShFB : kKernRayFB;
+  return dispatch_render(ctx, a.lut->D, fk, false, batch, p, w.fb_warps, kernel_smem(fk, a.tf_n, false), st);
 }
 
 sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w, PairSizer sizer, void* user,
@@ -538,6 +547,7 @@ sphdvr_status render_frame_ws(sphdvr_ctx* ctx, const RenderArgs& a, FrameWork& w
   p.cand_cap = a.cand_cap;
   p.dbg_field = a.dbg_field;
   p.field_cap = a.field_cap;
+  p.dbg_grad = a.dbg_grad;
   const bool dbg = a.n_dbg > 0;
   const int kind = kernel_kind(a.opts);
   const int grid = std::min(render_grid(ctx, a), w.table_ctas);

@@ -54,6 +54,36 @@ ld kernel_value(int kernel, ld r) {
   }
 }
 
+// w'(r) / r of the kernels of kernel_value, in a form that is finite at r = 0:
+// the across-ray part of a particle's gradient on a ray is proportional to
+// G_L(s) = w'(rho) / rho, rho = sqrt(L^2 + s^2), even in s like B_L.
+ld kernel_slope_over_r(int kernel, ld r) {
+  r = std::fabs(r);
+  switch (kernel) {
+    case 0: {  // (-3 (2-r)^2 + 12 (1-r)^2) / r = 9r - 12 below 1, -3 (2-r)^2 / r above
+      if (r >= 2) return 0;
+      if (r < 1) return (9 * r - 12) / (4 * kPi);
+      ld a = 2 - r;
+      return -3 * a * a / (r * 4 * kPi);
+    }
+    case 1: {
+      if (r >= 2) return 0;
+      ld a = 1 - r / 2;
+      return (21.0L / 16.0L) / kPi * (-5) * a * a * a;
+    }
+    case 2: {
+      if (r >= 2) return 0;
+      ld a = 1 - r / 2, a2 = a * a;
+      return (495.0L / 256.0L) / kPi * (-7.0L / 3.0L) * (5 * r + 2) * a2 * a2 * a;
+    }
+    default: {
+      if (r >= 1) return 0;
+      ld a = 1 - r * r;
+      return (315.0L / 64.0L) / kPi * (-6) * a * a;
+    }
+  }
+}
+
 // 16-point Gauss-Legendre rule on [-1, 1].
 struct GL16 {
   ld x[16], w[16];
@@ -92,6 +122,7 @@ const GL16& gl16() {
 
 struct Problem {
   int kernel, K, D, m;
+  int target = 0;  // approximated function: 0 B_L, 1 G_L (gradient tables)
   ld q, lam, T;
   ld tbrk;  // s where r crosses an interior kernel break (M4: r = 1), or -1
   int nb;
@@ -112,7 +143,10 @@ struct Problem {
       }
   }
 
-  ld B(ld s) const { return kernel_value(kernel, std::sqrt(lam * lam + s * s)); }
+  ld B(ld s) const {
+    const ld rho = std::sqrt(lam * lam + s * s);
+    return target ? kernel_slope_over_r(kernel, rho) : kernel_value(kernel, rho);
+  }
 
   // Integrate f(s) over [a, b] within [0, T].  For L > 0 the substitution
   // s = L sinh(u) turns sqrt(L^2 + s^2) = L cosh(u) into an entire function,
@@ -644,6 +678,46 @@ int build_lut_host(int kernel, int K, int D, int n_lambda, double* theta, double
     if (err) err[j] = (double)std::sqrt(e2);
   }
   return 0;
+}
+
+// Gradient table: for every entry of a table (its knots theta), the optimal
+// approximation of G_L(s) = w'(rho) / rho on the entry's own knots -- the same
+// projection onto the basis A~_kd (Sec. 3.3) with G_L in place of B_L, so the
+// across-ray gradient of a ray is a piecewise polynomial with the field's
+// knots (the Conclusion: features additively generated from particle
+// contributions are approximated the same way).  gerr may be NULL.
+int build_grad_host(int kernel, int K, int D, int n_lambda, const double* theta, double* gpieces, double* gerr) {
+  if (kernel < 0 || kernel > 3 || K < 1 || K > 2 * kMaxM || D < 1 || D > kMaxD || n_lambda < 2 ||
+      n_lambda > 65536 || !theta || !gpieces)
+    return 1;
+  const int m = (K + 1) / 2;
+  const ld q = kernel == 3 ? 1 : 2;
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(| : bad)
+  for (int j = 0; j < n_lambda; ++j) {
+    double* p_o = gpieces + (size_t)j * m * (D + 1);
+    for (int k = 0; k < m * (D + 1); ++k) p_o[k] = 0;
+    if (gerr) gerr[j] = 0;
+    Problem P(kernel, K, D, q * j / (n_lambda - 1));
+    P.target = 1;
+    const double* th_i = theta + (size_t)j * m;
+    if (j == n_lambda - 1 || !(P.T > 0) || !(th_i[0] > 0)) continue;  // zero function (knots at 0)
+    ld th[kMaxM], coef[kMaxB], pc[kMaxM * (kMaxD + 1)];
+    for (int k = 0; k < m; ++k) th[k] = th_i[k];
+    if (P.nb == 0) {
+      if (gerr) gerr[j] = (double)std::sqrt(2 * P.integrate(0, P.T, [&](ld s) { ld b = P.B(s); return b * b; }));
+      continue;
+    }
+    const ld e2 = P.solve(th, coef);
+    if (!std::isfinite((double)e2)) {
+      bad = 1;
+      continue;
+    }
+    P.pieces(th, coef, pc);
+    for (int k = 0; k < m * (D + 1); ++k) p_o[k] = (double)pc[k];
+    if (gerr) gerr[j] = (double)std::sqrt(e2);
+  }
+  return bad;
 }
 
 }  // namespace sphdvr

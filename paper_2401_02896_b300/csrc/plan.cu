@@ -71,7 +71,7 @@ sphdvr_status sphdvr_frame_plan_create(sphdvr_ctx* ctx, const sphdvr_dataset* ds
   *out = nullptr;
   sphdvr_status s = check_common(ctx, ds, lut);
   if (s != SPHDVR_OK) return s;
-  if ((s = check_opts(ctx, opts)) != SPHDVR_OK) return s;
+  if ((s = check_opts(ctx, opts)) != SPHDVR_OK || (s = reject_shading(ctx, opts, "frame_plan")) != SPHDVR_OK) return s;
   if (max_width < 1 || max_height < 1 || max_width > 32768 || max_height > 32768)
     return set_err(ctx, SPHDVR_EINVAL, "frame_plan_create: max size out of [1, 32768]");
   if (pair_cap < 2 || pair_cap > 0x7fffffffLL)

@@ -38,9 +38,6 @@ namespace sphdvr {
 #ifndef SPHDVR_RAY_NK
 #define SPHDVR_RAY_NK 512
 #endif
-#ifndef SPHDVR_RAY_FILL
-#define SPHDVR_RAY_FILL 0.85f
-#endif
 #ifndef SPHDVR_RAY_U1
 #define SPHDVR_RAY_U1 1
 #endif
@@ -60,28 +57,36 @@ constexpr int kRayWcap = kRayNK - 64;  // knots composited per window
 // is abandoned there, listed, and rendered again by the fallback pass, whose
 // warps hold four times as many (the parity hook uses the larger capacities
 // too).  Capacity changes no arithmetic of a ray that fits it.
-template <bool BIG>
+// GR: the shaded (gradient) variant, whose records also hold the vector d
+// from the ray to the particle (3 more words per active and waiting particle).
+template <bool BIG, bool GR = false>
 struct RayCaps {
   static constexpr int WC = BIG ? 16384 : 4096;   // waiting slots
   static constexpr int ACT = BIG ? 16384 : 4096;  // active particles in all (beyond kRayAS in global memory)
-  // per-warp shared memory: active records (t_chi hi, t_chi lo, h, c, j | done << 16),
-  // the window / new-particle buffers (two key/value pairs of kRayNK entries), the sort
-  // histogram (+ scratch words), the started bits of the waiting slots
-  static constexpr int SMEM = kRayAS * 20 + 4 * kRayNK * 4 + (256 + 32) * 4 + (WC / 32) * 4;
+  // per-warp shared memory: active records (t_chi hi, t_chi lo, h, c, j | done << 16
+  // [, d_x, d_y, d_z]), the window / new-particle buffers (two key/value pairs of
+  // kRayNK entries), the sort histogram (+ scratch words), the started bits of the waiting slots
+  static constexpr int SMEM = kRayAS * (GR ? 32 : 20) + 4 * kRayNK * 4 + (256 + 32) * 4 + (WC / 32) * 4;
   // per-warp global scratch (32-bit words): slot records (float4), slot table
   // entries, free stack, slot -> active index map, two waiting-list buffers
-  // (key, slot), the active extension (5 arrays)
-  static constexpr int WORDS = 4 * WC + 3 * WC + 4 * WC + 5 * (ACT - kRayAS);
+  // (key, slot), the active extension (5 arrays) [, slot d (float4), the
+  // active extension's d (3 arrays)]
+  static constexpr int WORDS =
+      4 * WC + 3 * WC + 4 * WC + 5 * (ACT - kRayAS) + (GR ? 4 * WC + 3 * (ACT - kRayAS) : 0);
   static_assert(WORDS % 4 == 0, "per-warp scratch keeps float4 alignment");
 };
 static_assert(kRayAS % 32 == 0, "the shared part of the active set is a whole number of lane groups");
 static_assert(kRayNK >= 256 && kRayNK <= 512 && kRayNK % 32 == 0, "the window sort and merge take 256..512 entries");
 constexpr int kRayWords = RayCaps<false>::WORDS;     // per warp of the frame pass
 constexpr int kRayWordsBig = RayCaps<true>::WORDS;   // per warp of the fallback pass and the parity hook
+constexpr int kRayWordsGR = RayCaps<false, true>::WORDS;    // the same, shaded variant
+constexpr int kRayWordsBigGR = RayCaps<true, true>::WORDS;
 constexpr int kRayFlagRefit = 32;  // frame flag: a ray overflowed the fallback's capacities too (image wrong)
 
-inline size_t ray_smem_bytes(int tf_n, int nw, bool big) {
-  return sizeof(float4) * tf_n + (size_t)(big ? RayCaps<true>::SMEM : RayCaps<false>::SMEM) * nw;
+inline size_t ray_smem_bytes(int tf_n, int nw, bool big, bool gr = false) {
+  const int per = gr ? (big ? RayCaps<true, true>::SMEM : RayCaps<false, true>::SMEM)
+                     : (big ? RayCaps<true>::SMEM : RayCaps<false>::SMEM);
+  return sizeof(float4) * tf_n + (size_t)per * nw;
 }
 
 // Active set: index i < kRayAS in shared memory, else at i - kRayAS in global memory.
@@ -90,6 +95,7 @@ struct ActSet {
   int* jk;  // table entry (bits 0..15) | knots processed (bits 16..19)
   float *gth, *gtl, *gh, *gc;
   int* gjk;
+  float *dx, *dy, *dz, *gdx, *gdy, *gdz;  // shaded variant: the vector from the ray to the particle
 };
 
 __device__ __forceinline__ void act_get(const ActSet& A, int i, float4& r, int& jk) {
@@ -119,6 +125,76 @@ __device__ __forceinline__ void act_put(const ActSet& A, int i, float4 r, int jk
   }
 }
 __device__ __forceinline__ int* act_jk_ptr(const ActSet& A, int i) { return i < kRayAS ? A.jk + i : A.gjk + (i - kRayAS); }
+__device__ __forceinline__ float3 act_getd(const ActSet& A, int i) {
+  if (i < kRayAS) return make_float3(A.dx[i], A.dy[i], A.dz[i]);
+  const int g = i - kRayAS;
+  return make_float3(A.gdx[g], A.gdy[g], A.gdz[g]);
+}
+__device__ __forceinline__ void act_putd(const ActSet& A, int i, float3 d) {
+  if (i < kRayAS) {
+    A.dx[i] = d.x;
+    A.dy[i] = d.y;
+    A.dz[i] = d.z;
+  } else {
+    const int g = i - kRayAS;
+    A.gdx[g] = d.x;
+    A.gdy[g] = d.y;
+    A.gdz[g] = d.z;
+  }
+}
+
+// Localized difference coefficients, orders 1..D, of sorted knot k of a
+// particle with table entry j, smoothing length h and amplitude c, from table
+// `tab` (the field's difference coefficients, or the gradient's; Sec. 2,
+// Sec. 3.1); mirrored knots take (-1)^(d+1).
+template <int D>
+__device__ __forceinline__ void knot_delta_tab(const float* tab, int K, int m, int j, float h, float c, int k,
+                                               float* dl) {
+  bool mir;
+  const int slot = knot_slot(K, m, k, mir);
+  const float* jr = tab + (size_t)j * 3 * D + slot * D;
+  const float ih = __fdividef(1.f, h);
+  float s = c;
+#pragma unroll
+  for (int d = 1; d <= D; ++d) {
+    s *= ih;
+    const float v = __ldg(jr + d - 1) * s;
+    dl[d - 1] = (mir && !(d & 1)) ? -v : v;
+  }
+}
+
+// Exact coefficients at Ta of a particle's own piece after its first kn knots,
+// from piece table `tab` with amplitude c (the anchor of a window).
+template <int D>
+__device__ __forceinline__ void entry_piece_at_tab(const float* tab, int K, int m, float4 E, float c, float2 th,
+                                                   int j, int kn, df Ta, float* A) {
+  const int pc = kn - 1;
+  int kp;
+  float sg;
+  if (!(K & 1)) {
+    if (pc < m) { kp = m - pc; sg = -1.f; } else { kp = pc - m + 1; sg = 1.f; }
+  } else {
+    if (pc < m - 1) { kp = m - pc; sg = -1.f; }
+    else if (pc == m - 1) { kp = 1; sg = 1.f; }
+    else { kp = pc - m + 2; sg = 1.f; }
+  }
+  const float th0 = kp == 1 ? 0.f : th.x;
+  const float h = E.z, ih = __fdividef(1.f, h);
+  const float rel = (Ta.hi - E.x) + (Ta.lo - E.y);
+  const float z = sg * rel * ih - th0;
+  const float* pr = tab + (size_t)j * 2 * (D + 1) + (kp - 1) * (D + 1);
+  float q[D + 1];
+#pragma unroll
+  for (int d = 0; d <= D; ++d) q[d] = __ldg(pr + d);
+  taylor_shift<D, float>(q, z);
+  float s = c;
+  const float f = sg * ih;
+#pragma unroll
+  for (int d = 0; d <= D; ++d) {
+    A[d] = q[d] * s;
+    s *= f;
+  }
+}
 
 // Normalised offsets of a particle's knots 0..K in sorted order (Sec. 3.1: the
 // table's positive knots theta_1, theta_2 mirrored, with a middle knot at 0
@@ -151,10 +227,15 @@ __device__ __forceinline__ int warp_excl_scan(int v, int* total) {
 
 // FB: the fallback pass -- its rays are those the frame pass listed in
 // p.ovf; it and the parity hook (DBG) hold the larger capacities.
-template <int D, int NW, bool DBG, bool BT, bool FB = false>
-__global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)) k_ray(RenderParams p) {
+// GR: shaded rendering -- besides the field, the across-ray gradient's three
+// components are carried through the same knots (channels 1..3 of every
+// polynomial), and the emission is shaded (Conclusion: additive features).
+template <int D, int NW, bool DBG, bool BT, bool FB = false, bool GR = false>
+__global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? (GR ? 1 : kRayMinBlocks) : 1)) k_ray(RenderParams p) {
   constexpr bool BIG = DBG || FB;
-  constexpr int WCX = RayCaps<BIG>::WC, ACTX = RayCaps<BIG>::ACT;
+  constexpr int NC = GR ? 4 : 1;  // polynomial channels: the field [, the across-ray gradient x, y, z]
+  constexpr int NP = NC * (D + 1);
+  constexpr int WCX = RayCaps<BIG, GR>::WC, ACTX = RayCaps<BIG, GR>::ACT;
   // capacities in force (the frame pass may be given smaller ones, to test the fallback)
   const int cap_wc = (!BIG && p.ray_cap > 0) ? min(p.ray_cap, WCX) : WCX;
   const int cap_act = (!BIG && p.ray_cap > 0) ? min(p.ray_cap, ACTX) : ACTX;
@@ -166,21 +247,28 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
   int *nv0, *nv1, *wv0, *wv1, *rh, *s_j, *s_fre, *s_map;
   unsigned* stb;
   float4* s_rec;
+  float4* s_dp = nullptr;  // shaded variant: slot d (the vector from the ray to the particle)
   {
-    unsigned char* b = smem + sizeof(float4) * p.tf_n + (size_t)RayCaps<BIG>::SMEM * wid;
+    unsigned char* b = smem + sizeof(float4) * p.tf_n + (size_t)RayCaps<BIG, GR>::SMEM * wid;
     A.th = (float*)b;
     A.tl = A.th + kRayAS;
     A.h = A.tl + kRayAS;
     A.c = A.h + kRayAS;
     A.jk = (int*)(A.c + kRayAS);
     float* w = (float*)(A.jk + kRayAS);
+    if (GR) {
+      A.dx = w;
+      A.dy = w + kRayAS;
+      A.dz = w + 2 * kRayAS;
+      w += 3 * kRayAS;
+    }
     nk0 = w;
     nv0 = (int*)(w + kRayNK);
     nk1 = w + 2 * kRayNK;
     nv1 = (int*)(w + 3 * kRayNK);
     rh = (int*)(w + 4 * kRayNK);
     stb = (unsigned*)(rh + 256 + 32);
-    float* g = p.scratch + (size_t)(blockIdx.x * NW + wid) * RayCaps<BIG>::WORDS;
+    float* g = p.scratch + (size_t)(blockIdx.x * NW + wid) * RayCaps<BIG, GR>::WORDS;
     s_rec = (float4*)g;
     s_j = (int*)(g + 4 * WCX);
     s_fre = s_j + WCX;
@@ -197,6 +285,13 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
     A.gh = o + 2 * OC;
     A.gc = o + 3 * OC;
     A.gjk = (int*)(o + 4 * OC);
+    if (GR) {
+      s_dp = (float4*)(o + 5 * OC);
+      float* gd = o + 5 * OC + 4 * WCX;
+      A.gdx = gd;
+      A.gdy = gd + OC;
+      A.gdz = gd + 2 * OC;
+    }
   }
   for (int i = threadIdx.x; i < p.tf_n; i += blockDim.x) s_tf[i] = p.tf[i];
   __syncthreads();
@@ -216,7 +311,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
   const float kInf = __int_as_float(0x7f800000);
   // aim a window at this many knots from the knot density of the previous one
   constexpr int kWcap = kRayWcap;
-  const float kTarget = SPHDVR_RAY_FILL * (float)kWcap;
+  const float kTarget = p.window_fill < 1.f ? p.window_fill * (float)kWcap : __int_as_float(0x7f800000);
 
   for (int it = 0;; ++it) {
     // ------------------------------------------------------------ work item
@@ -296,9 +391,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
     bool done = false, started = false;
     df Ta = {0.f, 0.f}, t_start = {0.f, 0.f};
     float tau_ray = 0.f, col[3] = {0.f, 0.f, 0.f};
-    float carry[D + 1];
+    float carry[NP];  // the polynomials at the end of the previous window (channel c at c * (D + 1))
 #pragma unroll
-    for (int d = 0; d <= D; ++d) carry[d] = 0.f;
+    for (int i = 0; i < NP; ++i) carry[i] = 0.f;
     // slots: hwm used so far, nfree on the free stack; active set [0, nal),
     // n_act of them not finished; waiting list [whead, nwait) of buffer wb;
     // nnk new particles in the batch
@@ -440,7 +535,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
 #pragma unroll
                 for (int d = 0; d <= D; ++d) z0.c[d] = 0.f;
                 const Acc g = composite_piece_v<D>(z0, L, tfc, Acc{0.f, 0.f, 0.f, 0.f});
-                float w = __expf(-tau_ray);
+                // a zero field has a zero gradient: shading ka + kd there
+                float w = __expf(-tau_ray) * (GR ? p.shade_ka + p.shade_kd : 1.f);
                 col[0] += w * g.r;
                 col[1] += w * g.g;
                 col[2] += w * g.b;
@@ -461,7 +557,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
             fresh = true;
             h_fresh = E0.z;
 #pragma unroll
-            for (int d = 0; d <= D; ++d) carry[d] = 0.f;
+            for (int i = 0; i < NP; ++i) carry[i] = 0.f;
           }
           // window end U (relative to Ta): the bound F; gamma times the
           // smallest h of the active set (at a restart: of the particle
@@ -495,9 +591,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
           // in the same pass the anchor (every anchor_every-th window) and the
           // compaction of the active set (finished particles leave)
           const bool do_anchor = !fresh && p.anchor_every > 0 && (win_count % p.anchor_every) == 0;
-          float acc[D + 1];
+          float acc[NP];
 #pragma unroll
-          for (int d = 0; d <= D; ++d) acc[d] = 0.f;
+          for (int i = 0; i < NP; ++i) acc[i] = 0.f;
           float cap2 = kInf, hmin_new = kInf;
           int T_all = 0;
 #pragma unroll 1
@@ -510,20 +606,36 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
               const bool valid = i < nal;
               float4 E = make_float4(0.f, 0.f, 1.f, 0.f);
               int jk = 0;
-              if (valid) act_get(A, i, E, jk);
+              float3 dp = make_float3(0.f, 0.f, 0.f);
+              if (valid) {
+                act_get(A, i, E, jk);
+                if (GR) dp = act_getd(A, i);
+              }
               const int kd = (jk >> 16) & 15, j = jk & 0xffff;
               const bool keep = valid && kd <= K;
               int ne = 0;
               float uk[5];  // the particle's knots relative to Ta (branch-free, fully unrolled)
               if (keep) {
+                const float2 th = __ldg(p.theta + j);
                 if (gen == 0 && do_anchor) {
                   float Ae[D + 1];
                   entry_piece_at<D>(p, E, j, kd, Ta, Ae);
 #pragma unroll
                   for (int d = 0; d <= D; ++d) acc[d] += Ae[d];
+                  if (GR) {
+                    // the across-ray gradient's own pieces: amplitude -c d / h^2
+                    const float gsc = -__fdividef(E.w, E.z * E.z);
+                    const float dc[3] = {dp.x, dp.y, dp.z};
+#pragma unroll
+                    for (int ch = 1; ch < NC; ++ch) {
+                      entry_piece_at_tab<D>(p.gpiece, K, m, E, gsc * dc[ch - 1], th, j, kd, Ta, Ae);
+#pragma unroll
+                      for (int d = 0; d <= D; ++d) acc[ch * (D + 1) + d] += Ae[d];
+                    }
+                  }
                 }
                 float sg[5];
-                knot_sigmas(K, __ldg(p.theta + j), sg);
+                knot_sigmas(K, th, sg);
                 const float base = (E.x - Ta.hi) + (E.y - Ta.lo);
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
@@ -547,7 +659,10 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
               if (gen == 0) {
                 __syncwarp();
                 if (keep) {
-                  if (ni != i) act_put(A, ni, E, jk);
+                  if (ni != i) {
+                    act_put(A, ni, E, jk);
+                    if (GR) act_putd(A, ni, dp);
+                  }
                   hmin_new = fminf(hmin_new, E.z);
                 }
                 wr += __popc(km);
@@ -605,9 +720,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
           PT_END(4)
           PT_BEGIN
           cap2 = warp_min(cap2);
-          float Aw[D + 1];  // the field's coefficients at the window start
+          float Aw[NP];  // the polynomials' coefficients at the window start
 #pragma unroll
-          for (int d = 0; d <= D; ++d) Aw[d] = do_anchor ? warp_sum(acc[d]) : (fresh ? 0.f : carry[d]);
+          for (int i = 0; i < NP; ++i) Aw[i] = do_anchor ? warp_sum(acc[i]) : (fresh ? 0.f : carry[i]);
           __syncwarp();
           // sort by position (ties: by id)
           const int rb = warp_bucket_sort(nk0, nv0, nk1, nv1, T_all, rh);
@@ -645,17 +760,23 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
           // every window knot lies below U (and below the window end), so only
           // the start needs clamping
           auto uat = [&](int i) -> float { return fmaxf(GK[i], 0.f); };
-          // difference coefficients of window knot i (Sec. 2, Sec. 3.1)
+          // difference coefficients of window knot i (Sec. 2, Sec. 3.1), orders
+          // 1..D of every channel: dl[ch * D + d - 1]
           auto deltas = [&](int i, float* dl) {
             const int vv = GV[i];
             const int k = vv & 7;
             float h, c;
             int j;
+            float3 dp = make_float3(0.f, 0.f, 0.f);
             if (vv & 8) {
               const float4 E = s_rec[vv >> 4];
               h = E.z;
               c = E.w;
               j = s_j[vv >> 4];
+              if (GR) {
+                const float4 d4 = s_dp[vv >> 4];
+                dp = make_float3(d4.x, d4.y, d4.z);
+              }
             } else {
               const int idx = vv >> 4;
               float4 E;
@@ -664,26 +785,41 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
               h = E.z;
               c = E.w;
               j = jk & 0xffff;
+              if (GR) dp = act_getd(A, idx);
             }
             knot_delta<D>(p, j, h, c, k, dl);
+            if (GR) {
+              // the across-ray gradient: amplitude -c d / h^2 on the gradient table
+              const float gsc = -__fdividef(c, h * h);
+              const float dc[3] = {dp.x, dp.y, dp.z};
+#pragma unroll
+              for (int ch = 1; ch < NC; ++ch) knot_delta_tab<D>(p.gjump, K, m, j, h, gsc * dc[ch - 1], k, dl + ch * D);
+            }
+          };
+          // every channel of a polynomial array shifted by s
+          auto shift_all = [&](float* q, float sft) {
+#pragma unroll
+            for (int ch = 0; ch < NC; ++ch) taylor_shift<D, float>(q + ch * (D + 1), sft);
           };
           const float ufirst = has ? uat(i0) : 0.f;
-          float P[D + 1];
+          float P[NP];
           float Uend;
           {
-            float agg[D + 1];
+            float agg[NP];
 #pragma unroll
-            for (int d = 0; d <= D; ++d) agg[d] = 0.f;
+            for (int q = 0; q < NP; ++q) agg[q] = 0.f;
             float ulast = ufirst;
             int nf = 0, nl = 0;  // the window's first and last knots of particles
 #pragma unroll kRayUnrollScan
             for (int i = i0; i < i1; ++i) {
               const float ur = uat(i);
-              if (i > i0) taylor_shift<D, float>(agg, ur - ulast);
-              float dl[D];
+              if (i > i0) shift_all(agg, ur - ulast);
+              float dl[NC * D];
               deltas(i, dl);
 #pragma unroll
-              for (int d = 1; d <= D; ++d) agg[d] += dl[d - 1];
+              for (int ch = 0; ch < NC; ++ch)
+#pragma unroll
+                for (int d = 1; d <= D; ++d) agg[ch * (D + 1) + d] += dl[ch * D + d - 1];
               ulast = ur;
               // mark the knot processed: a starter's first knot brings the
               // particle into the active set (its later knots in this window
@@ -698,6 +834,10 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
                 const float4 E = s_rec[e];
                 if (ni < cap_act) {
                   act_put(A, ni, E, s_j[e] | (1 << 16));
+                  if (GR) {
+                    const float4 d4 = s_dp[e];
+                    act_putd(A, ni, make_float3(d4.x, d4.y, d4.z));
+                  }
                   s_map[e] = ni;
                 } else {
                   s_map[e] = -1;
@@ -741,45 +881,45 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
             if (capped) ++r_capped;
             // inclusive warp scan of (agg, ulast, has):
             // (other, oe) (+) (mine, se) = (Shift(other, se - oe) + mine, se)
-            float sa[D + 1];
+            float sa[NP];
 #pragma unroll
-            for (int d = 0; d <= D; ++d) sa[d] = agg[d];
+            for (int q = 0; q < NP; ++q) sa[q] = agg[q];
             float se = ulast;
             int sh = has ? 1 : 0;
 #pragma unroll 1
             for (int o2 = 1; o2 < 32; o2 <<= 1) {
-              float oa[D + 1];
+              float oa[NP];
 #pragma unroll
-              for (int d = 0; d <= D; ++d) oa[d] = __shfl_up_sync(kFull, sa[d], o2);
+              for (int q = 0; q < NP; ++q) oa[q] = __shfl_up_sync(kFull, sa[q], o2);
               const float oe = __shfl_up_sync(kFull, se, o2);
               const int oh = __shfl_up_sync(kFull, sh, o2);
               if (lane >= o2 && oh) {
                 if (sh) {
-                  taylor_shift<D, float>(oa, se - oe);
+                  shift_all(oa, se - oe);
 #pragma unroll
-                  for (int d = 0; d <= D; ++d) sa[d] += oa[d];
+                  for (int q = 0; q < NP; ++q) sa[q] += oa[q];
                 } else {
 #pragma unroll
-                  for (int d = 0; d <= D; ++d) sa[d] = oa[d];
+                  for (int q = 0; q < NP; ++q) sa[q] = oa[q];
                   se = oe;
                   sh = 1;
                 }
               }
             }
-            // exclusive prefix: the field just before this lane's first knot
-            float pa[D + 1];
+            // exclusive prefix: the polynomials just before this lane's first knot
+            float pa[NP];
 #pragma unroll
-            for (int d = 0; d <= D; ++d) pa[d] = __shfl_up_sync(kFull, sa[d], 1);
+            for (int q = 0; q < NP; ++q) pa[q] = __shfl_up_sync(kFull, sa[q], 1);
             const float pe = __shfl_up_sync(kFull, se, 1);
             int ph = __shfl_up_sync(kFull, sh, 1);
             if (lane == 0) ph = 0;
 #pragma unroll
-            for (int d = 0; d <= D; ++d) P[d] = Aw[d];
-            taylor_shift<D, float>(P, ufirst);
+            for (int q = 0; q < NP; ++q) P[q] = Aw[q];
+            shift_all(P, ufirst);
             if (ph) {
-              taylor_shift<D, float>(pa, ufirst - pe);
+              shift_all(pa, ufirst - pe);
 #pragma unroll
-              for (int d = 0; d <= D; ++d) P[d] += pa[d];
+              for (int q = 0; q < NP; ++q) P[q] += pa[q];
             }
           }
           PT_END(7)
@@ -817,16 +957,16 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
           // memory around every piece)
 #pragma unroll kRayUnrollComp
           for (int i = (lane == 0 ? -1 : i0); i < i1; ++i) {
-            float Pc[D + 1], ua, ub;
+            float Pc[NP], ua, ub;
             if (i < 0) {
 #pragma unroll
-              for (int d = 0; d <= D; ++d) Pc[d] = Aw[d];
+              for (int q = 0; q < NP; ++q) Pc[q] = Aw[q];
               ua = 0.f;
               ub = nc > 0 ? uat(0) : Uend;
             } else {
               ua = uat(i);
-              if (i > i0) taylor_shift<D, float>(P, ua - lastu);
-              float dl[D];
+              if (i > i0) shift_all(P, ua - lastu);
+              float dl[NC * D];
               deltas(i, dl);
               {
                 // a starter's later knots in this window: count them on its new entry
@@ -837,16 +977,13 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
                 }
               }
 #pragma unroll
-              for (int d = 1; d <= D; ++d) P[d] += dl[d - 1];
+              for (int ch = 0; ch < NC; ++ch)
+#pragma unroll
+                for (int d = 1; d <= D; ++d) P[ch * (D + 1) + d] += dl[ch * D + d - 1];
               lastu = ua;
 #pragma unroll
-              for (int d = 0; d <= D; ++d) Pc[d] = P[d];
+              for (int q = 0; q < NP; ++q) Pc[q] = P[q];
               ub = i + 1 < nc ? uat(i + 1) : Uend;
-            }
-            const float a0 = fmaxf(ua, ystart);
-            if (ub > a0) {
-              if (a0 > ua) taylor_shift<D, float>(Pc, a0 - ua);
-              composite_piece_inl<D>(Pc, ub - a0, tfc, tau_l, col_l);
             }
             if (DBG && p.dbg_field && ub > ua) {
               const long long row = i < 0 ? dbg_np : dbg_base++;
@@ -854,8 +991,20 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
                 double* fo = p.dbg_field + ((size_t)dbg_row * p.field_cap + row) * (D + 3);
                 fo[0] = df_to_double(Ta) + (double)ua;
                 fo[1] = df_to_double(Ta) + (double)ub;
-                for (int d = 0; d <= D; ++d) fo[2 + d] = (double)(i < 0 ? Aw[d] : P[d]);
+                for (int d = 0; d <= D; ++d) fo[2 + d] = (double)Pc[d];
+                if (GR && p.dbg_grad) {
+                  double* go = p.dbg_grad + ((size_t)dbg_row * p.field_cap + row) * 3 * (D + 1);
+                  for (int q = 0; q < 3 * (D + 1); ++q) go[q] = (double)Pc[D + 1 + q];
+                }
               }
+            }
+            const float a0 = fmaxf(ua, ystart);
+            if (ub > a0) {
+              if (a0 > ua) shift_all(Pc, a0 - ua);
+              if (GR)
+                composite_piece_sh_inl<D>(Pc, Pc + D + 1, ub - a0, tfc, tau_l, col_l, p.shade_ka, p.shade_kd);
+              else
+                composite_piece_inl<D>(Pc, ub - a0, tfc, tau_l, col_l);
             }
           }
           if (DBG) dbg_np += npieces;
@@ -863,20 +1012,20 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
           PT_BEGIN
           // carry the polynomial to the window end (plain recurrence / next window)
           {
-            float cpy[D + 1];
+            float cpy[NP];
 #pragma unroll
-            for (int d = 0; d <= D; ++d) cpy[d] = P[d];
-            if (has) taylor_shift<D, float>(cpy, Uend - lastu);
+            for (int q = 0; q < NP; ++q) cpy[q] = P[q];
+            if (has) shift_all(cpy, Uend - lastu);
             const unsigned anym = __ballot_sync(kFull, has);
             if (anym) {
               const int lastlane = 31 - __clz(anym);
 #pragma unroll
-              for (int d = 0; d <= D; ++d) carry[d] = __shfl_sync(kFull, cpy[d], lastlane);
+              for (int q = 0; q < NP; ++q) carry[q] = __shfl_sync(kFull, cpy[q], lastlane);
             } else {
               // no knot in the window: the incoming polynomial spans it
 #pragma unroll
-              for (int d = 0; d <= D; ++d) carry[d] = Aw[d];
-              taylor_shift<D, float>(carry, Uend);
+              for (int q = 0; q < NP; ++q) carry[q] = Aw[q];
+              shift_all(carry, Uend);
             }
           }
           // combine lanes: transmittance as accumulated optical depth
@@ -975,6 +1124,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? kRayMinBlocks : 1)
             if (fabsf(fr - 0.5f) < 2e-3f) j = nearest_entry_fp64(wv[0], wv[1], wv[2], h, p.n_lambda, q);
             j = min(max(j, 0), p.n_lambda - 1);
             s_rec[e] = make_float4(tc.hi, tc.lo, h, __fdividef(a, h * h * h));
+            // shaded variant: the vector from the ray's closest point to the particle
+            if (GR) s_dp[e] = make_float4(wv[0].hi + wv[0].lo, wv[1].hi + wv[1].lo, wv[2].hi + wv[2].lo, 0.f);
             s_j[e] = j;
             atomicAnd(stb + (e >> 5), ~(1u << (e & 31)));
             const float2 th = __ldg(p.theta + j);

@@ -61,6 +61,8 @@ constexpr int kKernF64 = 1;     // FP64_NAIVE: k_render with FP64 running coeffi
 constexpr int kKernReinit = 2;  // FP32_REINIT: k_render with reinitialisation knots
 constexpr int kKernQuant = 3;   // INT64_QUANT: k_render's quantised integer path
 constexpr int kKernRayFB = 4;   // k_ray's fallback pass over the rays its frame pass abandoned
+constexpr int kKernRaySh = 5;   // shaded rendering: k_ray with the across-ray gradient (FP32 modes)
+constexpr int kKernRayShFB = 6; // its fallback pass
 // per-ray global scratch (32-bit words): particle records (4 words), table
 // entries, active list, free stack, two buffers of the waiting list (key, value)
 constexpr int kTableWords = 11 * kCap;
@@ -102,6 +104,11 @@ struct RenderParams {
   const float2* theta;
   const float* jump;
   const float* piece;
+  // gradient tables (shaded rendering): difference coefficients and pieces of
+  // G_L = w'(rho)/rho on the same knots, and the shading ka + kd |n . v|
+  const float* gjump;
+  const float* gpiece;
+  float shade_ka, shade_kd;
   // transfer function
   int tf_n;
   float tf_lo, tf_inv_dv, tf_dv;
@@ -112,6 +119,7 @@ struct RenderParams {
   // quantised path (QT instantiation): length quantum tau and value quantum sigma
   double q_tau, q_inv_tau, q_sigma;
   float window_h;    // window length limit in units of the smallest h it touches
+  float window_fill; // k_ray: windows aim at this fraction of their capacity from the previous density (>= 1: off)
   float tau_ert;     // stop when accumulated optical depth exceeds this
   float* out;
   unsigned long long* stats;
@@ -137,6 +145,7 @@ struct RenderParams {
   int cand_cap;
   double* dbg_field;
   int field_cap;
+  double* dbg_grad;  // shaded rendering: per field row the across-ray gradient's coefficients [3][D+1]
 };
 
 // ---------------------------------------------------------------------------
@@ -198,11 +207,26 @@ __device__ __forceinline__ int tf_cell(const TfCtx& t, float f) {
 // lying within TF cell c.  tau_l: accumulated optical depth before the
 // sub-piece (local to the lane); C: emitted colour (un-attenuated by the
 // lane's incoming transmittance).
+// Shading factor ka + kd |n . v| at y of a piece (gradient extension): the
+// gradient is F'(y) v + (GQ_x, GQ_y, GQ_z)(y), the across-ray part being
+// perpendicular to v; where it vanishes, ka + kd.
 template <int D>
+__device__ __forceinline__ float shade_factor(const float* Q, const float* GQ, float y, float ka, float kd) {
+  float dF = D * Q[D];
+#pragma unroll
+  for (int d = D - 1; d >= 1; --d) dF = fmaf(dF, y, d * Q[d]);
+  const float gx = horner<D>(GQ, y), gy = horner<D>(GQ + D + 1, y), gz = horner<D>(GQ + 2 * (D + 1), y);
+  const float n2 = fmaf(dF, dF, fmaf(gx, gx, fmaf(gy, gy, gz * gz)));
+  return n2 > 0.f ? fmaf(kd, fabsf(dF) * rsqrtf(n2), ka) : ka + kd;
+}
+
+// SH: the emission is shaded (shade_factor) with the across-ray gradient
+// polynomials GQ[3][D+1] expanded at the same point as Q.
+template <int D, bool SH = false>
 __device__ __forceinline__ void composite_cell(const float* Q, float L, int c, const TfCtx& t, float& tau_l,
-                                               float* C) {
+                                               float* C, const float* GQ = nullptr, float ka = 1.f, float kd = 0.f) {
   if (!(L > 0.f)) return;
-  if (c < 0 || c >= t.n - 1) {
+  if (!SH && (c < 0 || c >= t.n - 1)) {
     float4 k = t.tf[c < 0 ? 0 : t.n - 1];
     float tau = k.w * L;
     float w = __expf(-tau_l) * (-expm1f(-tau));
@@ -212,8 +236,10 @@ __device__ __forceinline__ void composite_cell(const float* Q, float L, int c, c
     tau_l += tau;
     return;
   }
-  float4 a = t.tf[c], b = t.tf[c + 1];
-  float vc = t.lo + c * t.dv;
+  // clamped ends (shaded path): a constant transfer function, integrated like a cell
+  const bool clamp = c < 0 || c >= t.n - 1;
+  float4 a = t.tf[clamp ? (c < 0 ? 0 : t.n - 1) : c], b = clamp ? a : t.tf[c + 1];
+  float vc = clamp ? 0.f : t.lo + c * t.dv;
   float g[D + 1];
 #pragma unroll
   for (int d = 0; d <= D; ++d) g[d] = Q[d];
@@ -237,6 +263,10 @@ __device__ __forceinline__ void composite_cell(const float* Q, float L, int c, c
     float e0 = __expf(-(tau_l + a.w * y0 + s1 * G0));
     float e1 = __expf(-(tau_l + a.w * y1 + s1 * G1));
     float sg0 = fmaxf(a.w + s1 * g0, 0.f) * e0, sg1 = fmaxf(a.w + s1 * g1, 0.f) * e1;
+    if (SH) {
+      sg0 *= shade_factor<D>(Q, GQ, y0, ka, kd);
+      sg1 *= shade_factor<D>(Q, GQ, y1, ka, kd);
+    }
     float hw = 0.5f * h;
     C[0] += hw * ((a.x + cr * g0) * sg0 + (a.x + cr * g1) * sg1);
     C[1] += hw * ((a.y + cg * g0) * sg0 + (a.y + cg * g1) * sg1);
@@ -246,9 +276,10 @@ __device__ __forceinline__ void composite_cell(const float* Q, float L, int c, c
   tau_l += tauL;
 }
 
-template <int D>
+template <int D, bool SH = false>
 __device__ __forceinline__ void composite_piece_slow_body(const float* P, float L, float f0, const TfCtx& t,
-                                                          float& tau_l, float* C);
+                                                          float& tau_l, float* C, const float* GP = nullptr,
+                                                          float ka = 1.f, float kd = 0.f);
 template <int D>
 __device__ __noinline__ void composite_piece_slow(const float* P, float L, float f0, const TfCtx& t, float& tau_l,
                                                    float* C) {
@@ -278,9 +309,10 @@ __device__ __forceinline__ void composite_piece(const float* P, float L, const T
 
 // Pieces that may cross transfer-function nodes: 8 sub-intervals, node
 // crossings found inside each by a bracketed root search (kept out of line).
-template <int D>
+template <int D, bool SH>
 __device__ __forceinline__ void composite_piece_slow_body(const float* P, float L, float f0, const TfCtx& t,
-                                                          float& tau_l, float* C) {
+                                                          float& tau_l, float* C, const float* GP, float ka,
+                                                          float kd) {
   const int NS = 8;
   const float step = L / NS;
   float ya = 0.f, fa = f0;
@@ -326,7 +358,16 @@ __device__ __forceinline__ void composite_piece_slow_body(const float* P, float 
 #pragma unroll
       for (int d = 0; d <= D; ++d) Q[d] = P[d];
       taylor_shift<D, float>(Q, ycur);
-      composite_cell<D>(Q, yend - ycur, ccur, t, tau_l, C);
+      if (SH) {
+        float GQ[3 * (D + 1)];
+#pragma unroll
+        for (int i = 0; i < 3 * (D + 1); ++i) GQ[i] = GP[i];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) taylor_shift<D, float>(GQ + ch * (D + 1), ycur);
+        composite_cell<D, true>(Q, yend - ycur, ccur, t, tau_l, C, GQ, ka, kd);
+      } else {
+        composite_cell<D>(Q, yend - ycur, ccur, t, tau_l, C);
+      }
       if (cnext == ccur) break;
       ycur = yend;
       fcur = t.lo + (c1 > ccur ? cnext : ccur) * t.dv;
@@ -365,6 +406,53 @@ __device__ __noinline__ Acc composite_piece_slow_v(Poly<D> P, float L, float f0,
   float tau = a.tau;
   composite_piece_slow_body<D>(P.c, L, f0, t, tau, C);
   return Acc{tau, C[0], C[1], C[2]};
+}
+
+// Across-ray gradient polynomials of a piece, by value (shaded compositing).
+template <int D>
+struct Poly3 {
+  float c[3 * (D + 1)];
+};
+
+template <int D>
+__device__ __noinline__ Acc composite_piece_slow_sh_v(Poly<D> P, Poly3<D> G, float L, float f0, TfCtx t, Acc a,
+                                                      float ka, float kd) {
+  float C[3] = {a.r, a.g, a.b};
+  float tau = a.tau;
+  composite_piece_slow_body<D, true>(P.c, L, f0, t, tau, C, G.c, ka, kd);
+  return Acc{tau, C[0], C[1], C[2]};
+}
+
+// Shaded compositing of [0, L] of a piece P with across-ray gradient GP[3][D+1]:
+// one transfer-function cell inline, crossings out of line.
+template <int D>
+__device__ __forceinline__ void composite_piece_sh_inl(const float* P, const float* GP, float L, const TfCtx& t,
+                                                       float& tau_l, float* C, float ka, float kd) {
+  if (!(L > 0.f)) return;
+  const float f0 = P[0], f1 = horner<D>(P, L);
+  float b2 = 0.f, Lp = 1.f;
+#pragma unroll
+  for (int d = 2; d <= D; ++d) {
+    b2 += d * (d - 1) * fabsf(P[d]) * Lp;
+    Lp *= L;
+  }
+  const float dev = 0.125f * L * L * b2;
+  const int ca = tf_cell(t, fminf(f0, f1) - dev), cb = tf_cell(t, fmaxf(f0, f1) + dev);
+  if (ca == cb) {
+    composite_cell<D, true>(P, L, ca, t, tau_l, C, GP, ka, kd);
+    return;
+  }
+  Poly<D> pp;
+  Poly3<D> gg;
+#pragma unroll
+  for (int d = 0; d <= D; ++d) pp.c[d] = P[d];
+#pragma unroll
+  for (int i = 0; i < 3 * (D + 1); ++i) gg.c[i] = GP[i];
+  const Acc r = composite_piece_slow_sh_v<D>(pp, gg, L, f0, t, Acc{tau_l, C[0], C[1], C[2]}, ka, kd);
+  tau_l = r.tau;
+  C[0] = r.r;
+  C[1] = r.g;
+  C[2] = r.b;
 }
 
 // Composite [0, L] of piece polynomial P, inline: the common case (the piece

@@ -52,9 +52,9 @@ sphdvr_status launch_old(sphdvr_ctx* ctx, const RenderParams& p, int grid, size_
   return launch_kernel(ctx, k_render<kD, S, NW, DBG, RE, BT, QT>, NW, p, grid, smem, st, "k_render");
 }
 
-template <int NW, bool DBG, bool BT, bool FB = false>
+template <int NW, bool DBG, bool BT, bool FB = false, bool GR = false>
 sphdvr_status launch_ray(sphdvr_ctx* ctx, const RenderParams& p, int grid, size_t smem, cudaStream_t st) {
-  return launch_kernel(ctx, k_ray<kD, NW, DBG, BT, FB>, NW, p, grid, smem, st, FB ? "k_ray fallback" : "k_ray", FB);
+  return launch_kernel(ctx, k_ray<kD, NW, DBG, BT, FB, GR>, NW, p, grid, smem, st, FB ? "k_ray fallback" : "k_ray", FB);
 }
 
 template <typename Kern>
@@ -77,6 +77,13 @@ sphdvr_status SPHDVR_CAT(launch_render_d, SPHDVR_D)(sphdvr_ctx* ctx, int kind, b
     case kKernRayFB:  // one warp per CTA, rays from the frame pass's list
       if (batch) return launch_ray<1, false, true, true>(ctx, p, grid, smem, st);
       return launch_ray<1, false, false, true>(ctx, p, grid, smem, st);
+    case kKernRaySh:  // shaded: single frames and the parity hook
+      if (batch) return set_err(ctx, SPHDVR_EINVAL, "render: shading is not available in batched launches");
+      if (dbg) return launch_ray<1, true, false, false, true>(ctx, p, grid, smem, st);
+      return launch_ray<kRayWarps, false, false, false, true>(ctx, p, grid, smem, st);
+    case kKernRayShFB:
+      if (batch) return set_err(ctx, SPHDVR_EINVAL, "render: shading is not available in batched launches");
+      return launch_ray<1, false, false, true, true>(ctx, p, grid, smem, st);
     case kKernQuant:  // integer knots and coefficients, FP32 compositing
       if (dbg) return launch_old<float, 1, true, false, false, true>(ctx, p, grid, smem, st);
       if (batch) return launch_old<float, kRenderWarps, false, false, true, true>(ctx, p, grid, smem, st);
@@ -98,6 +105,9 @@ int SPHDVR_CAT(render_occupancy_d, SPHDVR_D)(int kind, bool dbg, size_t smem) {
     case kKernRay:
       return dbg ? occupancy_of(k_ray<kD, 1, true, false>, 1, smem)
                  : occupancy_of(k_ray<kD, kRayWarps, false, false>, kRayWarps, smem);
+    case kKernRaySh:
+      return dbg ? occupancy_of(k_ray<kD, 1, true, false, false, true>, 1, smem)
+                 : occupancy_of(k_ray<kD, kRayWarps, false, false, false, true>, kRayWarps, smem);
     case kKernQuant:
       return dbg ? occupancy_of(k_render<kD, float, 1, true, false, false, true>, 1, smem)
                  : occupancy_of(k_render<kD, float, kRenderWarps, false, false, false, true>, kRenderWarps, smem);

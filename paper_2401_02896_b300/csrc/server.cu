@@ -366,7 +366,7 @@ sphdvr_status sphdvr_server_submit(sphdvr_server* S, const sphdvr_dataset* ds, c
   if (!rgba_out || !ticket) return set_err(ctx, SPHDVR_EINVAL, "server_submit: NULL argument");
   sphdvr_status s = check_common(ctx, ds, lut);
   if (s != SPHDVR_OK) return s;
-  if ((s = check_opts(ctx, opts)) != SPHDVR_OK) return s;
+  if ((s = check_opts(ctx, opts)) != SPHDVR_OK || (s = reject_shading(ctx, opts, "server")) != SPHDVR_OK) return s;
   Request* r = new (std::nothrow) Request();
   if (!r) return set_err(ctx, SPHDVR_ENOMEM, "server_submit: out of host memory");
   if ((s = check_camera(ctx, cam, &r->a.cam)) != SPHDVR_OK || (s = pack_tf(ctx, tf, r->tf)) != SPHDVR_OK) {

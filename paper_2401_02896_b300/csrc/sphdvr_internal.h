@@ -13,6 +13,8 @@ namespace sphdvr {
 
 // Host look-up-table builder (lutgen.cpp).  Returns 0 on success.
 int build_lut_host(int kernel, int K, int D, int n_lambda, double* theta, double* pieces, double* err);
+// Gradient table for given knots (the across-ray gradient's G_L).  Returns 0 on success.
+int build_grad_host(int kernel, int K, int D, int n_lambda, const double* theta, double* gpieces, double* gerr);
 // Per-particle relative approximation error of a table from its per-entry errors.  Returns 0 on success.
 int lut_error_measure_host(int kernel, int n_lambda, const double* err, double* E);
 // Quantisation error estimate Q_E(tau, sigma) (Sec. 4.4) and the quantum values
@@ -40,6 +42,10 @@ struct DevLut {
   float2* theta = nullptr;
   float* jump = nullptr;
   float* piece = nullptr;
+  // gradient tables (sphdvr_lut_set_gradient), same layouts as jump / piece,
+  // for G_L = w'(rho) / rho on the same knots; nullptr when absent
+  float* gjump = nullptr;
+  float* gpiece = nullptr;
 };
 
 // Per-frame camera, precomputed on the host in FP64.
@@ -69,7 +75,7 @@ struct sphdvr_ctx {
   std::string last_error;
   // frame work buffers (grow-only)
   sphdvr::DevBuf chunk_rect, chunk_front, chunk_ntile, chunk_off, pair_key, pair_val, pair_key2, pair_val2,
-      tile_range, scan_tmp, sort_tmp, stats, tf, img, dbg_pix, dbg_rgba, dbg_counts, dbg_cands, dbg_field, table,
+      tile_range, scan_tmp, sort_tmp, stats, tf, img, dbg_pix, dbg_rgba, dbg_counts, dbg_cands, dbg_field, dbg_grad, table,
       work, fb_table, fb_list;
   sphdvr::DevBuf frames;  // frame records of a batch
   int num_sms = 0;
@@ -109,6 +115,8 @@ namespace sphdvr {
 
 // helpers implemented in api.cpp
 sphdvr_status set_err(sphdvr_ctx* ctx, sphdvr_status st, const std::string& msg);
+// EINVAL when opts ask for shading (entry points whose buffers are sized for unshaded rendering).
+sphdvr_status reject_shading(sphdvr_ctx* ctx, const sphdvr_render_opts* o, const char* where);
 sphdvr_status cuda_err(sphdvr_ctx* ctx, cudaError_t e, const char* where);
 sphdvr_status ensure(sphdvr_ctx* ctx, DevBuf& b, size_t bytes);
 sphdvr_status dev_alloc(sphdvr_ctx* ctx, void** p, size_t bytes);
@@ -156,6 +164,7 @@ struct RenderArgs {
   int cand_cap = 0;
   double* dbg_field = nullptr;
   int field_cap = 0;
+  double* dbg_grad = nullptr;  // shaded rendering: across-ray gradient rows beside the field rows
 };
 // Device scratch of one frame: every buffer the binning and the render
 // kernel write besides the caller's image.
@@ -187,12 +196,12 @@ struct FrameWork {
 // Rays one frame (or batch) can hand to the fallback pass.
 constexpr int kFallbackList = 1 << 16;
 // Scratch floats of the fallback pass for `warps` warps.
-size_t fallback_floats(int warps);
+size_t fallback_floats(int warps, bool shaded = false);
 // Persistent render grid for this frame and the table scratch it needs (floats).
 int render_grid(sphdvr_ctx* ctx, const RenderArgs& a);
 // The same for a batch of frames sharing data set, table and options.
 int render_grid_batch(sphdvr_ctx* ctx, const RenderArgs* a, int n);
-size_t render_table_floats(int grid, bool dbg);
+size_t render_table_floats(int grid, bool dbg, bool shaded = false);
 // Render with scratch from the context's grow-only buffers.
 sphdvr_status render_frame(sphdvr_ctx* ctx, const RenderArgs& a, cudaStream_t st);
 // Render with caller-provided scratch; `sizer` (if non-null) is called with

@@ -115,7 +115,7 @@ extern "C" sphdvr_status sphdvr_render_static_scratch(sphdvr_ctx* ctx, const sph
   if (!rgba_out) return set_err(ctx, SPHDVR_EINVAL, "render_static_scratch: rgba_out is NULL");
   sphdvr_status s = check_common(ctx, ds, lut);
   if (s != SPHDVR_OK) return s;
-  if ((s = check_opts(ctx, opts)) != SPHDVR_OK) return s;
+  if ((s = check_opts(ctx, opts)) != SPHDVR_OK || (s = reject_shading(ctx, opts, "render_static_scratch")) != SPHDVR_OK) return s;
   RenderArgs a;
   a.ds = ds;
   a.lut = &lut->d;

@@ -64,6 +64,11 @@ class RenderOpts(ctypes.Structure):
         ("reserved", ctypes.c_int),
         ("quant_tau", ctypes.c_double),
         ("quant_sigma", ctypes.c_double),
+        ("window_fill", ctypes.c_float),
+        ("ctas_per_sm", ctypes.c_int),
+        ("shading", ctypes.c_int),
+        ("shade_ka", ctypes.c_float),
+        ("shade_kd", ctypes.c_float),
     ]
 
 
@@ -91,6 +96,9 @@ def _load():
         "sphdvr_dataset_info": (ctypes.c_int, [vp, i64p]),
         "sphdvr_ctx_info": (ctypes.c_int, [vp, i64p]),
         "sphdvr_measure_fp32_peak": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_double)]),
+        "sphdvr_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
+                                           ctypes.POINTER(RenderOpts), ctypes.c_char_p, vp, ctypes.POINTER(RenderOpts),
+                                           ctypes.POINTER(ctypes.c_double)]),
         "sphdvr_render": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                          ctypes.POINTER(RenderOpts), vp, vp]),
         "sphdvr_render_batch": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
@@ -126,6 +134,11 @@ def _load():
         "sphdvr_debug_rays": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
                                              ctypes.POINTER(RenderOpts), ctypes.c_int, vp, vp, vp, vp, ctypes.c_int,
                                              vp, ctypes.c_int]),
+        "sphdvr_debug_rays_grad": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(Tf),
+                                                  ctypes.POINTER(RenderOpts), ctypes.c_int, vp, vp, vp, vp, vp,
+                                                  ctypes.c_int]),
+        "sphdvr_lut_build_grad": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, vp, vp]),
+        "sphdvr_lut_set_gradient": (ctypes.c_int, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -211,6 +224,11 @@ def opts_struct(opts=None):
     o.quant_tau = float(opts.get("quant_tau", 0.0))
     o.quant_sigma = float(opts.get("quant_sigma", 0.0))
     o.ray_capacity = int(opts.get("ray_capacity", 0))
+    o.window_fill = float(opts.get("window_fill", 0.0))
+    o.ctas_per_sm = int(opts.get("ctas_per_sm", 0))
+    o.shading = int(opts.get("shading", 0))
+    o.shade_ka = float(opts.get("shade_ka", 0.0))
+    o.shade_kd = float(opts.get("shade_kd", 0.0))
     return o
 
 
@@ -269,6 +287,24 @@ def sphdvr_lut_create(ctx, kernel, K, D, n_lambda, theta, pieces):
     h = ctypes.c_void_p()
     _check(_lib.sphdvr_lut_create(ctx, _kid(kernel), K, D, n_lambda, _p(th), _p(pc), ctypes.byref(h)), ctx)
     return h
+
+
+def sphdvr_lut_build_grad(kernel, K, D, n_lambda, theta):
+    """FP64 gradient table on a table's knots (host): returns (gpieces [n,m,D+1], gerr [n])."""
+    m = (K + 1) // 2
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    if th.shape != (n_lambda, m):
+        raise ValueError("theta must have shape (n_lambda, m)")
+    gp = np.zeros((n_lambda, m, D + 1))
+    ge = np.zeros(n_lambda)
+    _check(_lib.sphdvr_lut_build_grad(_kid(kernel), K, D, n_lambda, _p(th), _p(gp), _p(ge)))
+    return gp, ge
+
+
+def sphdvr_lut_set_gradient(lut, theta, gpieces):
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    gp = np.ascontiguousarray(gpieces, dtype=np.float64)
+    return _check(_lib.sphdvr_lut_set_gradient(lut, _p(th), _p(gp)))
 
 
 def sphdvr_lut_save(path, kernel, K, D, n_lambda, theta, pieces, err=None):
@@ -331,6 +367,19 @@ def sphdvr_dataset_quant_params(ctx, ds, kernel, D, int_bits=64):
     _check(_lib.sphdvr_dataset_quant_params(ctx, ds, _kid(kernel), int(D), int(int_bits), *[ctypes.byref(x) for x in v]),
            ctx)
     return dict(zip(("tau", "sigma", "qe", "a_max"), (x.value for x in v)))
+
+
+def sphdvr_autotune(ctx, ds, lut, camera, tf, opts=None, cache_path=None, stream=None):
+    """Tuned render options (dict) and the frame times before and after (ms)."""
+    c, t, o = camera_struct(camera), tf_struct(tf), opts_struct(opts)
+    out = RenderOpts()
+    ms = (ctypes.c_double * 2)()
+    _check(_lib.sphdvr_autotune(ctx, ds, lut, ctypes.byref(c), ctypes.byref(t), ctypes.byref(o),
+                                os.fsencode(cache_path) if cache_path else None, ctypes.c_void_p(stream or 0),
+                                ctypes.byref(out), ms), ctx)
+    tuned = dict(opts or {})
+    tuned.update(ctas_per_sm=out.ctas_per_sm, window_h=out.window_h, window_fill=out.window_fill)
+    return tuned, (ms[0], ms[1])
 
 
 def sphdvr_measure_fp32_peak(ctx, stream=None):
@@ -425,6 +474,22 @@ def sphdvr_debug_rays(ctx, ds, lut, camera, tf, opts, pixels, cand_cap=0, field_
                                 _p(rgba), _p(counts), _p(cands), int(cand_cap), _p(field), int(field_cap))
     _check(st, ctx, (EOVERFLOW,))
     return dict(rgba=rgba, counts=counts, cand_ids=cands, field=field, overflow=st == EOVERFLOW)
+
+
+def sphdvr_debug_rays_grad(ctx, ds, lut, camera, tf, opts, pixels, field_cap, D):
+    """Shaded parity hook: rgba, counts, field rows [n, field_cap, D+3] and the across-ray gradient's rows
+    [n, field_cap, 3, D+1] (localized coefficients at each row's t_a)."""
+    pix = np.ascontiguousarray(pixels, dtype=np.int32)
+    n = pix.shape[0]
+    rgba = np.zeros((n, 4), np.float32)
+    counts = np.zeros((n, 8), np.int64)
+    field = np.zeros((n, field_cap, D + 3))
+    grad = np.zeros((n, field_cap, 3, D + 1))
+    c, t, o = camera_struct(camera), tf_struct(tf), opts_struct(opts)
+    st = _lib.sphdvr_debug_rays_grad(ctx, ds, lut, ctypes.byref(c), ctypes.byref(t), ctypes.byref(o), n, _p(pix),
+                                     _p(rgba), _p(counts), _p(field), _p(grad), int(field_cap))
+    _check(st, ctx, (EOVERFLOW,))
+    return dict(rgba=rgba, counts=counts, field=field, grad=grad, overflow=st == EOVERFLOW)
 
 
 class FramePlan:

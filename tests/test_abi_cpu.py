@@ -208,3 +208,20 @@ def test_header_is_plain_c(tmp_path):
                    check=True)
     subprocess.run(["g++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, "-x", "c++", str(src)],
                    check=True)
+
+
+@pytest.mark.parametrize("kernel,K,D", [("m4", 4, 3), ("wendland_c2", 4, 3), ("m4", 3, 2), ("poly6", 1, 6)])
+def test_library_gradient_table_matches_the_oracle(kernel, K, D):
+    """The library's gradient builder (host, long double) and the oracle's (FP64) project the same
+    G_L = w'(rho)/rho on the same knots: the pieces agree to rounding, relative to the entry's norm of G."""
+    n = 65
+    L = oracle.lut_build(kernel, K, D, n)
+    G = oracle.lut_build_grad(L)
+    gp, ge = S.sphdvr_lut_build_grad(kernel, K, D, n, L["theta"])
+    for j in range(n - 1):
+        scale = max(G["normG"][j], 1e-300)
+        assert np.abs(gp[j] - G["gpieces"][j]).max() <= 1e-9 * scale
+        assert abs(ge[j] - G["gerr"][j]) <= 1e-12 * scale
+    assert np.all(gp[-1] == 0)
+    with pytest.raises(S.SphdvrError):
+        S.sphdvr_lut_build_grad(kernel, K, 9, n, L["theta"])
