@@ -43,7 +43,7 @@ def _load():
             ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_double,  # tf
             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,  # n_rays pix rgba stats
             ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
-            ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,  # gpieces ka kd gfield
+            ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,  # gpieces ka kd g0 gfield
         ]
         lib.orc_kernel_dw_r.restype = ctypes.c_double
         lib.orc_kernel_dw_r.argtypes = [ctypes.c_int, ctypes.c_double]
@@ -53,7 +53,7 @@ def _load():
         lib.orc_composite_piece_shaded.argtypes = [
             ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_double,
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-            ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
         ]
         lib.orc_composite_piece.restype = None
         lib.orc_composite_piece.argtypes = [
@@ -231,7 +231,8 @@ def render(particles, lut, camera, tf, pixels, cand_cap=0, field_cap=0, grad=Non
     FP32 ``mass``, ``value``, ``density`` (n,) of the C ABI (each optional, 1
     if missing); the amplitude is ``particle_amplitude``.
     ``grad``: a gradient table of lut_build_grad, or None; with it the emission is
-    shaded by ka + kd |n . v| (``shade`` = (ka, kd)) and ``gfield`` holds per field
+    shaded by ka + kd |F'| / sqrt(|grad|^2 + g0^2) (``shade`` = (ka, kd) or (ka, kd, g0); g0 = 0 is the
+    cosine |n . v|) and ``gfield`` holds per field
     row the perpendicular gradient's localized coefficients [3][D+1].
     Returns dict(rgba (r,4), stats (r,8) int64, cand_ids (r,cand_cap) or None,
     field (r, field_cap, D+3) or None, gfield (r, field_cap, 3, D+1) or None, truncated bool).
@@ -260,6 +261,7 @@ def render(particles, lut, camera, tf, pixels, cand_cap=0, field_cap=0, grad=Non
         float(tf["sigma_scale"]), nr, _ptr(pix), _ptr(out), _ptr(stats),
         _ptr(cids) if cids is not None else None, int(cand_cap), _ptr(fld) if fld is not None else None,
         int(field_cap), _ptr(gp) if gp is not None else None, float(shade[0]), float(shade[1]),
+        float(shade[2]) if len(shade) > 2 else 0.0,
         _ptr(gfld) if gfld is not None else None,
     )
     return dict(rgba=out, stats=stats, cand_ids=cids, field=fld, gfield=gfld, truncated=bool(rc & 2))
@@ -277,8 +279,9 @@ def composite_piece(tf, F, ya, yb, rgb=(0.0, 0.0, 0.0), T=1.0):
     return c, float(t[0])
 
 
-def composite_piece_shaded(tf, F, GP, ka, kd, ya, yb, rgb=(0.0, 0.0, 0.0), T=1.0):
-    """Composite one piece with shading ka + kd |n . v| (oracle part 5); GP: [3][D+1] perpendicular gradient."""
+def composite_piece_shaded(tf, F, GP, ka, kd, ya, yb, rgb=(0.0, 0.0, 0.0), T=1.0, g0=0.0):
+    """Composite one piece with shading ka + kd |F'| / sqrt(|grad|^2 + g0^2) (oracle part 5); GP: [3][D+1]
+    perpendicular gradient."""
     lib = _load()
     F = np.ascontiguousarray(F, dtype=np.float64)
     G = np.ascontiguousarray(GP, dtype=np.float64)
@@ -287,7 +290,7 @@ def composite_piece_shaded(tf, F, GP, ka, kd, ya, yb, rgb=(0.0, 0.0, 0.0), T=1.0
     t = np.array([T], dtype=np.float64)
     lib.orc_composite_piece_shaded(int(rgba_tf.shape[0]), float(tf["lo"]), float(tf["hi"]), _ptr(rgba_tf),
                                    float(tf["sigma_scale"]), _ptr(F), _ptr(G), len(F) - 1, float(ka), float(kd),
-                                   float(ya), float(yb), _ptr(c), _ptr(t))
+                                   float(g0), float(ya), float(yb), _ptr(c), _ptr(t))
     return c, float(t[0])
 
 

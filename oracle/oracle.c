@@ -37,7 +37,8 @@
  *      perpendicular gradient of the ray is a piecewise polynomial with the
  *      same knots; the along-ray part is the derivative of the field's pieces.
  *      Shading (a reading: the paper names no model): the emitted colour is
- *      scaled by ka + kd |n . v|, n = grad / |grad| (a light along the ray).
+ *      scaled by ka + kd |grad . v| / sqrt(|grad|^2 + g0^2) (a light along the ray;
+ *      g0 >= 0 softens the cosine where the gradient is small, a reading).
  */
 #include <math.h>
 #include <stdint.h>
@@ -938,11 +939,12 @@ typedef struct {
   double c0[3], c1[3];
   double ya, Gya;
   const double* GP;  /* perpendicular gradient polynomials [3][D+1] (part 5), NULL: no shading */
-  double ka, kd;
+  double ka, kd, g2; /* g2 = g0^2 */
 } emis_ctx;
 
-/* Shading factor ka + kd |n . v| at y: n . v = F'(y) / |grad|, |grad|^2 = F'^2 + |GP(y)|^2
- * (the perpendicular part is orthogonal to v); where the gradient vanishes, ka + kd. */
+/* Shading factor ka + kd |F'(y)| / sqrt(|grad|^2 + g0^2) at y, |grad|^2 = F'^2 + |GP(y)|^2
+ * (the perpendicular part is orthogonal to v); g0 = 0 gives the cosine |n . v|, and where
+ * that gradient vanishes, ka + kd. */
 static double shade_at(const emis_ctx* e, double y) {
   double dF = 0, yp = 1;
   for (int i = 1; i <= e->D; i++) { dF += i * e->F[i] * yp; yp *= y; }
@@ -951,6 +953,7 @@ static double shade_at(const emis_ctx* e, double y) {
     double g = poly_eval(e->GP + comp * (e->D + 1), e->D, y);
     n2 += g * g;
   }
+  n2 += e->g2;
   return n2 > 0 ? e->ka + e->kd * fabs(dF) / sqrt(n2) : e->ka + e->kd;
 }
 
@@ -1032,7 +1035,7 @@ static int cmp_d(const void* a, const void* b) {
 /* Composite one field piece F(y), y in [ya, yb] (local to the piece start);
  * with GP (perpendicular gradient polynomials, part 5) the emission is shaded. */
 static void composite_piece(const orc_tf* tf, const double* F, int D, double ya, double yb, double* rgb, double* Tacc,
-                            const double* GP, double ka, double kd) {
+                            const double* GP, double ka, double kd, double g0) {
   if (!(yb > ya)) return;
   /* monotone sub-intervals: critical points of F */
   double dF[ORC_MAXD + 1], crit[ORC_MAXD + 2];
@@ -1071,7 +1074,7 @@ static void composite_piece(const orc_tf* tf, const double* F, int D, double ya,
   qsort(cuts, ncut, sizeof(double), cmp_d);
   emis_ctx e;
   e.F = F; e.D = D;
-  e.GP = GP; e.ka = ka; e.kd = kd;
+  e.GP = GP; e.ka = ka; e.kd = kd; e.g2 = g0 * g0;
   e.G[0] = 0;
   for (int i = 0; i <= D; i++) e.G[i + 1] = F[i] / (i + 1);
   double lo = ya;
@@ -1111,7 +1114,8 @@ int orc_render(int64_t n, const float* pos, const float* hs, const double* amp, 
                int n_lambda, const double* theta, const double* pieces, const orc_camera* cam, int tf_n,
                double tf_lo, double tf_hi, const double* tf_rgba, double sigma_scale, int n_rays,
                const int* pix, double* rgba, int64_t* stats, int64_t* cand_ids, int cand_cap, double* field,
-               int field_cap, const double* gpieces, double shade_ka, double shade_kd, double* gfield) {
+               int field_cap, const double* gpieces, double shade_ka, double shade_kd, double shade_g0,
+               double* gfield) {
   orc_lut L = {K, D, n_lambda, kernel, theta, pieces};
   orc_tf tf = {tf_n, tf_lo, tf_hi, tf_rgba, sigma_scale};
   double q = orc_kernel_support(kernel);
@@ -1215,7 +1219,7 @@ int orc_render(int64_t n, const float* pos, const float* hs, const double* amp, 
       nf++;
       /* composite the part of the piece inside [t0, t1] */
       double ya = t0 > ta ? t0 - ta : 0, yb = (tb < t1 ? tb : t1) - ta;
-      composite_piece(&tf, A, D, ya, yb, rgb, &Tacc, gpieces ? GP : NULL, shade_ka, shade_kd);
+      composite_piece(&tf, A, D, ya, yb, rgb, &Tacc, gpieces ? GP : NULL, shade_ka, shade_kd, shade_g0);
     }
     st[5] = nf;
     out[0] = rgb[0]; out[1] = rgb[1]; out[2] = rgb[2]; out[3] = 1 - Tacc;
@@ -1229,15 +1233,16 @@ int orc_render(int64_t n, const float* pos, const float* hs, const double* amp, 
 void orc_composite_piece(int tf_n, double tf_lo, double tf_hi, const double* tf_rgba, double sigma_scale,
                          const double* F, int D, double ya, double yb, double* rgb_inout, double* T_inout) {
   orc_tf tf = {tf_n, tf_lo, tf_hi, tf_rgba, sigma_scale};
-  composite_piece(&tf, F, D, ya, yb, rgb_inout, T_inout, NULL, 1.0, 0.0);
+  composite_piece(&tf, F, D, ya, yb, rgb_inout, T_inout, NULL, 1.0, 0.0, 0.0);
 }
 
 /* The same with shading (part 5): GP are the three perpendicular gradient polynomials [3][D+1]. */
 void orc_composite_piece_shaded(int tf_n, double tf_lo, double tf_hi, const double* tf_rgba, double sigma_scale,
-                                const double* F, const double* GP, int D, double ka, double kd, double ya, double yb,
+                                const double* F, const double* GP, int D, double ka, double kd, double g0, double ya,
+                                double yb,
                                 double* rgb_inout, double* T_inout) {
   orc_tf tf = {tf_n, tf_lo, tf_hi, tf_rgba, sigma_scale};
-  composite_piece(&tf, F, D, ya, yb, rgb_inout, T_inout, GP, ka, kd);
+  composite_piece(&tf, F, D, ya, yb, rgb_inout, T_inout, GP, ka, kd, g0);
 }
 
 int orc_num_threads(void) {

@@ -8,7 +8,8 @@ scaled by ka + kd |n . v|, a light along the viewing ray).
   no worse than the field's own relative error bound class for M4;
 * along a ray, F'(t) v + F_perp(t) matches the finite-difference gradient of the exact SPH sum within the
   approximation error, and F_perp is perpendicular to the ray;
-* ka = 1, kd = 0 reproduces the unshaded image; a single shaded piece equals a fine midpoint sum.
+* ka = 1, kd = 0 reproduces the unshaded image; a single shaded piece equals a fine midpoint sum, with and
+  without the softening gradient g0; a huge g0 leaves ka times the unshaded emission.
 """
 import numpy as np
 import pytest
@@ -133,17 +134,22 @@ def test_unit_shading_reproduces_the_unshaded_image_and_a_piece_matches_a_midpoi
     F = np.array([0.9, 0.8, -1.5, 0.7])
     GP = np.array([[0.3, -0.2, 0.1, 0.0], [-0.4, 0.5, 0.2, -0.1], [0.0, 0.0, 0.0, 0.0]])
     ka, kd, yb = 0.25, 0.75, 0.9
-    rgb, T = oracle.composite_piece_shaded(tf, F, GP, ka, kd, 0.0, yb)
     n = 200000
     y = (np.arange(n) + 0.5) * (yb / n)
     f = np.polyval(F[::-1], y)
     dF = np.polyval((F[1:] * np.arange(1, 4))[::-1], y)
     gp = np.stack([np.polyval(g[::-1], y) for g in GP])
-    shade = ka + kd * np.abs(dF) / np.sqrt(dF ** 2 + (gp ** 2).sum(axis=0))
     v = np.linspace(tf["lo"], tf["hi"], tf["rgba"].shape[0])
     rgba_f = np.stack([np.interp(f, v, tf["rgba"][:, k]) for k in range(4)], axis=1)
     sig = tf["sigma_scale"] * rgba_f[:, 3]
     tau = np.cumsum(sig) * (yb / n) - 0.5 * sig * (yb / n)
-    ref = (rgba_f[:, :3] * (sig * shade * np.exp(-tau))[:, None]).sum(axis=0) * (yb / n)
-    assert np.abs(rgb - ref).max() <= 1e-6
-    assert T == pytest.approx(np.exp(-sig.sum() * (yb / n)), rel=1e-6)
+    for g0 in (0.0, 0.5):
+        rgb, T = oracle.composite_piece_shaded(tf, F, GP, ka, kd, 0.0, yb, g0=g0)
+        shade = ka + kd * np.abs(dF) / np.sqrt(dF ** 2 + (gp ** 2).sum(axis=0) + g0 ** 2)
+        ref = (rgba_f[:, :3] * (sig * shade * np.exp(-tau))[:, None]).sum(axis=0) * (yb / n)
+        assert np.abs(rgb - ref).max() <= 1e-6, g0
+        assert T == pytest.approx(np.exp(-sig.sum() * (yb / n)), rel=1e-6)
+    # a softening gradient far above |grad F| leaves the ambient part: ka times the unshaded emission
+    rgb_inf, T_inf = oracle.composite_piece_shaded(tf, F, GP, ka, kd, 0.0, yb, g0=1e12)
+    rgb_u, T_u = oracle.composite_piece(tf, F, 0.0, yb)
+    assert np.abs(rgb_inf - ka * rgb_u).max() <= 1e-9 * np.abs(rgb_u).max() and T_inf == pytest.approx(T_u, rel=1e-12)
