@@ -11,6 +11,10 @@ field) is not available, so these sets stand in for it:
                           expected distance to the 32nd nearest neighbour from the
                           analytic number density, the value is the analytic mass
                           density (what an SPH density estimate converges to).
+* ``halo_mixture_knn`` -- the same positions, prepared the way an SPH code would:
+                          h = the distance to the 32nd nearest neighbour (a k-d
+                          tree query), value = density = the SPH density
+                          estimate over those neighbours (mass 1/N).
 * ``dam_break_slab``   -- a dense, floor-graded lower layer plus a sparse splash,
                           h clamped to [1e-4, 1e-2].
 
@@ -57,6 +61,55 @@ def halo_mixture(n=1_000_000, n_halos=64, bg_frac=0.2, a_range=(0.005, 0.05), se
     h_i = (neighbours / (4/3 pi n(x_i)))^(1/3) with n the analytic number
     density of the mixture; value_i = mass * n(x_i) (mass density); mass 1/N.
     """
+    pos32, cen, a, counts, n_bg = _halo_positions(n, n_halos, bg_frac, a_range, seed)
+    # analytic number density of the mixture at each particle
+    xmax = 10.0 ** 3 / (10.0 ** 2 + 1.0) ** 1.5
+    if device is not None:
+        nd = _halo_density_torch(pos32, cen, a, counts, xmax, float(n_bg), device)
+    else:
+        nd = _halo_density_np(pos32, cen, a, counts, xmax, float(n_bg), chunk)
+    h = (neighbours / (4.0 / 3.0 * math.pi * nd)) ** (1.0 / 3.0)
+    mass = np.full(n, 1.0 / n, np.float32)
+    dens = (nd / n).astype(np.float32)
+    return dict(pos=pos32, h=h.astype(np.float32), mass=mass, density=dens, value=dens.copy())
+
+
+def halo_mixture_knn(n=1_000_000, n_halos=64, bg_frac=0.2, a_range=(0.005, 0.05), seed=BASE_SEED + 1,
+                     neighbours=32, chunk=1 << 20, workers=-1):
+    """The positions of ``halo_mixture`` (same arguments, same seed), with h and the value computed from
+    the particles themselves, as an SPH code prepares its output:
+
+    * h_i = the distance from particle i to its 32nd nearest neighbour (scipy k-d tree, FP64);
+    * rho_i = sum over i and those neighbours j of m_j W(|x_i - x_j|; h_i), W the normalised cubic
+      spline with support radius h_i (the common "N_ngb neighbours inside the kernel" convention of SPH
+      density estimates); value_i = density_i = rho_i, mass 1/N.
+
+    This is input preparation (the SPH simulation's job), not part of the rendering method: the renderer
+    and the oracle receive the resulting arrays.  Cost: a k-d tree over N points and one query of
+    neighbours + 1 per point (about 20 s for 16.8M points on 8 cores).
+    """
+    from scipy.spatial import cKDTree
+
+    pos32, _, _, _, _ = _halo_positions(n, n_halos, bg_frac, a_range, seed)
+    p64 = pos32.astype(np.float64)
+    tree = cKDTree(p64, leafsize=16, balanced_tree=False, compact_nodes=False)
+    h = np.empty(n, np.float64)
+    rho = np.empty(n, np.float64)
+    m = 1.0 / n
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        d, _ = tree.query(p64[s:e], k=neighbours + 1, workers=workers)  # column 0: the particle itself
+        H = d[:, neighbours]
+        u = d / H[:, None]
+        wq = np.where(u < 0.5, 1.0 - 6.0 * u ** 2 + 6.0 * u ** 3, np.where(u < 1.0, 2.0 * (1.0 - u) ** 3, 0.0))
+        h[s:e] = H
+        rho[s:e] = m * 8.0 / (math.pi * H ** 3) * wq.sum(axis=1)
+    dens = rho.astype(np.float32)
+    return dict(pos=pos32, h=h.astype(np.float32), mass=np.full(n, m, np.float32), density=dens, value=dens.copy())
+
+
+def _halo_positions(n, n_halos, bg_frac, a_range, seed):
+    """Positions of the halo mixture (FP32) and its parameters (centres, scales, counts, background)."""
     r = _rng(seed)
     n_bg = int(round(bg_frac * n))
     n_h = n - n_bg
@@ -77,17 +130,7 @@ def halo_mixture(n=1_000_000, n_halos=64, bg_frac=0.2, a_range=(0.005, 0.05), se
         pos[o:o + c] = cen[k] + rad[:, None] * d
         o += c
     pos[o:] = r.random((n - o, 3))
-    pos32 = pos.astype(np.float32)
-    # analytic number density of the mixture at each particle
-    xmax = 10.0 ** 3 / (10.0 ** 2 + 1.0) ** 1.5
-    if device is not None:
-        nd = _halo_density_torch(pos32, cen, a, counts, xmax, float(n_bg), device)
-    else:
-        nd = _halo_density_np(pos32, cen, a, counts, xmax, float(n_bg), chunk)
-    h = (neighbours / (4.0 / 3.0 * math.pi * nd)) ** (1.0 / 3.0)
-    mass = np.full(n, 1.0 / n, np.float32)
-    dens = (nd / n).astype(np.float32)
-    return dict(pos=pos32, h=h.astype(np.float32), mass=mass, density=dens, value=dens.copy())
+    return pos.astype(np.float32), cen, a, counts, n_bg
 
 
 def _halo_density_np(pos32, cen, a, counts, xmax, n_bg, chunk):

@@ -2,6 +2,8 @@
 
 * 16,777,216-particle halo mixture (h over ~3 decades), Wendland C2, K=4 D=3,
   4096-entry table, perspective 2048x2048 -- the benchmark's frame;
+* the same 16,777,216 positions prepared as an SPH code would: h = distance to the
+  32nd nearest neighbour, value = the SPH density estimate (noisy h and values);
 * 64,000,000-particle dam-break slab (dense graded layer + sparse splash),
   Wendland C4, K=4 D=4, perspective 4096x4096, a high-opacity transfer function.
 
@@ -85,6 +87,20 @@ def test_halo_16m_2048_sampled_pixels(S, ctx):
     pix = SY.pixel_sample(2048, 2048, 48, seed=21)
     try:
         _three_way(S, ctx, ds, lt, P, lut, cam, tf, pix, "halo16m")
+    finally:
+        S.sphdvr_dataset_free(ds)
+        S.sphdvr_lut_free(lt)
+
+
+def test_halo_knn_16m_2048_sampled_pixels(S, ctx):
+    P = SY.halo_mixture_knn(16_777_216, a_range=(5e-4, 0.05), seed=SY.BASE_SEED + 2)
+    lut = oracle_lut("wendland_c2", 4, 3, 4096)
+    ds, lt = _mk(S, ctx, P, lut)
+    cam = SY.orbit_camera(2048, 2048, azimuth_deg=30.0, elevation_deg=20.0)
+    tf = SY.tf_density(P["value"])
+    pix = SY.pixel_sample(2048, 2048, 48, seed=23)
+    try:
+        _three_way(S, ctx, ds, lt, P, lut, cam, tf, pix, "halo16m kNN")
     finally:
         S.sphdvr_dataset_free(ds)
         S.sphdvr_lut_free(lt)
