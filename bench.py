@@ -37,6 +37,12 @@ WORKLOADS = {
                     desc="halo mixture 16,777,216 particles (64 Plummer halos + 20% uniform background, "
                          "h = expected 32-NN distance, ~3 decades), Wendland C2, K=4, D=3, 4096-entry table, "
                          "perspective 2048x2048, FP32 anchored"),
+    # the same positions with h = the true 32nd-neighbour distance and the SPH density estimate as value
+    "halo16m_knn": dict(n=16_777_216, a_range=(5e-4, 0.05), seed=SY.BASE_SEED + 2, knn=True, kernel="wendland_c2",
+                        K=4, D=3, n_lambda=4096, res=2048,
+                        desc="halo mixture 16,777,216 particles (64 Plummer halos + 20% uniform background), "
+                             "h = distance to the 32nd nearest neighbour (k-d tree), value = SPH density estimate, "
+                             "Wendland C2, K=4, D=3, 4096-entry table, perspective 2048x2048, FP32 anchored"),
     "halo1m": dict(n=1_000_000, a_range=(5e-3, 0.05), seed=SY.BASE_SEED + 1, kernel="wendland_c2", K=4, D=3,
                    n_lambda=4096, res=1024,
                    desc="halo mixture 1,000,000 particles, Wendland C2, K=4, D=3, perspective 1024x1024"),
@@ -47,10 +53,13 @@ WORKLOADS = {
                          "sigma x500 (early ray termination), FP32 anchored"),
 }
 
-# DRAM bytes (read + write) of one render launch, from the ncu capture named in
-# profiles/ for the render kernel as it is in this tree, scaled to the frame
-# (None where no capture of the current kernel exists).
-PROFILED_DRAM_BYTES = {}
+# DRAM bytes (read + write) of one frame-pass launch of the render kernel, from the
+# ncu capture named in profiles/ (launches_halo16m_2048.md) of the kernel as it is in
+# this tree, keyed by (workload, image size, precision, window_h); None where no
+# capture of the current kernel and options exists.
+PROFILED_DRAM_BYTES = {
+    ("halo16m", 2048, "fp32_anchored", 1.0): 8.737e9 + 254.47e9,
+}
 
 
 def replica_rate(total_ms, rays, dist=None, device="cpu"):
@@ -127,6 +136,8 @@ def clocks_stop(proc, f, path, device):
 def make_inputs(w, device):
     if w.get("slab"):
         P = SY.dam_break_slab(w["n"])
+    elif w.get("knn"):
+        P = SY.halo_mixture_knn(w["n"], a_range=w["a_range"], seed=w["seed"])
     else:
         P = SY.halo_mixture(w["n"], a_range=w["a_range"], seed=w["seed"], device=device)
     tf = SY.tf_density(P["value"], sigma_scale=w.get("sigma_scale", 1.0)) if w.get("sigma_scale") else \
@@ -324,10 +335,10 @@ def precision_sweep_times(S, torch, ctx, ds, w, tf, cam, dev, stream, degrees=(1
         th, pc, _ = S.sphdvr_lut_build(w["kernel"], w["K"], D, w["n_lambda"])
         lt = S.sphdvr_lut_create(ctx, w["kernel"], w["K"], D, w["n_lambda"], th, pc)
         imgs = {}
-        for mode in ("fp32_anchored", "fp32_naive", "fp64_naive", "fp32_reinit", "int64_quant"):
+        for mode in ("fp32_anchored", "fp32_naive", "fp32_kahan", "fp64_naive", "fp32_reinit", "int64_quant"):
             o = dict(precision=mode, ert_eps=1e-5)
             if mode == "fp32_reinit":
-                o["reinit_dt"] = 0.02
+                o["reinit_dt"] = 0.02 if D <= 3 else 0.005  # the spacing the parity sweep validates
             if mode == "int64_quant":
                 q = S.sphdvr_dataset_quant_params(ctx, ds, w["kernel"], D, 64)
                 o.update(quant_tau=q["tau"], quant_sigma=q["sigma"])
@@ -371,6 +382,8 @@ def main():
                     help="tune the render options on the workload's frame before timing (sphdvr_autotune; 0: defaults)")
     ap.add_argument("--plain-vs-served", type=int, default=16,
                     help="requests of the plain-vs-served comparison (0: skip)")
+    ap.add_argument("--shading-frame", type=int, default=1,
+                    help="time a shaded frame beside the unshaded one (1M-particle halo mixture, 512x512; 0: skip)")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="also time every precision mode x D in {1,2,3,4} on the workload's frame (C3)")
     ap.add_argument("--serving-stream", type=int, default=0,
@@ -628,6 +641,42 @@ def main():
         S.sphdvr_dataset_free(ds1)
         del ga, sc
 
+    # ---- shaded rendering (the across-ray gradient reconstructed beside the field) against the unshaded frame
+    shading = None
+    if args.shading_frame:
+        w1 = WORKLOADS["halo1m"]
+        P1, tf1 = make_inputs(w1, "cuda")
+        ds1 = S.sphdvr_dataset_create(ctx, P1["pos"], P1["h"], P1["mass"], P1["density"], P1["value"])
+        th1, pc1, _ = S.sphdvr_lut_build(w1["kernel"], w1["K"], w1["D"], w1["n_lambda"])
+        lt1 = S.sphdvr_lut_create(ctx, w1["kernel"], w1["K"], w1["D"], w1["n_lambda"], th1, pc1)
+        gp1, _ = S.sphdvr_lut_build_grad(w1["kernel"], w1["K"], w1["D"], w1["n_lambda"], th1)
+        S.sphdvr_lut_set_gradient(lt1, th1, gp1)
+        # softening gradient: 1e-3 of the data's typical gradient scale (median value / median h)
+        g0 = 1e-3 * float(np.median(P1["value"])) / float(np.median(P1["h"]))
+        cam1 = SY.orbit_camera(512, 512)
+        imgs_ = {k: torch.empty((512, 512, 4), dtype=torch.float32, device=dev) for k in ("plain", "shaded", "unit")}
+        modes_ = (("plain", dict(ert_eps=1e-5)),
+                  ("shaded", dict(ert_eps=1e-5, shading=1, shade_ka=0.3, shade_kd=0.7, shade_g0=g0)),
+                  ("unit", dict(ert_eps=1e-5, shading=1, shade_ka=1.0, shade_kd=0.0, shade_g0=g0)))
+        tsh = {}
+        for name, o_ in modes_:
+            S.sphdvr_render(ctx, ds1, lt1, cam1, tf1, o_, imgs_[name].data_ptr(), stream=stream)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(2):
+                S.sphdvr_render(ctx, ds1, lt1, cam1, tf1, o_, imgs_[name].data_ptr(), stream=stream)
+                torch.cuda.synchronize()
+                best = min(best, S.sphdvr_frame_stats(ctx)["render_ns"] / 1e6)
+            tsh[name] = best
+        shading = dict(workload="halo mixture 1,000,000 particles, Wendland C2, K=4, D=3, perspective 512x512",
+                       ka=0.3, kd=0.7, g0=g0, unshaded_ms=tsh["plain"], shaded_ms=tsh["shaded"],
+                       ratio=tsh["shaded"] / tsh["plain"],
+                       unit_shading_max_pixel_diff=float((imgs_["unit"] - imgs_["plain"]).abs().max()),
+                       note="render-kernel time (CUDA events), best of 2; unit shading = ka 1, kd 0")
+        S.sphdvr_dataset_free(ds1)
+        S.sphdvr_lut_free(lt1)
+        del imgs_
+
     sweep = precision_sweep_times(S, torch, ctx, ds, w, tf, cam, dev, stream) if args.precision_sweep else None
     stream_c4 = serving_stream(S, torch, ctx, tf, dev, per_rate=args.serving_stream) if args.serving_stream > 0 else None
 
@@ -652,7 +701,8 @@ def main():
                              render_kernel_ms=kern_s * 1e3),
             roofline=dict(bound="alu", achieved=achieved, peak=fp32_peak, unit="TFLOP/s",
                           frac=achieved / fp32_peak,
-                          traffic=PROFILED_DRAM_BYTES.get((args.workload, w["res"], args.precision)),
+                          traffic=PROFILED_DRAM_BYTES.get((args.workload, w["res"], args.precision,
+                                                           round(float(opts.get("window_h") or 1.0), 3))),
                           note="peak: FP32 FMA rate measured in this run (sphdvr_measure_fp32_peak, an FFMA "
                                "loop on every resident thread; MEASURED_PEAKS.json has no FP32 figure); "
                                "achieved: %d algorithmic FLOP per segment x segments per frame / render "
@@ -680,6 +730,8 @@ def main():
             line["quantised"] = quant
         if scatter:
             line["scatter_order"] = scatter
+        if shading:
+            line["shading"] = shading
         info = S.sphdvr_dataset_info(ds)
         line["dataset_build"] = dict(ms=t_build * 1e3, particles_per_s=w["n"] / t_build,
                                      input_bytes=int(w["n"] * 28), resident_bytes=int(info["bytes"]),

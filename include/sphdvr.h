@@ -86,7 +86,15 @@ typedef enum {
    * estimate).  quant_sigma must bound the field as Sec. 4.4 prescribes
    * (A_max / 2^63) so that every coefficient fits 64 bits; compositing is
    * FP32 as in the other modes. */
-  SPHDVR_PREC_INT64_QUANT = 4
+  SPHDVR_PREC_INT64_QUANT = 4,
+  /* as FP32_NAIVE, with compensated running sums: every addition of
+   * difference coefficients to the running coefficients, and of one lane's
+   * prefix to the next, keeps its rounding error (TwoSum) in a second set of
+   * coefficients that is Taylor-shifted alongside; the field is the sum of
+   * both.  The shifts themselves and the FP32 difference coefficients are not
+   * compensated: a particle's FP32 difference coefficients do not sum to zero,
+   * and that residue of Sec. 4.1's drift remains. */
+  SPHDVR_PREC_FP32_KAHAN = 5
 } sphdvr_precision;
 
 /* Viewing rays.  Basis: f = normalize(target - eye), r = normalize(f x up),
@@ -150,13 +158,19 @@ typedef struct {
                          (0 selects 0.85; values >= 1 turn the rule off) */
   int ctas_per_sm;    /* render-grid CTAs per SM (0: as many as fit; else 1 .. that) */
   int shading;        /* 1: shaded rendering -- the emission of every point is scaled by
-                           ka + kd |n . v|, n the direction of the field's gradient and v the
-                           ray's (a light at the eye); the gradient is reconstructed along the
-                           ray like the field (see sphdvr_lut_set_gradient), which the table
-                           must carry.  FP32_ANCHORED / FP32_NAIVE, through sphdvr_render and
-                           sphdvr_debug_rays only.  0: off (shade_ka / shade_kd ignored) */
+                           ka + kd |dF/dt| / sqrt(|grad F|^2 + g0^2): the cosine between the
+                           field's gradient and the ray (a light at the eye), softened where the
+                           gradient is small against g0 (there the shading tends to ka, and the
+                           rounding noise of a vanishing gradient changes nothing).  The
+                           gradient is reconstructed along the ray like the field (see
+                           sphdvr_lut_set_gradient), which the table must carry.  FP32_ANCHORED
+                           / FP32_NAIVE, through sphdvr_render and sphdvr_debug_rays only.
+                           0: off (the shade_* fields are ignored) */
   float shade_ka;     /* shading: ambient weight, finite and >= 0 */
   float shade_kd;     /* shading: diffuse weight, finite and >= 0 */
+  float shade_g0;     /* shading: softening gradient magnitude g0 (field units per length),
+                         finite and >= 0; 0 gives the plain cosine, which is ill-conditioned
+                         where the gradient vanishes */
 } sphdvr_render_opts;
 
 typedef struct sphdvr_ctx sphdvr_ctx;

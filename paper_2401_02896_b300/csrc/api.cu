@@ -125,7 +125,7 @@ sphdvr_status pack_tf(sphdvr_ctx* ctx, const sphdvr_tf* tf, std::vector<float4>&
 
 sphdvr_status check_opts(sphdvr_ctx* ctx, const sphdvr_render_opts* o) {
   if (!o) return SPHDVR_OK;
-  if (o->precision < 0 || o->precision > 4) return set_err(ctx, SPHDVR_EINVAL, "opts: precision out of range");
+  if (o->precision < 0 || o->precision > 5) return set_err(ctx, SPHDVR_EINVAL, "opts: precision out of range");
   if (o->precision == SPHDVR_PREC_INT64_QUANT &&
       !(o->quant_tau > 0 && std::isfinite(o->quant_tau) && o->quant_sigma > 0 && std::isfinite(o->quant_sigma)))
     return set_err(ctx, SPHDVR_EINVAL, "opts: INT64_QUANT needs finite quant_tau > 0 and quant_sigma > 0");
@@ -146,8 +146,9 @@ sphdvr_status check_opts(sphdvr_ctx* ctx, const sphdvr_render_opts* o) {
   if (o->shading) {
     if (o->precision != SPHDVR_PREC_FP32_ANCHORED && o->precision != SPHDVR_PREC_FP32_NAIVE)
       return set_err(ctx, SPHDVR_EINVAL, "opts: shading needs FP32_ANCHORED or FP32_NAIVE");
-    if (!(o->shade_ka >= 0.f) || !std::isfinite(o->shade_ka) || !(o->shade_kd >= 0.f) || !std::isfinite(o->shade_kd))
-      return set_err(ctx, SPHDVR_EINVAL, "opts: shade_ka and shade_kd must be finite and >= 0");
+    if (!(o->shade_ka >= 0.f) || !std::isfinite(o->shade_ka) || !(o->shade_kd >= 0.f) || !std::isfinite(o->shade_kd) ||
+        !(o->shade_g0 >= 0.f) || !std::isfinite(o->shade_g0 * o->shade_g0))
+      return set_err(ctx, SPHDVR_EINVAL, "opts: shade_ka, shade_kd and shade_g0 must be finite and >= 0");
   }
   return SPHDVR_OK;
 }

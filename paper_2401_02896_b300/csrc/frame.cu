@@ -182,14 +182,16 @@ static int kernel_kind(const sphdvr_render_opts* o) {
     case SPHDVR_PREC_FP64_NAIVE: return kKernF64;
     case SPHDVR_PREC_FP32_REINIT: return kKernReinit;
     case SPHDVR_PREC_INT64_QUANT: return kKernQuant;
+    case SPHDVR_PREC_FP32_KAHAN: return kKernRayCp;
     default: return kKernRay;
   }
 }
 
 // Dynamic shared memory of a render launch.
 static size_t kernel_smem(int kind, int tf_n, bool dbg) {
-  if (kind == kKernRayFB || kind == kKernRayShFB) return ray_smem_bytes(tf_n, 1, true, kind == kKernRayShFB);
-  const bool ray = kind == kKernRay || kind == kKernRaySh;
+  if (kind == kKernRayFB || kind == kKernRayShFB || kind == kKernRayCpFB)
+    return ray_smem_bytes(tf_n, 1, true, kind == kKernRayShFB);
+  const bool ray = kind == kKernRay || kind == kKernRaySh || kind == kKernRayCp;
   const int nw = dbg ? 1 : (ray ? kRayWarps : kRenderWarps);
   return ray ? ray_smem_bytes(tf_n, nw, dbg, kind == kKernRaySh) : render_smem_bytes(tf_n, nw);
 }
@@ -463,6 +465,7 @@ static void common_params(const RenderArgs& a, const FrameWork& w, RenderParams&
   p.gpiece = L->gpiece;
   p.shade_ka = (a.opts && a.opts->shading) ? a.opts->shade_ka : 1.f;
   p.shade_kd = (a.opts && a.opts->shading) ? a.opts->shade_kd : 0.f;
+  p.shade_g2 = (a.opts && a.opts->shading) ? a.opts->shade_g0 * a.opts->shade_g0 : 0.f;
   p.tf_n = a.tf_n;
   p.tf_lo = a.tf_lo;
   p.tf_dv = (a.tf_hi - a.tf_lo) / (a.tf_n - 1);
@@ -505,7 +508,8 @@ static sphdvr_status clear_counters(sphdvr_ctx* ctx, const FrameWork& w, cudaStr
 static sphdvr_status launch_frame(sphdvr_ctx* ctx, const RenderArgs& a, const FrameWork& w, RenderParams p,
                                   bool batch, int grid, cudaStream_t st) {
   const int kind = kernel_kind(a.opts);
-  const bool fb = (kind == kKernRay || kind == kKernRaySh) && w.fb_table && w.fb_list && w.fb_warps > 0;
+  const bool fb = (kind == kKernRay || kind == kKernRaySh || kind == kKernRayCp) && w.fb_table && w.fb_list &&
+                  w.fb_warps > 0;
   p.ray_cap = a.opts ? a.opts->ray_capacity : 0;
   p.ovf = fb ? w.fb_list : nullptr;
   p.ovf_cap = fb ? w.fb_cap : 0;
@@ -513,7 +517,7 @@ static sphdvr_status launch_frame(sphdvr_ctx* ctx, const RenderArgs& a, const Fr
       dispatch_render(ctx, a.lut->D, kind, false, batch, p, grid, kernel_smem(kind, a.tf_n, false), st);
   if (s != SPHDVR_OK || !fb) return s;
   p.scratch = w.fb_table;
-  const int fk = kind == kKernRaySh ? kKernRayShFB : kKernRayFB;
+  const int fk = kind == kKernRaySh ? kKernRayShFB : (kind == kKernRayCp ? kKernRayCpFB : kKernRayFB);
   return dispatch_render(ctx, a.lut->D, fk, false, batch, p, w.fb_warps, kernel_smem(fk, a.tf_n, false), st);
 }
 

@@ -230,10 +230,16 @@ __device__ __forceinline__ int warp_excl_scan(int v, int* total) {
 // GR: shaded rendering -- besides the field, the across-ray gradient's three
 // components are carried through the same knots (channels 1..3 of every
 // polynomial), and the emission is shaded (Conclusion: additive features).
-template <int D, int NW, bool DBG, bool BT, bool FB = false, bool GR = false>
-__global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? (GR ? 1 : kRayMinBlocks) : 1)) k_ray(RenderParams p) {
+// CP: compensated running sums (FP32_KAHAN) -- channel 1 holds the rounding
+// error of every addition of difference coefficients and of lane prefixes
+// (TwoSum), shifted alongside the sum; the field is the sum of both channels.
+template <int D, int NW, bool DBG, bool BT, bool FB = false, bool GR = false, bool CP = false>
+__global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR ? 1 : 2) : kRayMinBlocks) : 1))
+    k_ray(RenderParams p) {
+  static_assert(!(GR && CP), "shading runs on the anchored and plain FP32 recurrences only");
   constexpr bool BIG = DBG || FB;
-  constexpr int NC = GR ? 4 : 1;  // polynomial channels: the field [, the across-ray gradient x, y, z]
+  // polynomial channels: the field [, the across-ray gradient x, y, z | the compensation]
+  constexpr int NC = GR ? 4 : (CP ? 2 : 1);
   constexpr int NP = NC * (D + 1);
   constexpr int WCX = RayCaps<BIG, GR>::WC, ACTX = RayCaps<BIG, GR>::ACT;
   // capacities in force (the frame pass may be given smaller ones, to test the fallback)
@@ -535,8 +541,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? (GR ? 1 : kRayMinB
 #pragma unroll
                 for (int d = 0; d <= D; ++d) z0.c[d] = 0.f;
                 const Acc g = composite_piece_v<D>(z0, L, tfc, Acc{0.f, 0.f, 0.f, 0.f});
-                // a zero field has a zero gradient: shading ka + kd there
-                float w = __expf(-tau_ray) * (GR ? p.shade_ka + p.shade_kd : 1.f);
+                // a zero field has a zero gradient: the shading factor is ka with a
+                // softening gradient g0 > 0, ka + kd without one
+                float w = __expf(-tau_ray) * (GR ? (p.shade_g2 > 0.f ? p.shade_ka : p.shade_ka + p.shade_kd) : 1.f);
                 col[0] += w * g.r;
                 col[1] += w * g.g;
                 col[2] += w * g.b;
@@ -801,6 +808,38 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? (GR ? 1 : kRayMinB
 #pragma unroll
             for (int ch = 0; ch < NC; ++ch) taylor_shift<D, float>(q + ch * (D + 1), sft);
           };
+          // X += the difference coefficients dl of one knot (compensated: TwoSum into channel 1)
+          auto add_deltas = [&](float* X, const float* dl) {
+            if (CP) {
+#pragma unroll
+              for (int d = 1; d <= D; ++d) {
+                const float a = X[d], b = dl[d - 1];
+                const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+                X[d] = s;
+                X[D + 1 + d] += __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+              }
+            } else {
+#pragma unroll
+              for (int ch = 0; ch < NC; ++ch)
+#pragma unroll
+                for (int d = 1; d <= D; ++d) X[ch * (D + 1) + d] += dl[ch * D + d - 1];
+            }
+          };
+          // X += Y, polynomials of every channel (compensated: TwoSum of the sums, errors added)
+          auto add_poly = [&](float* X, const float* Y) {
+            if (CP) {
+#pragma unroll
+              for (int d = 0; d <= D; ++d) {
+                const float a = X[d], b = Y[d];
+                const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+                X[d] = s;
+                X[D + 1 + d] += Y[D + 1 + d] + __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+              }
+            } else {
+#pragma unroll
+              for (int q = 0; q < NP; ++q) X[q] += Y[q];
+            }
+          };
           const float ufirst = has ? uat(i0) : 0.f;
           float P[NP];
           float Uend;
@@ -816,10 +855,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? (GR ? 1 : kRayMinB
               if (i > i0) shift_all(agg, ur - ulast);
               float dl[NC * D];
               deltas(i, dl);
-#pragma unroll
-              for (int ch = 0; ch < NC; ++ch)
-#pragma unroll
-                for (int d = 1; d <= D; ++d) agg[ch * (D + 1) + d] += dl[ch * D + d - 1];
+              add_deltas(agg, dl);
               ulast = ur;
               // mark the knot processed: a starter's first knot brings the
               // particle into the active set (its later knots in this window
@@ -896,8 +932,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? (GR ? 1 : kRayMinB
               if (lane >= o2 && oh) {
                 if (sh) {
                   shift_all(oa, se - oe);
-#pragma unroll
-                  for (int q = 0; q < NP; ++q) sa[q] += oa[q];
+                  add_poly(sa, oa);
                 } else {
 #pragma unroll
                   for (int q = 0; q < NP; ++q) sa[q] = oa[q];
@@ -918,8 +953,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? (GR ? 1 : kRayMinB
             shift_all(P, ufirst);
             if (ph) {
               shift_all(pa, ufirst - pe);
-#pragma unroll
-              for (int q = 0; q < NP; ++q) P[q] += pa[q];
+              add_poly(P, pa);
             }
           }
           PT_END(7)
@@ -976,14 +1010,15 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? (GR ? 1 : kRayMinB
                   if (idx >= 0) atomicAdd(act_jk_ptr(A, idx), 1 << 16);
                 }
               }
-#pragma unroll
-              for (int ch = 0; ch < NC; ++ch)
-#pragma unroll
-                for (int d = 1; d <= D; ++d) P[ch * (D + 1) + d] += dl[ch * D + d - 1];
+              add_deltas(P, dl);
               lastu = ua;
 #pragma unroll
               for (int q = 0; q < NP; ++q) Pc[q] = P[q];
               ub = i + 1 < nc ? uat(i + 1) : Uend;
+            }
+            if (CP) {  // the field: sum and compensation
+#pragma unroll
+              for (int d = 0; d <= D; ++d) Pc[d] += Pc[D + 1 + d];
             }
             if (DBG && p.dbg_field && ub > ua) {
               const long long row = i < 0 ? dbg_np : dbg_base++;
@@ -1002,7 +1037,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? (GR ? 1 : kRayMinB
             if (ub > a0) {
               if (a0 > ua) shift_all(Pc, a0 - ua);
               if (GR)
-                composite_piece_sh_inl<D>(Pc, Pc + D + 1, ub - a0, tfc, tau_l, col_l, p.shade_ka, p.shade_kd);
+                composite_piece_sh_inl<D>(Pc, Pc + D + 1, ub - a0, tfc, tau_l, col_l, p.shade_ka, p.shade_kd,
+                                          p.shade_g2);
               else
                 composite_piece_inl<D>(Pc, ub - a0, tfc, tau_l, col_l);
             }

@@ -63,6 +63,8 @@ constexpr int kKernQuant = 3;   // INT64_QUANT: k_render's quantised integer pat
 constexpr int kKernRayFB = 4;   // k_ray's fallback pass over the rays its frame pass abandoned
 constexpr int kKernRaySh = 5;   // shaded rendering: k_ray with the across-ray gradient (FP32 modes)
 constexpr int kKernRayShFB = 6; // its fallback pass
+constexpr int kKernRayCp = 7;   // FP32_KAHAN: k_ray with compensated running sums
+constexpr int kKernRayCpFB = 8; // its fallback pass
 // per-ray global scratch (32-bit words): particle records (4 words), table
 // entries, active list, free stack, two buffers of the waiting list (key, value)
 constexpr int kTableWords = 11 * kCap;
@@ -105,10 +107,10 @@ struct RenderParams {
   const float* jump;
   const float* piece;
   // gradient tables (shaded rendering): difference coefficients and pieces of
-  // G_L = w'(rho)/rho on the same knots, and the shading ka + kd |n . v|
+  // G_L = w'(rho)/rho on the same knots, and the shading ka + kd |F'| / sqrt(|grad F|^2 + g0^2)
   const float* gjump;
   const float* gpiece;
-  float shade_ka, shade_kd;
+  float shade_ka, shade_kd, shade_g2;  // shading: ka, kd and the squared softening gradient g0^2
   // transfer function
   int tf_n;
   float tf_lo, tf_inv_dv, tf_dv;
@@ -207,16 +209,17 @@ __device__ __forceinline__ int tf_cell(const TfCtx& t, float f) {
 // lying within TF cell c.  tau_l: accumulated optical depth before the
 // sub-piece (local to the lane); C: emitted colour (un-attenuated by the
 // lane's incoming transmittance).
-// Shading factor ka + kd |n . v| at y of a piece (gradient extension): the
-// gradient is F'(y) v + (GQ_x, GQ_y, GQ_z)(y), the across-ray part being
-// perpendicular to v; where it vanishes, ka + kd.
+// Shading factor ka + kd |F'(y)| / sqrt(|grad F|^2 + g0^2) at y of a piece (gradient
+// extension): the gradient is F'(y) v + (GQ_x, GQ_y, GQ_z)(y), the across-ray part
+// being perpendicular to v; g2 = g0^2 softens the cosine where the gradient is small
+// (with g0 = 0, a vanishing gradient gives ka + kd).
 template <int D>
-__device__ __forceinline__ float shade_factor(const float* Q, const float* GQ, float y, float ka, float kd) {
+__device__ __forceinline__ float shade_factor(const float* Q, const float* GQ, float y, float ka, float kd, float g2) {
   float dF = D * Q[D];
 #pragma unroll
   for (int d = D - 1; d >= 1; --d) dF = fmaf(dF, y, d * Q[d]);
   const float gx = horner<D>(GQ, y), gy = horner<D>(GQ + D + 1, y), gz = horner<D>(GQ + 2 * (D + 1), y);
-  const float n2 = fmaf(dF, dF, fmaf(gx, gx, fmaf(gy, gy, gz * gz)));
+  const float n2 = fmaf(dF, dF, fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, g2))));
   return n2 > 0.f ? fmaf(kd, fabsf(dF) * rsqrtf(n2), ka) : ka + kd;
 }
 
@@ -224,7 +227,8 @@ __device__ __forceinline__ float shade_factor(const float* Q, const float* GQ, f
 // polynomials GQ[3][D+1] expanded at the same point as Q.
 template <int D, bool SH = false>
 __device__ __forceinline__ void composite_cell(const float* Q, float L, int c, const TfCtx& t, float& tau_l,
-                                               float* C, const float* GQ = nullptr, float ka = 1.f, float kd = 0.f) {
+                                               float* C, const float* GQ = nullptr, float ka = 1.f, float kd = 0.f,
+                                               float g2 = 0.f) {
   if (!(L > 0.f)) return;
   if (!SH && (c < 0 || c >= t.n - 1)) {
     float4 k = t.tf[c < 0 ? 0 : t.n - 1];
@@ -264,8 +268,8 @@ __device__ __forceinline__ void composite_cell(const float* Q, float L, int c, c
     float e1 = __expf(-(tau_l + a.w * y1 + s1 * G1));
     float sg0 = fmaxf(a.w + s1 * g0, 0.f) * e0, sg1 = fmaxf(a.w + s1 * g1, 0.f) * e1;
     if (SH) {
-      sg0 *= shade_factor<D>(Q, GQ, y0, ka, kd);
-      sg1 *= shade_factor<D>(Q, GQ, y1, ka, kd);
+      sg0 *= shade_factor<D>(Q, GQ, y0, ka, kd, g2);
+      sg1 *= shade_factor<D>(Q, GQ, y1, ka, kd, g2);
     }
     float hw = 0.5f * h;
     C[0] += hw * ((a.x + cr * g0) * sg0 + (a.x + cr * g1) * sg1);
@@ -279,7 +283,7 @@ __device__ __forceinline__ void composite_cell(const float* Q, float L, int c, c
 template <int D, bool SH = false>
 __device__ __forceinline__ void composite_piece_slow_body(const float* P, float L, float f0, const TfCtx& t,
                                                           float& tau_l, float* C, const float* GP = nullptr,
-                                                          float ka = 1.f, float kd = 0.f);
+                                                          float ka = 1.f, float kd = 0.f, float g2 = 0.f);
 template <int D>
 __device__ __noinline__ void composite_piece_slow(const float* P, float L, float f0, const TfCtx& t, float& tau_l,
                                                    float* C) {
@@ -312,7 +316,7 @@ __device__ __forceinline__ void composite_piece(const float* P, float L, const T
 template <int D, bool SH>
 __device__ __forceinline__ void composite_piece_slow_body(const float* P, float L, float f0, const TfCtx& t,
                                                           float& tau_l, float* C, const float* GP, float ka,
-                                                          float kd) {
+                                                          float kd, float g2) {
   const int NS = 8;
   const float step = L / NS;
   float ya = 0.f, fa = f0;
@@ -364,7 +368,7 @@ __device__ __forceinline__ void composite_piece_slow_body(const float* P, float 
         for (int i = 0; i < 3 * (D + 1); ++i) GQ[i] = GP[i];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) taylor_shift<D, float>(GQ + ch * (D + 1), ycur);
-        composite_cell<D, true>(Q, yend - ycur, ccur, t, tau_l, C, GQ, ka, kd);
+        composite_cell<D, true>(Q, yend - ycur, ccur, t, tau_l, C, GQ, ka, kd, g2);
       } else {
         composite_cell<D>(Q, yend - ycur, ccur, t, tau_l, C);
       }
@@ -416,10 +420,10 @@ struct Poly3 {
 
 template <int D>
 __device__ __noinline__ Acc composite_piece_slow_sh_v(Poly<D> P, Poly3<D> G, float L, float f0, TfCtx t, Acc a,
-                                                      float ka, float kd) {
+                                                      float ka, float kd, float g2) {
   float C[3] = {a.r, a.g, a.b};
   float tau = a.tau;
-  composite_piece_slow_body<D, true>(P.c, L, f0, t, tau, C, G.c, ka, kd);
+  composite_piece_slow_body<D, true>(P.c, L, f0, t, tau, C, G.c, ka, kd, g2);
   return Acc{tau, C[0], C[1], C[2]};
 }
 
@@ -427,7 +431,7 @@ __device__ __noinline__ Acc composite_piece_slow_sh_v(Poly<D> P, Poly3<D> G, flo
 // one transfer-function cell inline, crossings out of line.
 template <int D>
 __device__ __forceinline__ void composite_piece_sh_inl(const float* P, const float* GP, float L, const TfCtx& t,
-                                                       float& tau_l, float* C, float ka, float kd) {
+                                                       float& tau_l, float* C, float ka, float kd, float g2) {
   if (!(L > 0.f)) return;
   const float f0 = P[0], f1 = horner<D>(P, L);
   float b2 = 0.f, Lp = 1.f;
@@ -439,7 +443,7 @@ __device__ __forceinline__ void composite_piece_sh_inl(const float* P, const flo
   const float dev = 0.125f * L * L * b2;
   const int ca = tf_cell(t, fminf(f0, f1) - dev), cb = tf_cell(t, fmaxf(f0, f1) + dev);
   if (ca == cb) {
-    composite_cell<D, true>(P, L, ca, t, tau_l, C, GP, ka, kd);
+    composite_cell<D, true>(P, L, ca, t, tau_l, C, GP, ka, kd, g2);
     return;
   }
   Poly<D> pp;
@@ -448,7 +452,7 @@ __device__ __forceinline__ void composite_piece_sh_inl(const float* P, const flo
   for (int d = 0; d <= D; ++d) pp.c[d] = P[d];
 #pragma unroll
   for (int i = 0; i < 3 * (D + 1); ++i) gg.c[i] = GP[i];
-  const Acc r = composite_piece_slow_sh_v<D>(pp, gg, L, f0, t, Acc{tau_l, C[0], C[1], C[2]}, ka, kd);
+  const Acc r = composite_piece_slow_sh_v<D>(pp, gg, L, f0, t, Acc{tau_l, C[0], C[1], C[2]}, ka, kd, g2);
   tau_l = r.tau;
   C[0] = r.r;
   C[1] = r.g;

@@ -5,8 +5,8 @@
 // render_occupancy_d<D>), so that the six degrees compile in parallel and
 // share one source.
 //
-// Precision modes FP32_ANCHORED and FP32_NAIVE run the lean window kernel
-// k_ray (ray.cuh); FP64_NAIVE, FP32_REINIT and INT64_QUANT run k_render
+// Precision modes FP32_ANCHORED, FP32_NAIVE and FP32_KAHAN run the lean window
+// kernel k_ray (ray.cuh); FP64_NAIVE, FP32_REINIT and INT64_QUANT run k_render
 // (render.cuh), which carries their variants.
 #include "ray.cuh"
 
@@ -52,9 +52,10 @@ sphdvr_status launch_old(sphdvr_ctx* ctx, const RenderParams& p, int grid, size_
   return launch_kernel(ctx, k_render<kD, S, NW, DBG, RE, BT, QT>, NW, p, grid, smem, st, "k_render");
 }
 
-template <int NW, bool DBG, bool BT, bool FB = false, bool GR = false>
+template <int NW, bool DBG, bool BT, bool FB = false, bool GR = false, bool CP = false>
 sphdvr_status launch_ray(sphdvr_ctx* ctx, const RenderParams& p, int grid, size_t smem, cudaStream_t st) {
-  return launch_kernel(ctx, k_ray<kD, NW, DBG, BT, FB, GR>, NW, p, grid, smem, st, FB ? "k_ray fallback" : "k_ray", FB);
+  return launch_kernel(ctx, k_ray<kD, NW, DBG, BT, FB, GR, CP>, NW, p, grid, smem, st,
+                       FB ? "k_ray fallback" : "k_ray", FB);
 }
 
 template <typename Kern>
@@ -84,6 +85,13 @@ sphdvr_status SPHDVR_CAT(launch_render_d, SPHDVR_D)(sphdvr_ctx* ctx, int kind, b
     case kKernRayShFB:
       if (batch) return set_err(ctx, SPHDVR_EINVAL, "render: shading is not available in batched launches");
       return launch_ray<1, false, false, true, true>(ctx, p, grid, smem, st);
+    case kKernRayCp:  // compensated running sums
+      if (dbg) return launch_ray<1, true, false, false, false, true>(ctx, p, grid, smem, st);
+      if (batch) return launch_ray<kRayWarps, false, true, false, false, true>(ctx, p, grid, smem, st);
+      return launch_ray<kRayWarps, false, false, false, false, true>(ctx, p, grid, smem, st);
+    case kKernRayCpFB:
+      if (batch) return launch_ray<1, false, true, true, false, true>(ctx, p, grid, smem, st);
+      return launch_ray<1, false, false, true, false, true>(ctx, p, grid, smem, st);
     case kKernQuant:  // integer knots and coefficients, FP32 compositing
       if (dbg) return launch_old<float, 1, true, false, false, true>(ctx, p, grid, smem, st);
       if (batch) return launch_old<float, kRenderWarps, false, false, true, true>(ctx, p, grid, smem, st);
@@ -108,6 +116,9 @@ int SPHDVR_CAT(render_occupancy_d, SPHDVR_D)(int kind, bool dbg, size_t smem) {
     case kKernRaySh:
       return dbg ? occupancy_of(k_ray<kD, 1, true, false, false, true>, 1, smem)
                  : occupancy_of(k_ray<kD, kRayWarps, false, false, false, true>, kRayWarps, smem);
+    case kKernRayCp:
+      return dbg ? occupancy_of(k_ray<kD, 1, true, false, false, false, true>, 1, smem)
+                 : occupancy_of(k_ray<kD, kRayWarps, false, false, false, false, true>, kRayWarps, smem);
     case kKernQuant:
       return dbg ? occupancy_of(k_render<kD, float, 1, true, false, false, true>, 1, smem)
                  : occupancy_of(k_render<kD, float, kRenderWarps, false, false, false, true>, kRenderWarps, smem);

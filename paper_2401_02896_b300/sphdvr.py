@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libsphdvr.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, EOVERFLOW, EDEVICE, ENOTFOUND = range(9)
 KERNELS = {"m4": 0, "wendland_c2": 1, "wendland_c4": 2, "poly6": 3}
-PRECISIONS = {"fp32_anchored": 0, "fp32_naive": 1, "fp64_naive": 2, "fp32_reinit": 3, "int64_quant": 4}
+PRECISIONS = {"fp32_anchored": 0, "fp32_naive": 1, "fp64_naive": 2, "fp32_reinit": 3, "int64_quant": 4,
+              "fp32_kahan": 5}
 
 
 class SphdvrError(RuntimeError):
@@ -69,6 +70,7 @@ class RenderOpts(ctypes.Structure):
         ("shading", ctypes.c_int),
         ("shade_ka", ctypes.c_float),
         ("shade_kd", ctypes.c_float),
+        ("shade_g0", ctypes.c_float),
     ]
 
 
@@ -229,6 +231,7 @@ def opts_struct(opts=None):
     o.shading = int(opts.get("shading", 0))
     o.shade_ka = float(opts.get("shade_ka", 0.0))
     o.shade_kd = float(opts.get("shade_kd", 0.0))
+    o.shade_g0 = float(opts.get("shade_g0", 0.0))
     return o
 
 

@@ -62,7 +62,8 @@ def _batch(S, torch, ctx, ds, lt, cams, tf, opts):
 
 
 @pytest.mark.parametrize("opts", [None, dict(precision="fp64_naive"), dict(precision="fp32_reinit", reinit_dt=0.05),
-                                  dict(persistent=0)], ids=["anchored", "fp64", "reinit", "static"])
+                                  dict(precision="fp32_kahan"), dict(persistent=0)],
+                         ids=["anchored", "fp64", "reinit", "kahan", "static"])
 def test_batch_equals_separate_frames(env, opts):
     S, torch, ctx, lut, lt, P, ds, _, tf, _ = env
     cams = _cams()

@@ -1,7 +1,9 @@
 """Shaded rendering on the GPU against the oracle: the across-ray gradient reconstructed along every ray from
 the particles' gradient contributions (the Conclusion: features generated additively from the particle
 contributions, gradients among them, are approximated like the field), and emission shaded by
-ka + kd |n . v| (a light at the eye; a reading).
+ka + kd |dF/dt| / sqrt(|grad F|^2 + g0^2) (a light at the eye, the cosine softened where the gradient is
+small against g0; a reading).  g0 here is 1e-3 of the RMS across-ray gradient on the oracle's rays: above the
+FP32 noise of a vanishing gradient, far below the gradients that shape the image.
 
 * the field rows of the shaded kernel equal the oracle's within the field tolerance (the extra channels
   change nothing of the field);
@@ -73,7 +75,11 @@ def setup(S):
     cam = SY.orbit_camera(res, res)
     tf = SY.tf_density(P["value"])
     pix = SY.pixel_sample(res, res, 48, seed=57)
-    yield dict(P=P, D=D, lut=lut, G=G, ctx=ctx, ds=ds, lt=lt, cam=cam, tf=tf, pix=pix, res=res)
+    R0 = oracle.render(P, lut, cam, tf, pix[:12], field_cap=1 << 16, grad=G)
+    g = np.concatenate([R0["gfield"][r, :R0["stats"][r, 5], :, 0] for r in range(12)])
+    g0 = 1e-3 * float(np.sqrt((g ** 2).sum(axis=1).mean()))
+    shade = dict(shading=1, shade_ka=KA, shade_kd=KD, shade_g0=g0)
+    yield dict(P=P, D=D, lut=lut, G=G, ctx=ctx, ds=ds, lt=lt, cam=cam, tf=tf, pix=pix, res=res, g0=g0, shade=shade)
     S.sphdvr_dataset_free(ds)
     S.sphdvr_lut_free(lt)
     S.sphdvr_destroy(ctx)
@@ -83,9 +89,9 @@ def test_shaded_field_gradient_and_pixels_match_the_oracle(S, setup):
     s = setup
     D, pix = s["D"], s["pix"]
     cap = 1 << 16
-    R = oracle.render(s["P"], s["lut"], s["cam"], s["tf"], pix, field_cap=cap, grad=s["G"], shade=(KA, KD))
-    g = S.sphdvr_debug_rays_grad(s["ctx"], s["ds"], s["lt"], s["cam"], s["tf"],
-                                 dict(ert_eps=0.0, shading=1, shade_ka=KA, shade_kd=KD), pix, cap, D)
+    R = oracle.render(s["P"], s["lut"], s["cam"], s["tf"], pix, field_cap=cap, grad=s["G"], shade=(KA, KD, s["g0"]))
+    g = S.sphdvr_debug_rays_grad(s["ctx"], s["ds"], s["lt"], s["cam"], s["tf"], dict(ert_eps=0.0, **s["shade"]),
+                                 pix, cap, D)
     assert not g["overflow"]
     fe, ge = [], []
     for r in range(len(pix)):
@@ -94,7 +100,7 @@ def test_shaded_field_gradient_and_pixels_match_the_oracle(S, setup):
         n_o, n_g = R["stats"][r, 5], g["counts"][r, 2]
         fe.append(field_rel_l2(g["field"][r, :n_g], R["field"][r, :n_o], D))
         ge.append(grad_rel_l2(g["field"][r, :n_g], g["grad"][r, :n_g], R["field"][r, :n_o], R["gfield"][r, :n_o], D))
-    print("field worst %.3g, gradient worst %.3g median %.3g" % (max(fe), max(ge), np.median(ge)))
+    print("g0 %.4g: field worst %.3g, gradient worst %.3g median %.3g" % (s["g0"], max(fe), max(ge), np.median(ge)))
     assert max(fe) <= FIELD_REL_L2
     assert max(ge) <= GRAD_REL_L2
     pe = np.abs(g["rgba"].astype(np.float64) - R["rgba"]).max()
@@ -123,7 +129,7 @@ def test_shaded_frame_matches_the_parity_hook_and_the_fallback_pass(S, setup):
 
     s = setup
     res, pix = s["res"], s["pix"]
-    o = dict(ert_eps=0.0, shading=1, shade_ka=KA, shade_kd=KD)
+    o = dict(ert_eps=0.0, **s["shade"])
     img = torch.zeros((res, res, 4), dtype=torch.float32, device="cuda")
     S.sphdvr_render(s["ctx"], s["ds"], s["lt"], s["cam"], s["tf"], o, img.data_ptr())
     torch.cuda.synchronize()
@@ -161,7 +167,8 @@ def test_shading_argument_errors(S, setup):
         assert e.value.status == S.EINVAL
     finally:
         S.sphdvr_lut_free(lt2)
-    for bad in (dict(shading=1, precision="fp64_naive"), dict(shading=2), dict(shading=1, shade_kd=-1.0)):
+    for bad in (dict(shading=1, precision="fp64_naive"), dict(shading=2), dict(shading=1, shade_kd=-1.0),
+                dict(shading=1, shade_g0=float("inf"))):
         with pytest.raises(S.SphdvrError) as e:
             S.sphdvr_render(s["ctx"], s["ds"], s["lt"], s["cam"], s["tf"], bad, out.data_ptr())
         assert e.value.status == S.EINVAL
