@@ -11,9 +11,10 @@ rays, worst and median absolute pixel error.  What must hold:
   reinitialisations: at D = 4 the 0.02 spacing, four times the smallest h, reached 2.6e-5 on the worst ray);
 * the plain recurrences (FP32, and FP64 running coefficients over FP32 difference coefficients) drift:
   their field error is larger than the anchored one (Sec. 4.1 "sprinkling");
-* FP32 with compensated running sums (TwoSum, the compensation shifted alongside) drifts too, no less than
-  the plain FP32 recurrence's tenth: the residue of each finished particle's FP32 difference coefficients,
-  not the summation's rounding, drives the drift;
+* FP32 with compensated running sums (TwoSum, the compensation shifted alongside) drifts too: it lowers the
+  plain FP32 recurrence's field error (by 4x to 35x on the 1M set) but stays above
+  the anchored path's, and from D = 2 on above the field tolerance: the residue of each finished particle's
+  FP32 difference coefficients, which no summation order removes, drives the drift;
 * the quantised integer path (Sec. 4.2-4.4, 64 bits, quanta of the data set) renders without a flag; its
   error is the quantisation's (one length quantum serves particles whose h spans two decades) and is
   reported, bounded only against gross failure here.
@@ -85,5 +86,7 @@ def test_precision_degree_sweep():
         assert ri["field_worst"] <= FIELD_REL_L2 and ri["pixel_worst"] <= PIXEL_ABS, ri
         assert by[(D, "fp32_naive")]["field_worst"] > a["field_worst"]
         k = by[(D, "fp32_kahan")]
-        assert k["field_worst"] > a["field_worst"] and k["field_worst"] > 0.1 * by[(D, "fp32_naive")]["field_worst"], k
+        assert a["field_worst"] < k["field_worst"] <= by[(D, "fp32_naive")]["field_worst"], k
+        if D >= 2:
+            assert k["field_worst"] > FIELD_REL_L2, k
         assert by[(D, "int64_quant")]["pixel_worst"] < 0.05, by[(D, "int64_quant")]
