@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
 #pragma unroll
           for (int i = 0; i < NP; ++i) acc[i] = 0.f;
           float cap2 = kInf, hmin_new = kInf;
-          int T_all = 0;
+          int T_all = 0, ns = 0, ns_as = 0;
 #pragma unroll 1
           for (int gen = 0;; ++gen) {
             T_all = 0;
@@ -677,8 +677,12 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
             }
             if (gen == 0) nal = wr;
             __syncwarp();
-            // the starters: waiting particles whose first knot lies below U
-            const int ns = warp_count_below(WK, whead, nwait, Ta.hi + U);
+            // the starters: waiting particles whose first knot lies below U;
+            // each gets an entry of the active set now (knots processed 0), so
+            // that its knots index the active set like every other knot; the
+            // entry is kept if its first knot turns out to be processed
+            ns = warp_count_below(WK, whead, nwait, Ta.hi + U);
+            ns_as = 0;
 #pragma unroll 1
             for (int b0 = 0; b0 < ns; b0 += 32) {
               const int ii = b0 + lane;
@@ -686,10 +690,13 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
               if (e >= 0 && ((stb[e >> 5] >> (e & 31)) & 1u)) e = -1;  // started already (FP32 ties)
               int ne = 0;
               float uk[5];
+              float4 E = make_float4(0.f, 0.f, 1.f, 0.f);
+              int je = 0;
               if (e >= 0) {
-                const float4 E = s_rec[e];
+                E = s_rec[e];
+                je = s_j[e];
                 float sg[5];
-                knot_sigmas(K, __ldg(p.theta + s_j[e]), sg);
+                knot_sigmas(K, __ldg(p.theta + je), sg);
                 const float base = (E.x - Ta.hi) + (E.y - Ta.lo);
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
@@ -700,6 +707,23 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
                 // gamma h, or by its first knot when that lies farther
                 if (ne > 0) cap2 = fminf(cap2, fmaxf(uk[0], gam * E.z));
               }
+              const unsigned sm = __ballot_sync(kFull, ne > 0);
+              const int ni = nal + ns_as + __popc(sm & lanemask_lt());
+              ns_as += __popc(sm);
+              if (ne > 0) {
+                if (ni < cap_act) {
+                  act_put(A, ni, E, je);
+                  if (GR) {
+                    const float4 d4 = s_dp[e];
+                    act_putd(A, ni, make_float3(d4.x, d4.y, d4.z));
+                  }
+                  s_map[e] = ni;
+                } else {
+                  rf |= 1;  // the active set is full
+                  s_map[e] = -1;
+                  ne = 0;
+                }
+              }
               int tot;
               const int off = T_all + warp_excl_scan(ne, &tot);
 #pragma unroll
@@ -707,7 +731,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
                 const int pos = off + k;
                 if (k < ne && pos < kRayNK) {
                   nk0[pos] = uk[k];
-                  nv0[pos] = (e << 4) | 8 | k;
+                  nv0[pos] = (ni << 4) | k;
                 }
               }
               T_all += tot;
@@ -752,10 +776,9 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
             break;  // nothing final below F: wait for more particles
           }
 
-          // (the knots are marked processed in the scan's first pass below: a
-          // starter whose first knot is in the window joins the active set there)
-          if (lane == 0) rh[256] = nal;  // next free index of the active set
-          __syncwarp();
+          // (the knots are marked processed in the scan's first pass below; the
+          // starters given entries in the generation pass are part of the set)
+          const int nal_w = nal + ns_as;
           PT_END(5)
           PT_BEGIN
 
@@ -775,16 +798,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
             float h, c;
             int j;
             float3 dp = make_float3(0.f, 0.f, 0.f);
-            if (vv & 8) {
-              const float4 E = s_rec[vv >> 4];
-              h = E.z;
-              c = E.w;
-              j = s_j[vv >> 4];
-              if (GR) {
-                const float4 d4 = s_dp[vv >> 4];
-                dp = make_float3(d4.x, d4.y, d4.z);
-              }
-            } else {
+            {
               const int idx = vv >> 4;
               float4 E;
               int jk;
@@ -855,33 +869,35 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
               if (i > i0) shift_all(agg, ur - ulast);
               float dl[NC * D];
               deltas(i, dl);
+              const int vv = GV[i];
               add_deltas(agg, dl);
               ulast = ur;
-              // mark the knot processed: a starter's first knot brings the
-              // particle into the active set (its later knots in this window
-              // are counted in the second pass, once every starter is in);
-              // an active particle's knot increments its count
-              const int vv = GV[i], k = vv & 7;
+              // mark the knot processed (a starter's first knot starts it)
+              const int k = vv & 7;
               nf += k == 0;
               nl += k == K;
-              if ((vv & 15) == 8) {
-                const int e = vv >> 4;
-                const int ni = atomicAdd(rh + 256, 1);
-                const float4 E = s_rec[e];
-                if (ni < cap_act) {
-                  act_put(A, ni, E, s_j[e] | (1 << 16));
-                  if (GR) {
-                    const float4 d4 = s_dp[e];
-                    act_putd(A, ni, make_float3(d4.x, d4.y, d4.z));
+              atomicAdd(act_jk_ptr(A, vv >> 4), 1 << 16);
+            }
+            __syncwarp();
+            // the starters whose first knot was processed leave the waiting
+            // list (started bit); the entries of the others become holes
+            // (dropped by the next window's compaction)
+#pragma unroll 1
+            for (int b0 = 0; b0 < ns; b0 += 32) {
+              const int ii = b0 + lane;
+              const int e = ii < ns ? WV[whead + ii] : -1;
+              if (e >= 0 && !((stb[e >> 5] >> (e & 31)) & 1u)) {
+                const int ni = s_map[e];
+                if (ni >= 0) {
+                  int* jp = act_jk_ptr(A, ni);
+                  const int jk = *jp;
+                  if ((jk >> 16) & 15) {
+                    atomicOr(stb + (e >> 5), 1u << (e & 31));
+                    hmin_new = fminf(hmin_new, s_rec[e].z);
+                  } else {
+                    *jp = jk | (15 << 16);
                   }
-                  s_map[e] = ni;
-                } else {
-                  s_map[e] = -1;
                 }
-                hmin_new = fminf(hmin_new, E.z);
-                atomicOr(stb + (e >> 5), 1u << (e & 31));
-              } else if (!(vv & 8)) {
-                atomicAdd(act_jk_ptr(A, vv >> 4), 1 << 16);
               }
             }
             nf = warp_sum_i(nf);
@@ -902,7 +918,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
             ++why_n[why];
 #endif
             __syncwarp();
-            nal = rh[256];
+            nal = nal_w;
             if (nal > cap_act) {
               rf |= 1;
               nal = cap_act;
@@ -1002,14 +1018,6 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
               if (i > i0) shift_all(P, ua - lastu);
               float dl[NC * D];
               deltas(i, dl);
-              {
-                // a starter's later knots in this window: count them on its new entry
-                const int vv = GV[i];
-                if ((vv & 8) && (vv & 7)) {
-                  const int idx = s_map[vv >> 4];
-                  if (idx >= 0) atomicAdd(act_jk_ptr(A, idx), 1 << 16);
-                }
-              }
               add_deltas(P, dl);
               lastu = ua;
 #pragma unroll

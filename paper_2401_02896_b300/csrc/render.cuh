@@ -244,25 +244,27 @@ __device__ __forceinline__ void composite_cell(const float* Q, float L, int c, c
   const bool clamp = c < 0 || c >= t.n - 1;
   float4 a = t.tf[clamp ? (c < 0 ? 0 : t.n - 1) : c], b = clamp ? a : t.tf[c + 1];
   float vc = clamp ? 0.f : t.lo + c * t.dv;
-  float g[D + 1];
+  float g[D + 1], gi[D + 1];  // g - v_c, and its antiderivative's coefficients over y (gi_d = g_d / (d + 1))
 #pragma unroll
   for (int d = 0; d <= D; ++d) g[d] = Q[d];
   g[0] -= vc;
+#pragma unroll
+  for (int d = 0; d <= D; ++d) gi[d] = g[d] * (1.f / (d + 1));
   float s1 = (b.w - a.w) * t.inv_dv;
   float cr = (b.x - a.x) * t.inv_dv, cg = (b.y - a.y) * t.inv_dv, cb = (b.z - a.z) * t.inv_dv;
   // sub-divide when the sub-piece is optically thick, so that 2-point
   // Gauss-Legendre stays accurate
-  float tauL = a.w * L + s1 * horner_int<D>(g, L);
+  float tauL = a.w * L + s1 * (L * horner<D>(gi, L));
   int ns = 1;
   if (tauL > 0.25f) ns = min(32, (int)ceilf(tauL * 4.f));
-  float h = L / ns;
+  const float h = ns == 1 ? L : L / ns;
   const float x0 = 0.21132486540518713f, x1 = 0.78867513459481287f;
   float Gprev = 0.f;
 #pragma unroll 1
   for (int s = 0; s < ns; ++s) {
     float ya = s * h;
     float y0 = ya + x0 * h, y1 = ya + x1 * h;
-    float G0 = horner_int<D>(g, y0), G1 = horner_int<D>(g, y1);
+    float G0 = y0 * horner<D>(gi, y0), G1 = y1 * horner<D>(gi, y1);
     float g0 = horner<D>(g, y0), g1 = horner<D>(g, y1);
     float e0 = __expf(-(tau_l + a.w * y0 + s1 * G0));
     float e1 = __expf(-(tau_l + a.w * y1 + s1 * G1));
