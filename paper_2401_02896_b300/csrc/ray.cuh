@@ -51,6 +51,7 @@ constexpr int kRayWarps = 4;             // warps (rays in flight) per CTA
 constexpr int kRayMinBlocks = SPHDVR_RAY_MINB;  // CTAs per SM the register budget is set for
 constexpr int kRayNK = SPHDVR_RAY_NK;    // window / new-particle buffer (knots)
 constexpr int kRayWcap = kRayNK - 64;  // knots composited per window
+constexpr int kRayStats = 12;          // the warp's statistics, summed over its rays (shared memory)
 
 // Per-ray capacities.  The frame pass holds up to 4096 waiting particles
 // (gathered, not started) and 4096 active ones per ray; a ray that needs more
@@ -65,8 +66,9 @@ struct RayCaps {
   static constexpr int ACT = BIG ? 16384 : 4096;  // active particles in all (beyond kRayAS in global memory)
   // per-warp shared memory: active records (t_chi hi, t_chi lo, h, c, j | done << 16
   // [, d_x, d_y, d_z]), the window / new-particle buffers (two key/value pairs of
-  // kRayNK entries), the sort histogram (+ scratch words), the started bits of the waiting slots
-  static constexpr int SMEM = kRayAS * (GR ? 32 : 20) + 4 * kRayNK * 4 + (256 + 32) * 4 + (WC / 32) * 4;
+  // kRayNK entries), the sort histogram (+ scratch words), the started bits of the waiting slots, the
+  // warp's frame statistics
+  static constexpr int SMEM = kRayAS * (GR ? 32 : 20) + 4 * kRayNK * 4 + (256 + 32) * 4 + (WC / 32) * 4 + kRayStats * 8;
   // per-warp global scratch (32-bit words): slot records (float4), slot table
   // entries, free stack, slot -> active index map, two waiting-list buffers
   // (key, slot), the active extension (5 arrays) [, slot d (float4), the
@@ -107,6 +109,11 @@ __device__ __forceinline__ void act_get(const ActSet& A, int i, float4& r, int& 
     r = make_float4(A.gth[g], A.gtl[g], A.gh[g], A.gc[g]);
     jk = A.gjk[g];
   }
+}
+__device__ __forceinline__ float4 act_getE(const ActSet& A, int i) {
+  if (i < kRayAS) return make_float4(A.th[i], A.tl[i], A.h[i], A.c[i]);
+  const int g = i - kRayAS;
+  return make_float4(A.gth[g], A.gtl[g], A.gh[g], A.gc[g]);
 }
 __device__ __forceinline__ void act_put(const ActSet& A, int i, float4 r, int jk) {
   if (i < kRayAS) {
@@ -252,6 +259,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
   float *nk0, *nk1, *wk0, *wk1;
   int *nv0, *nv1, *wv0, *wv1, *rh, *s_j, *s_fre, *s_map;
   unsigned* stb;
+  unsigned long long* wst;  // the warp's statistics: rays, candidates, knots, windows, tests, largest waiting
+                            // table, flags, terminated rays, most active, capped windows, tangency tests
   float4* s_rec;
   float4* s_dp = nullptr;  // shaded variant: slot d (the vector from the ray to the particle)
   {
@@ -274,6 +283,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
     nv1 = (int*)(w + 3 * kRayNK);
     rh = (int*)(w + 4 * kRayNK);
     stb = (unsigned*)(rh + 256 + 32);
+    wst = (unsigned long long*)(stb + WCX / 32);
     float* g = p.scratch + (size_t)(blockIdx.x * NW + wid) * RayCaps<BIG, GR>::WORDS;
     s_rec = (float4*)g;
     s_j = (int*)(g + 4 * WCX);
@@ -302,9 +312,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
   for (int i = threadIdx.x; i < p.tf_n; i += blockDim.x) s_tf[i] = p.tf[i];
   __syncthreads();
   const TfCtx tfc{s_tf, p.tf_n, p.tf_lo, p.tf_inv_dv, p.tf_dv};
-  unsigned long long st_cand = 0, st_tests = 0, st_knots = 0, st_win = 0, st_rays = 0, st_ert = 0, st_capped = 0,
-                     st_tan = 0;
-  int st_maxtab = 0, st_flags = 0, st_maxact = 0;
+  if (lane < kRayStats) wst[lane] = 0ull;
+  __syncwarp();
   PT_DECL
 #ifdef SPHDVR_PHASE_TIMING
   unsigned long long why_n[6] = {0, 0, 0, 0, 0, 0};  // what ended each window (instrumented builds)
@@ -408,8 +417,8 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
     float dens = 0.f;   // knots per unit length of the previous window (0: none)
     long long dbg_np = 0, dbg_nc = 0, dbg_win = 0;
     int rf = 0, ray_tan = 0, ray_maxact = 0;  // this ray's flags, tangency-band tests, most active particles
-    unsigned long long r_tests = 0, r_cand = 0, r_win = 0, r_capped = 0;  // this ray's counters
-    unsigned long long my_knots = 0;
+    unsigned r_tests = 0, r_cand = 0, r_win = 0, r_capped = 0, my_knots = 0;  // this ray's counters
+    int ray_maxtab = 0;  // most waiting slots in use
 
     const int2 tr = p.tile_range[(BT ? p.frames[fb].tile_base : 0) + tile];
     const int ce = tr.y;
@@ -893,7 +902,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
                   const int jk = *jp;
                   if ((jk >> 16) & 15) {
                     atomicOr(stb + (e >> 5), 1u << (e & 31));
-                    hmin_new = fminf(hmin_new, s_rec[e].z);
+                    hmin_new = fminf(hmin_new, act_getE(A, ni).z);
                   } else {
                     *jp = jk | (15 << 16);
                   }
@@ -1189,7 +1198,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
           nnk += n_store;
           r_cand += n_new;
           dbg_nc += n_new;
-          st_maxtab = max(st_maxtab, hwm - nfree);
+          ray_maxtab = max(ray_maxtab, hwm - nfree);
         }
         __syncwarp();
       }
@@ -1207,22 +1216,31 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
         if (k < (unsigned)p.ovf_cap) {
           p.ovf[1 + k] = (unsigned)item_all;
         } else {
-          st_flags |= kRayFlagRefit | (rf & 3);  // the list is full: this pixel stays unwritten
+          wst[6] |= (unsigned long long)(kRayFlagRefit | (rf & 3));  // the list is full: this pixel stays unwritten
         }
       }
       continue;
     }
     if (FB && (rf & 3)) rf |= kRayFlagRefit;
-    ++st_rays;
-    if (p.tau_ert > 0.f && tau_ray > p.tau_ert) ++st_ert;
-    st_knots += my_knots;
-    st_tests += r_tests;
-    st_cand += r_cand;
-    st_win += r_win;
-    st_capped += r_capped;
-    st_flags |= rf;
-    st_maxact = max(st_maxact, ray_maxact);
-    st_tan += (unsigned long long)ray_tan;
+    {
+      // the ray's counters into the warp's statistics (tests and tangency-band
+      // tests are counted per lane)
+      const int tn = warp_sum_i(ray_tan), rt = warp_sum_i((int)r_tests);
+      if (lane == 0) {
+        wst[0] += 1ull;
+        wst[1] += r_cand;
+        wst[2] += my_knots;
+        wst[3] += r_win;
+        wst[4] += (unsigned)rt;
+        wst[5] = max(wst[5], (unsigned long long)ray_maxtab);
+        wst[6] |= (unsigned long long)rf;
+        if (p.tau_ert > 0.f && tau_ray > p.tau_ert) wst[7] += 1ull;
+        wst[8] = max(wst[8], (unsigned long long)ray_maxact);
+        wst[9] += r_capped;
+        wst[10] += (unsigned)tn;
+      }
+      __syncwarp();
+    }
     if (DBG) {
       const int tn = warp_sum_i(ray_tan);
       if (lane == 0) {
@@ -1248,24 +1266,19 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
     }
   }
   // ---- statistics (one set of atomics per warp)
-  unsigned long long tests = st_tests, tan = st_tan;
-#pragma unroll
-  for (int o2 = 16; o2; o2 >>= 1) {
-    tests += __shfl_xor_sync(kFull, tests, o2);
-    tan += __shfl_xor_sync(kFull, tan, o2);
-  }
+  __syncwarp();
   if (lane == 0 && p.stats) {
-    atomicAdd(p.stats + 0, st_rays);
-    atomicAdd(p.stats + 1, st_cand);
-    atomicAdd(p.stats + 2, st_knots);
-    atomicAdd(p.stats + 3, st_win);
-    atomicAdd(p.stats + 5, tests);
-    atomicMax(p.stats + 6, (unsigned long long)st_maxtab);
-    atomicOr(p.stats + 7, (unsigned long long)st_flags);
-    atomicAdd(p.stats + 8, st_ert);
-    atomicMax(p.stats + 11, (unsigned long long)st_maxact);
-    atomicAdd(p.stats + 12, st_capped);
-    atomicAdd(p.stats + 13, tan);
+    atomicAdd(p.stats + 0, wst[0]);
+    atomicAdd(p.stats + 1, wst[1]);
+    atomicAdd(p.stats + 2, wst[2]);
+    atomicAdd(p.stats + 3, wst[3]);
+    atomicAdd(p.stats + 5, wst[4]);
+    atomicMax(p.stats + 6, wst[5]);
+    atomicOr(p.stats + 7, wst[6]);
+    atomicAdd(p.stats + 8, wst[7]);
+    atomicMax(p.stats + 11, wst[8]);
+    atomicAdd(p.stats + 12, wst[9]);
+    atomicAdd(p.stats + 13, wst[10]);
 #ifdef SPHDVR_PHASE_TIMING
     for (int ph = 0; ph < 10; ++ph) atomicAdd(p.stats + 16 + ph, (unsigned long long)pt_acc[ph]);
     for (int k = 0; k < 6; ++k) atomicAdd(p.stats + 26 + k, why_n[k]);
