@@ -768,6 +768,15 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
           const int rb = warp_bucket_sort(nk0, nv0, nk1, nv1, T_all, rh);
           const float* GK = rb ? nk1 : nk0;
           const int* GV = rb ? nv1 : nv0;
+          // the first pass keeps each knot's difference coefficients for the
+          // second (D <= 3, unshaded): in the free key/value buffers and in
+          // the knot's own value word, which the second pass no longer needs
+          constexpr bool kStash = !GR && D <= 3;
+          // (the value words hold the bits of a float: written and read as int,
+          // so that no access of the value array goes through another type)
+          float* const stash0 = rb ? nk0 : nk1;
+          int* const stash1 = rb ? nv0 : nv1;
+          int* const stash2 = rb ? nv1 : nv0;
           if (cap2 < U) {
             U = cap2;
             capped = true;
@@ -879,6 +888,11 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
               float dl[NC * D];
               deltas(i, dl);
               const int vv = GV[i];
+              if (kStash) {
+                stash0[i] = dl[0];
+                if (D >= 2) stash1[i] = __float_as_int(dl[1 % D]);
+                if (D >= 3) stash2[i] = __float_as_int(dl[2 % D]);
+              }
               add_deltas(agg, dl);
               ulast = ur;
               // mark the knot processed (a starter's first knot starts it)
@@ -1026,7 +1040,13 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
               ua = uat(i);
               if (i > i0) shift_all(P, ua - lastu);
               float dl[NC * D];
-              deltas(i, dl);
+              if (kStash) {
+                dl[0] = stash0[i];
+                if (D >= 2) dl[1 % D] = __int_as_float(stash1[i]);
+                if (D >= 3) dl[2 % D] = __int_as_float(stash2[i]);
+              } else {
+                deltas(i, dl);
+              }
               add_deltas(P, dl);
               lastu = ua;
 #pragma unroll
