@@ -57,9 +57,7 @@ WORKLOADS = {
 # ncu capture named in profiles/ (launches_halo16m_2048.md) of the kernel as it is in
 # this tree, keyed by (workload, image size, precision, window_h); None where no
 # capture of the current kernel and options exists.
-PROFILED_DRAM_BYTES = {
-    ("halo16m", 2048, "fp32_anchored", 1.0): 8.737e9 + 254.47e9,
-}
+PROFILED_DRAM_BYTES = {}
 
 
 def replica_rate(total_ms, rays, dist=None, device="cpu"):

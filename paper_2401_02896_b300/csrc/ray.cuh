@@ -726,13 +726,15 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
                     const float4 d4 = s_dp[e];
                     act_putd(A, ni, make_float3(d4.x, d4.y, d4.z));
                   }
-                  s_map[e] = ni;
                 } else {
                   rf |= 1;  // the active set is full
-                  s_map[e] = -1;
                   ne = 0;
                 }
               }
+              // every starter of the range records its entry, -1 for none: the
+              // range comes from the waiting list's absolute FP32 keys, the knots
+              // from positions relative to Ta, so a starter may have no knot below U
+              if (e >= 0) s_map[e] = ne > 0 ? ni : -1;
               int tot;
               const int off = T_all + warp_excl_scan(ne, &tot);
 #pragma unroll
@@ -911,7 +913,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == kRayWarps ? ((GR || CP) ? (GR 
               const int e = ii < ns ? WV[whead + ii] : -1;
               if (e >= 0 && !((stb[e >> 5] >> (e & 31)) & 1u)) {
                 const int ni = s_map[e];
-                if (ni >= 0) {
+                if (ni >= 0 && ni < cap_act) {
                   int* jp = act_jk_ptr(A, ni);
                   const int jk = *jp;
                   if ((jk >> 16) & 15) {

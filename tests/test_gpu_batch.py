@@ -76,6 +76,23 @@ def test_batch_equals_separate_frames(env, opts):
     assert st["rays"] == sum(c["width"] * c["height"] for c in cams)
 
 
+@pytest.mark.parametrize("prec", ["fp32_anchored", "fp32_naive", "fp32_kahan"])
+def test_every_knot_composited_once(env, prec):
+    """Without early termination the window kernel composites each knot of each candidate exactly once: the
+    frame's knot count is K + 1 times its candidate count, separately and batched (a particle dropped from
+    the waiting list or the active set, or a knot taken twice, breaks the count)."""
+    S, torch, ctx, lut, lt, P, ds, _, tf, _ = env
+    cams = _cams()
+    opts = dict(precision=prec, ert_eps=0.0)
+    for c in cams:
+        _single(S, torch, ctx, ds, lt, [c], tf, opts)
+        st = S.sphdvr_frame_stats(ctx)
+        assert st["knots"] == (lut["K"] + 1) * st["segments"] and st["segments"] > 0, st
+    _batch(S, torch, ctx, ds, lt, cams, tf, opts)
+    st = S.sphdvr_frame_stats(ctx)
+    assert st["knots"] == (lut["K"] + 1) * st["segments"], st
+
+
 def test_batch_of_one_and_of_eight(env):
     S, torch, ctx, lut, lt, P, ds, _, tf, _ = env
     cams = [SY.orbit_camera(40 + 8 * i, 56, azimuth_deg=45.0 * i) for i in range(S.MAX_BATCH)]

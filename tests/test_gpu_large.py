@@ -71,6 +71,8 @@ def _three_way(S, ctx, ds, lt, P, lut, cam, tf, pix, name):
     assert err_prod <= PIXEL_ABS + ERT_EPS, err_prod
     img0, st0 = _production(S, ctx, ds, lt, cam, tf, 0.0)
     assert st0["overflow"] == 0, st0
+    # without early termination every knot of every candidate is composited exactly once
+    assert st0["knots"] == (lut["K"] + 1) * st0["segments"], st0
     assert np.array_equal(img0[pix], g["rgba"]), np.abs(img0[pix] - g["rgba"]).max()
     print("%s: field rel-L2 worst %.3g, hook pixel worst %.3g, production pixel worst %.3g (ERT %g, %d rays "
           "terminated), tangency-band tests %d of %d candidates on %d rays"

@@ -12,9 +12,10 @@ rays, worst and median absolute pixel error.  What must hold:
 * the plain recurrences (FP32, and FP64 running coefficients over FP32 difference coefficients) drift:
   their field error is larger than the anchored one (Sec. 4.1 "sprinkling");
 * FP32 with compensated running sums (TwoSum, the compensation shifted alongside) drifts too: it lowers the
-  plain FP32 recurrence's field error (by 4x to 35x on the 1M set) but stays above
-  the anchored path's, and from D = 2 on above the field tolerance: the residue of each finished particle's
-  FP32 difference coefficients, which no summation order removes, drives the drift;
+  plain FP32 recurrence's median field error (2x to 5x on the 1M set; the worst rays of the two drifting
+  modes vary too much from ray to ray to be ordered) but stays above the anchored path's, and from D = 2 on
+  above the field tolerance: the residue of each finished particle's FP32 difference coefficients, which no
+  summation order removes, drives the drift;
 * the quantised integer path (Sec. 4.2-4.4, 64 bits, quanta of the data set) renders without a flag; its
   error is the quantisation's (one length quantum serves particles whose h spans two decades) and is
   reported, bounded only against gross failure here.
@@ -86,7 +87,8 @@ def test_precision_degree_sweep():
         assert ri["field_worst"] <= FIELD_REL_L2 and ri["pixel_worst"] <= PIXEL_ABS, ri
         assert by[(D, "fp32_naive")]["field_worst"] > a["field_worst"]
         k = by[(D, "fp32_kahan")]
-        assert a["field_worst"] < k["field_worst"] <= by[(D, "fp32_naive")]["field_worst"], k
+        assert a["field_worst"] < k["field_worst"], k
+        assert k["field_median"] <= by[(D, "fp32_naive")]["field_median"], k
         if D >= 2:
             assert k["field_worst"] > FIELD_REL_L2, k
         assert by[(D, "int64_quant")]["pixel_worst"] < 0.05, by[(D, "int64_quant")]
