@@ -57,7 +57,9 @@ WORKLOADS = {
 # ncu capture named in profiles/ (launches_halo16m_2048.md) of the kernel as it is in
 # this tree, keyed by (workload, image size, precision, window_h); None where no
 # capture of the current kernel and options exists.
-PROFILED_DRAM_BYTES = {}
+PROFILED_DRAM_BYTES = {
+    ("halo16m", 2048, "fp32_anchored", 2.0): 8.46e9 + 256.28e9,
+}
 
 
 def replica_rate(total_ms, rays, dist=None, device="cpu"):
