@@ -244,6 +244,24 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def poll_completions(srv, tickets, clock=time.perf_counter, sleep=time.sleep, period=0.005):
+    """Latencies of submitted frames, polled: `tickets` holds (submission time, size, ticket); the server's
+    wait(ticket, 0) returns False while a frame is in flight and True once it has completed (it raises for a
+    failed frame).  Returns [(completion - submission, size)] in completion order."""
+    lat, pending = [], list(tickets)
+    while pending:
+        still = []
+        for ts, r_, t_ in pending:
+            if srv.wait(t_, 0):
+                lat.append((clock() - ts, r_))
+            else:
+                still.append((ts, r_, t_))
+        pending = still
+        if pending:
+            sleep(period)
+    return lat
+
+
 def serving_stream(S, torch, ctx, tf_all, dev, per_rate=20, seed=2024, workers=3):
     """C4: four resident clustered data sets (1M, 4M, 16M, 32M particles of the halo generator, seeds +0..3),
     requests with random orbit cameras and sizes uniform over {256, 512, 1024, 2048} squared, Poisson arrivals.
@@ -278,18 +296,7 @@ def serving_stream(S, torch, ctx, tf_all, dev, per_rate=20, seed=2024, workers=3
             outs.append(o_)
             tix.append((time.perf_counter(), r_, srv.submit(sets[k][1], lut, c_, sets[k][2], dict(ert_eps=1e-5),
                                                             o_.data_ptr())))
-        lat = []
-        pending = list(tix)
-        while pending:  # completion times, polled
-            still = []
-            for ts, r_, t_ in pending:
-                if srv.wait(t_, 0):  # False while the frame is still in flight; raises if it failed
-                    lat.append((time.perf_counter() - ts, r_))
-                else:
-                    still.append((ts, r_, t_))
-            pending = still
-            if pending:
-                time.sleep(0.005)
+        lat = poll_completions(srv, tix)
         wall = time.perf_counter() - t0
         srv.destroy()
         rays = sum(r_ * r_ for _, r_, _ in reqs)
