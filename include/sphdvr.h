@@ -476,7 +476,9 @@ sphdvr_status sphdvr_measure_fp32_peak(sphdvr_ctx* ctx, void* stream, double* tf
  * knot arrived behind the processed part of its ray, bit 4 INT64_QUANT: a
  * particle's rounded coefficient, integer knot offset or centre beyond 2^62,
  * the quanta too fine for it -- a per-particle bound, not a proof that the
- * summed integers fit: that needs quant_sigma to bound the field),
+ * summed integers fit: that needs quant_sigma to bound the field; bit 6 a
+ * ray of the FP64, reinitialisation or quantised modes reached 65,536 windows
+ * and was ended there, its pixel wrong),
  * [8] rays stopped
  * by early termination, [9] device time of the render kernel in ns (CUDA
  * events on the render stream), [10] kernel launches of the frame,

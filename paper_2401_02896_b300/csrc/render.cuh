@@ -51,6 +51,8 @@
 namespace sphdvr {
 
 constexpr int kCap = 4096;          // particle entries per ray
+constexpr int kMaxRayWindows = 1 << 16;  // windows one ray may take in k_render
+constexpr int kFlagWindowLimit = 64;     // frame flag: a ray reached kMaxRayWindows (pixel wrong)
 constexpr int kNK = 512;            // new knots awaiting a merge (shared memory)
 constexpr int kLevels = 128;        // smoothing-length bins (quarter octaves) for the window limit
 constexpr int kLevelBase = (127 - 28) << 2;  // bin 0 starts at h = 2^-28
@@ -1230,6 +1232,13 @@ __global__ void __launch_bounds__(NW * 32, (NW == 4 ? 4 : 1)) k_render(RenderPar
 
         // ---- windows: every knot below F is final
         while (!done) {
+          if (win_count >= kMaxRayWindows) {
+            // a ray this long (two orders of magnitude beyond the windows of
+            // any ray measured) is ended here and flagged: its pixel is wrong
+            st_flags |= kFlagWindowLimit;
+            done = true;
+            break;
+          }
           PT_BEGIN
           const float* WK = wb ? T.wk1 : T.wk0;
           const int* WV = wb ? T.wv1 : T.wv0;
