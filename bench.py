@@ -263,7 +263,7 @@ def poll_completions(srv, tickets, clock=time.perf_counter, sleep=time.sleep, pe
 
 
 def serving_stream(S, torch, ctx, tf_all, dev, per_rate=20, seed=2024, workers=3):
-    """C4: four resident clustered data sets (1M, 4M, 16M, 32M particles of the halo generator, seeds +0..3),
+    """Serving stream: four resident clustered data sets (1M, 4M, 16M, 32M particles of the halo generator, seeds +0..3),
     requests with random orbit cameras and sizes uniform over {256, 512, 1024, 2048} squared, Poisson arrivals.
     The service rate is measured first (a burst of requests queued at once); then three arrival rates
     (0.5, 0.8 and 1.2 times it) with `per_rate` requests each: p50/p99 submission-to-completion latency per
@@ -330,7 +330,7 @@ def serving_stream(S, torch, ctx, tf_all, dev, per_rate=20, seed=2024, workers=3
 
 
 def precision_sweep_times(S, torch, ctx, ds, w, tf, cam, dev, stream, degrees=(1, 2, 3, 4)):
-    """C3's frame times: each precision mode x degree D on the workload's frame (kernel time, CUDA events),
+    """Precision / degree sweep frame times: each precision mode x degree D on the workload's frame (kernel time, CUDA events),
     and each mode's largest pixel difference from the FP32 anchored frame of the same D.  (The errors against
     the FP64 oracle are measured by tests/test_gpu_precision_sweep.py.)"""
     W, H = cam["width"], cam["height"]
@@ -389,9 +389,9 @@ def main():
     ap.add_argument("--shading-frame", type=int, default=1,
                     help="time a shaded frame beside the unshaded one (1M-particle halo mixture, 512x512; 0: skip)")
     ap.add_argument("--precision-sweep", action="store_true",
-                    help="also time every precision mode x D in {1,2,3,4} on the workload's frame (C3)")
+                    help="also time every precision mode x D in {1,2,3,4} on the workload's frame")
     ap.add_argument("--serving-stream", type=int, default=0,
-                    help="requests per arrival rate of the C4 serving stream over four resident data sets (0: skip)")
+                    help="requests per arrival rate of the serving stream over four resident data sets (0: skip)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.res > 0:

@@ -1,4 +1,4 @@
-"""Precision / degree sweep (the survey's C3 workload): every precision mode x D in {1, 2, 3, 4}, errors per
+"""Precision / degree sweep (halo mixture, h over three decades): every precision mode x D in {1, 2, 3, 4}, errors per
 pixel and per ray field against the FP64 oracle on 48 seeded rays.
 
 By default a 1,000,000-particle halo mixture at 512x512 (the test suite's size); with SPHDVR_SWEEP_FULL=1 the
